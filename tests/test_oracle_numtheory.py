@@ -1,0 +1,86 @@
+"""Pins for oracle.numtheory: Miller-Rabin, the prime table, primitive roots, cosets."""
+
+import random
+
+from oracle import numtheory as nt
+
+
+def _trial(n):
+    if n < 2:
+        return False
+    d = 2
+    while d * d <= n:
+        if n % d == 0:
+            return False
+        d += 1
+    return True
+
+
+def test_is_prime_matches_trial_division_small():
+    for n in range(0, 5000):
+        assert nt.is_prime(n) == _trial(n), n
+
+
+def test_is_prime_random_31_bit():
+    rng = random.Random(7)
+    for _ in range(300):
+        n = rng.randrange(1 << 30, 1 << 31)
+        assert nt.is_prime(n) == _trial(n), n
+
+
+def test_strong_pseudoprimes_rejected():
+    # 2047 is a base-2 strong pseudoprime; 3215031751 is one to bases 2, 3, 5 and 7;
+    # 25326001 to bases 2, 3 and 5; all composite.
+    for n in (2047, 3215031751, 25326001, 561, 1105, 1729):
+        assert not nt.is_prime(n)
+
+
+def test_prime_table_definition():
+    t = nt.prime_table(40)
+    step = 1 << nt.PRIME_LOG_ORDER
+    assert all((1 << 30) < p < (1 << 31) for p in t)
+    assert all(p % step == 1 for p in t)
+    assert all(t[i] > t[i + 1] for i in range(len(t) - 1))
+    for p in t[:5]:
+        assert _trial(p)
+    # no candidate of the form q*2^14+1 between consecutive entries is prime
+    for a, b in zip(t[:4], t[1:5]):
+        c = b + step
+        while c < a:
+            assert not _trial(c)
+            c += step
+    # the first candidate below 2^31 that is skipped is composite
+    top = ((1 << 31) - 2) // step * step + 1
+    c = top
+    while c > t[0]:
+        assert not _trial(c)
+        c -= step
+
+
+def test_primitive_root_brute_force_small_primes():
+    for p in [3, 5, 7, 17, 97, 257, 769, 7681, 12289]:
+        g = nt.primitive_root(p)
+
+        def order(x):
+            k, y = 1, x % p
+            while y != 1:
+                y = y * x % p
+                k += 1
+            return k
+
+        assert order(g) == p - 1
+        for h in range(2, g):
+            assert order(h) < p - 1
+
+
+def test_root_of_unity_and_coset():
+    for p in nt.prime_table(3):
+        for n in (1, 2, 64, 1024, 1 << 14):
+            w = nt.root_of_unity(p, n)
+            assert pow(w, n, p) == 1
+            if n > 1:
+                assert pow(w, n // 2, p) == p - 1
+        pts = nt.coset_points(p, 64)
+        assert len(set(pts)) == 64
+        assert all(pow(x, 64, p) != 1 for x in pts)
+        assert 1 not in pts and p - 1 not in pts and 0 not in pts
