@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the exact bivariate resultant on GB300.
+
+Workload: the discriminant-type resultant res_y(f, df/dy) of one dense random curve f of
+total degree 32 with uniform signed 32-bit coefficients (seeded, synthetic).  One step is
+one whole resultant: plan, reduction mod every prime, evaluation on each prime's point
+set, the univariate resultants mod p, interpolation and mixed-radix reconstruction of
+the integer coefficients.
+
+``value`` is resultants per second over all ranks with device-resident inputs (CUDA
+events on the library's stream, L2 flushed between steps outside the events); ``e2e``
+is the same metric through the C ABI call with host buffers (copies included).
+
+--impl reference times the CPU oracle (exact Bareiss determinants at integer points
+plus exact interpolation) on a bounded sample of the same workload on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact res_y(f,g) in Z[x] per second"
+UNIT = "resultants/s"
+WORKLOAD = "res_y(f, df/dy), f dense total degree 32, signed 32-bit coefficients, seed 1"
+SEED = 1
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------------------
+
+def _oracle_point(args):
+    f, g, x0 = args
+    from oracle.resultant import res_at_point
+    return res_at_point(f, g, x0)
+
+
+def _oracle_sample(f, g, npts, pool, cores):
+    """Wall time of npts exact point determinants on the pool (the oracle's route)."""
+    from oracle.resultant import degree_bound
+    D = degree_bound(f, g)
+    x0 = -(D // 2)
+    xs = [x0 + (t * 131) % (D + 1) for t in range(npts)]
+    t0 = time.perf_counter()
+    pool.map(_oracle_point, [(f, g, x) for x in xs], chunksize=1)
+    return time.perf_counter() - t0, D
+
+
+def _oracle_interp_time(D, bits):
+    """Exact interpolation of D + 1 values of the result's size (synthetic values)."""
+    import random
+    from oracle.resultant import interpolate_consecutive
+    rng = random.Random(5)
+    # values of a degree-D polynomial with `bits`-bit coefficients at small integers:
+    vals = [rng.getrandbits(bits + 12) - (1 << (bits + 11)) for _ in range(D + 1)]
+    t0 = time.perf_counter()
+    try:
+        interpolate_consecutive(-(D // 2), vals)
+    except ArithmeticError:
+        pass  # synthetic values need not interpolate to an integer polynomial
+    return time.perf_counter() - t0
+
+
+def _cpu_pool():
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+def _cpu_baseline(f, g, pool, cores, npts):
+    from oracle.resultant import bound_sq
+    t_pts, D = _oracle_sample(f, g, npts, pool, cores)
+    bits = (bound_sq(f, g).bit_length() + 1) // 2
+    t_int = _oracle_interp_time(D, bits)
+    per_res = t_pts * (D + 1) / npts + t_int
+    return {"value": 1.0 / per_res, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{npts} of the {D + 1} exact Bareiss point determinants (63x63 over Z) "
+                      f"on {cores} processes, scaled to all {D + 1} points, plus one exact "
+                      f"interpolation of {D + 1} values ({t_pts:.2f} s + {t_int:.2f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from workloads import cfg2_pair
+    f, g = cfg2_pair(SEED)
+    pool, cores = _cpu_pool()
+    npts = max(cores, 8)
+    from oracle.resultant import bound_sq
+    t_int = None
+    step_s = []
+    for i in range(args.warmup + args.steps):
+        t_pts, D = _oracle_sample(f, g, npts, pool, cores)
+        if t_int is None:
+            t_int = _oracle_interp_time(D, (bound_sq(f, g).bit_length() + 1) // 2)
+        per_res = t_pts * (D + 1) / npts + t_int
+        if i >= args.warmup:
+            step_s.append(per_res)
+    pool.close()
+    ms = 1000.0 * statistics.mean(step_s)
+    value = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step {npts} exact point determinants on {cores} "
+                                       f"processes scaled to {D + 1} points, plus one exact "
+                                       f"interpolation"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        self.path = tempfile.mktemp(suffix=".csv")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pool = cores = None
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if want_cpu:
+        pool, cores = _cpu_pool()   # spawn before the first GPU call
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1201_1548_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    import paper_1201_1548_gb300 as bs
+    from paper_1201_1548_gb300._abi import _Bipoly, _Upoly
+    import ctypes as C
+    from workloads import cfg2_pair
+
+    f, g = cfg2_pair(SEED)
+    plan = bs.bs_plan(f, g)
+    ctx = bs.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream.cuda_stream)
+    af, dxf, dyf, Lf = bs.bipoly_to_limbs(f)
+    ag, dxg, dyg, Lg = bs.bipoly_to_limbs(g)
+    df = torch.from_numpy(af.view(np.int32).copy()).cuda()
+    dg = torch.from_numpy(ag.view(np.int32).copy()).cuda()
+    dcap, lcap = ctx.resultant_bounds((dxf, dyf, Lf), (dxg, dyg, Lg))
+    out = torch.zeros((dcap + 1) * lcap, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        ctx.resultant_device(df.data_ptr(), (dxf, dyf, Lf), dg.data_ptr(), (dxg, dyg, Lg),
+                             out.data_ptr(), (dcap, lcap))
+
+    # correctness guard outside timing: device path == host path
+    host = ctx.resultant(f, g)
+    step()
+    ctx.device_status()
+    dev = bs.limbs_to_ints(out.cpu().numpy().view(np.uint32), dcap + 1, lcap)
+    while dev and dev[-1] == 0:
+        dev.pop()
+    if dev != host:
+        raise SystemExit("device path and host path disagree")
+
+    ctx.profile(True)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    ctx.device_status()
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stages = []
+    for i in range(args.steps):
+        flush.zero_()
+        e0[i].record(stream)
+        step()
+        e1[i].record(stream)
+        stages.append(ctx.stage_times())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ctx.device_status()
+    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+    srt = sorted(step_ms)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+    k3 = statistics.mean(s[2] for s in stages)
+    stage_avg = [statistics.mean(s[i] for s in stages) for i in range(5)]
+    instances = plan["k_total"] * plan["N"]
+    m_e, n_e = plan["m_e"], plan["n_e"]
+    # dominant kernel: the univariate-resultant stage (ALU bound)
+    alg_mulmods = instances * m_e * n_e
+    achieved = alg_mulmods / (k3 * 1e-3) / 1e9
+    probe = {k: ctx.alu_probe(i) / 1e12 for i, k in
+             enumerate(("mad_lo_Tops", "mad_hi_Tops", "mad_wide_Tops", "mulmod_Tops"))}
+    import torch.cuda as tc
+    props = tc.get_device_properties(local)
+    sms = props.multi_processor_count
+    max_mhz = clk.get("sm_max_mhz") or 2070.0
+    # peak: SMs x max clock x 64 32-bit integer multiply lanes per SM per clock, divided by
+    # the 4 multiply-pipe issues of one Montgomery multiplication (two wide products
+    # counted twice, one low product, one high product)
+    peak = sms * max_mhz * 1e6 * 64 / 4 / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gmulmod/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_unires<33>", "alg_per_launch": alg_mulmods,
+            "note": "algorithmic m_e*n_e mulmods per (prime, point) instance"}
+
+    # e2e through the C ABI with pinned host buffers
+    hf = torch.from_numpy(af.view(np.int32).copy()).pin_memory()
+    hg = torch.from_numpy(ag.view(np.int32).copy()).pin_memory()
+    pdeg = plan["D"]
+    hout = torch.zeros((pdeg + 1) * plan["out_limbs"], dtype=torch.int32).pin_memory()
+    fb = _Bipoly(dxf, dyf, Lf, hf.data_ptr())
+    gb = _Bipoly(dxg, dyg, Lg, hg.data_ptr())
+    lib = bs.load_library()
+    ctx.profile(False)
+
+    def e2e_call():
+        ob = _Upoly(pdeg, plan["out_limbs"], hout.data_ptr())
+        rc = lib.bs_resultant(ctx.h, C.byref(fb), C.byref(gb), 1, C.byref(ob))
+        if rc:
+            raise SystemExit(f"bs_resultant failed: {rc}")
+        return ob.deg
+
+    for _ in range(args.warmup):
+        e2e_call()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        deg = e2e_call()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_val = world * 1.0 / e2e_s
+    h2d = (af.nbytes + ag.nbytes)
+    d2h = (deg + 1) * plan["out_limbs"] * 4
+
+    cpu = None
+    if want_cpu:
+        cpu = _cpu_baseline(f, g, pool, cores, npts=max(32, 2 * cores))
+        pool.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "m_y": m_e, "n_y": n_e, "D": plan["D"],
+                           "points_per_prime": plan["N"], "primes": plan["k_need"],
+                           "primes_evaluated": plan["k_total"],
+                           "l2": "flushed between steps (256 MiB write, outside the events)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "latency_ms": {"p50": p50, "p99": p99},
+                "modp_univariate_resultants_per_s": world * instances / (ms * 1e-3),
+                "stage_ms": dict(zip(("plan", "reduce_eval", "unires", "interp", "crt"), stage_avg)),
+                "roofline": roof, "alu_probe": probe, "clocks": clk,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": 6 * args.steps,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * bsres.h -- C ABI of the GB300 multi-modular resultant / gcd library (libbsres.so).
+ *
+ * The library computes, exactly and on one GPU, the symbolic operations that the
+ * Bisolve / GeoTop curve analysis needs (Sec. 5.1 of the paper, "GPU-accelerated
+ * symbolic computations"):
+ *
+ *   - the bivariate resultant res(f, g; y) in Z[x] (or res(f, g; x) in Z[y]) by the
+ *     modular route of Sec. 5.1 steps (a)-(e): reduce modulo many 31-bit primes,
+ *     evaluate at many points, take univariate resultants mod p, interpolate, and
+ *     reconstruct the integer coefficients by mixed-radix Chinese remaindering;
+ *   - the monic gcd of two polynomials in Z_p[x] (Sec. 5.1, "Computing gcds in Z[x]",
+ *     step (b));
+ *   - the square-free part of a polynomial in Z[x] (Sec. 2.1, BiProject: Yun's
+ *     square-free factorisation starts from gcd(R, R')).
+ *
+ * Integer encoding.  Every integer coefficient is a fixed number of little-endian
+ * uint32 limbs in two's complement (limb 0 is the least significant; the sign is the
+ * top bit of the last limb).  All coefficients of one polynomial use the same limb count.
+ *
+ * Bivariate layout (Sec. 2, "Notation": f = sum f_ij x^i y^j).  A bs_bipoly is a dense
+ * (deg_y + 1) x (deg_x + 1) grid: the coefficient of x^i y^j starts at
+ * c[(j * (deg_x + 1) + i) * limbs].  deg_x and deg_y are grid extents; trailing zero rows
+ * or columns are allowed (the library finds the actual degrees itself).
+ *
+ * Univariate layout.  A bs_upoly holds deg + 1 coefficients in ascending order, the
+ * coefficient of x^i at c[i * limbs]; deg = -1 denotes the zero polynomial.
+ *
+ * Ownership.  Inputs are borrowed for the duration of a call (or, for the *_device
+ * entry points, until the work enqueued on the context's stream has finished).
+ * Outputs are caller-allocated.  The context owns its device memory and stream.
+ *
+ * Errors.  Every entry point returns a status code (BS_OK = 0 on success).  A call that
+ * fails leaves its outputs unspecified and the context usable.  bs_error_string()
+ * turns a code into text; bs_last_error_detail() returns a message about the most
+ * recent failure on a context.
+ *
+ * Threads.  A context may be used by one host thread at a time.
+ */
+#ifndef BSRES_H
+#define BSRES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BS_OK            0
+#define BS_ERR_ARG       1  /* invalid argument (null pointer, negative size, bad var)  */
+#define BS_ERR_NOMEM     2  /* device memory budget exceeded (admission refused)        */
+#define BS_ERR_UNLUCKY   3  /* more unlucky primes than spare primes were provided for  */
+#define BS_ERR_TIMEOUT   4  /* a bounded device-side wait expired                       */
+#define BS_ERR_CUDA      5  /* a CUDA runtime call failed                               */
+#define BS_ERR_ZERO      6  /* square-free part of the zero polynomial                  */
+#define BS_ERR_RANGE     7  /* problem exceeds the prime table or the transform size    */
+#define BS_ERR_INTERNAL  8  /* a device-side consistency check failed                   */
+#define BS_ERR_CAPACITY  9  /* caller-provided output capacity is too small             */
+
+typedef struct bs_ctx bs_ctx;
+
+typedef struct {
+    int32_t deg_x;        /* grid extent in x (>= 0)                                   */
+    int32_t deg_y;        /* grid extent in y (>= 0)                                   */
+    int32_t limbs;        /* uint32 limbs per coefficient (1..64)                      */
+    const uint32_t *c;    /* (deg_y+1)*(deg_x+1)*limbs limbs, layout above             */
+} bs_bipoly;
+
+typedef struct {
+    int32_t deg;          /* degree, or -1 for the zero polynomial (capacity on input) */
+    int32_t limbs;        /* limbs per coefficient (capacity on input)                 */
+    uint32_t *c;          /* (deg+1)*limbs limbs                                       */
+} bs_upoly;
+
+/* Work statistics of the most recent resultant call on a context. */
+typedef struct {
+    int32_t jobs;             /* resultants in the call                                 */
+    int64_t primes_needed;    /* sum over jobs of the primes the coefficient bound asks */
+    int64_t primes_evaluated; /* sum over jobs of the primes evaluated (with spares)    */
+    int64_t primes_rejected;  /* primes dropped as unlucky (lc vanishing mod p or at a  */
+                              /* point of the prime's evaluation set)                   */
+    int64_t instances;        /* univariate resultants mod p computed                   */
+    int64_t mulmods_alg;      /* algorithmic count m_y*n_y summed over instances        */
+    int32_t max_points;       /* largest transform size N used                          */
+    int32_t max_primes;       /* largest prime count of one job                         */
+} bs_stats;
+
+/* ---------------------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `mem_budget` caps the device memory the
+ * context may hold for work buffers (0 = 90% of the free memory).  The context creates
+ * its own non-blocking stream.  On success *out receives the context. */
+int bs_init(int device, size_t mem_budget, bs_ctx **out);
+
+/* Destroy a context and release its device memory (waits for its stream). */
+void bs_free(bs_ctx *ctx);
+
+/* Make the context enqueue its work on `stream` (a cudaStream_t; NULL restores the
+ * context's own stream).  The caller keeps ownership of the stream. */
+int bs_set_stream(bs_ctx *ctx, void *stream);
+
+const char *bs_error_string(int status);
+const char *bs_last_error_detail(const bs_ctx *ctx);
+int bs_last_stats(const bs_ctx *ctx, bs_stats *out);
+
+/* ---------------------------------------------------------------------------------
+ * Resultants (Sec. 2 "Resultants"; modular route Sec. 5.1 steps (a)-(e))
+ * ------------------------------------------------------------------------------ */
+
+/* The plan of res(f, g; var) (host only, no context or GPU needed).  Degrees are the
+ * actual degrees found in the data; e is the eliminated variable, o the other one. */
+typedef struct {
+    int32_t trivial;      /* 0 general; 1 the result is 0; 2 the result is 1            */
+    int32_t m_e, n_e;     /* degrees of f and g in the eliminated variable              */
+    int32_t D;            /* degree bound of the result: min(tdeg f * tdeg g,           */
+                          /*   n_e deg_o f + m_e deg_o g) (Sec. 2); -1 if the result is 0 */
+    int32_t N;            /* points per prime: the smallest power of two > D            */
+    int32_t k_need;       /* primes with prod p > 4 B (B the coefficient bound)         */
+    int32_t k_total;      /* primes evaluated: k_need plus spares for unlucky primes    */
+    int32_t out_limbs;    /* limbs that hold every coefficient of the result            */
+    int64_t log2B_q16;    /* upper bound of log2 B in units of 2^-16                    */
+} bs_plan_info;
+
+int bs_plan(const bs_bipoly *f, const bs_bipoly *g, int var, bs_plan_info *out);
+
+/* Size query.  Upper bounds, computed from the grid extents and limb counts only, on
+ * the degree and on the limbs per coefficient of res(f, g; var).  var = 1 eliminates y
+ * (result in Z[x]), var = 0 eliminates x (result in Z[y]). */
+int bs_resultant_bounds(const bs_bipoly *f, const bs_bipoly *g, int var,
+                        int32_t *deg_cap, int32_t *limbs_cap);
+
+/* res(f, g; var) with host-resident inputs and output.  The result is exact.
+ * If out->c is NULL the call only stores the degree and limb capacities the result
+ * needs into out->deg and out->limbs and returns BS_OK (nothing is computed on the GPU
+ * beyond planning); the degree stored is the bound D of the plan and the limb count
+ * is an upper bound.  Otherwise out->deg and out->limbs give the capacity; on success
+ * out->deg is set to the true degree (-1 for the zero polynomial) and coefficients
+ * deg+1..capacity are zero-filled; each coefficient is sign-extended to out->limbs. */
+int bs_resultant(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var,
+                 bs_upoly *out);
+
+/* res(f, g; var) with device-resident inputs and output, enqueued on the context's
+ * stream without host synchronisation.  f->c, g->c, out->c are device pointers;
+ * out->deg and out->limbs must be at least the capacities that bs_resultant_bounds()
+ * returns.  The plan (degrees, coefficient bound, prime count) is computed on the
+ * device.  The output receives coefficients 0..out->deg (zero above the true degree),
+ * sign-extended to out->limbs.  Device-side failures (unlucky-prime cap, consistency
+ * checks) are recorded in a status word that bs_device_status() returns. */
+int bs_resultant_device(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var,
+                        bs_upoly *out);
+
+/* Wait for the context's stream and return the first device-side status recorded since
+ * the previous call of this function (BS_OK if none), then clear it. */
+int bs_device_status(bs_ctx *ctx);
+
+/* n resultants res(f[i], g[i]; var) with host-resident inputs and outputs, computed
+ * as one batch: all pairs share each kernel launch, the univariate-resultant stage is
+ * one persistent launch per degree class, and the device stages are replayed from a
+ * CUDA graph.  out[i] follows the rules of bs_resultant (a NULL out[i].c makes the
+ * whole call a size query). */
+int bs_resultant_batch(bs_ctx *ctx, int n, const bs_bipoly *f, const bs_bipoly *g,
+                       int var, bs_upoly *out);
+
+/* Univariate resultants mod p with formal degrees (step (c) of Sec. 5.1 on given
+ * images).  For each of n instances: a has da+1 coefficients and b has db+1
+ * coefficients (ascending, reduced into [0, p)), read from a + i*lda and b + i*ldb;
+ * the instance's prime is p[i] and must be one of the library's table primes
+ * (2^30 < p < 2^31, p = 1 mod 2^14).  res[i] = det of the Sylvester matrix of (a, b)
+ * mod p[i], leading coefficients allowed to vanish.  Host buffers; 0 <= da, db < 128. */
+int bs_uni_resultant_modp(bs_ctx *ctx, int n, const uint32_t *p,
+                          const uint32_t *a, int da, int lda,
+                          const uint32_t *b, int db, int ldb, uint32_t *res);
+
+/* The first `count` table primes (2^30 < p < 2^31, p = 1 mod 2^14, decreasing). */
+int bs_prime_table(int count, uint32_t *primes);
+
+/* ---------------------------------------------------------------------------------
+ * gcd and square-free part (Sec. 5.1 "Computing gcds in Z[x]"; Sec. 2.1 BiProject)
+ * ------------------------------------------------------------------------------ */
+
+/* Monic gcd of a (degree da) and b (degree db) in Z_p[x], p prime (2 < p < 2^31),
+ * coefficients in [0, p), ascending, host buffers.  g must hold max(da, db) + 1 entries;
+ * *dg receives the gcd's degree (-1 when a = b = 0).  da or db may be -1 (zero poly). */
+int bs_gcd_modp(bs_ctx *ctx, const uint32_t *a, int da, const uint32_t *b, int db,
+                uint32_t p, uint32_t *g, int *dg);
+
+/* Square-free part R* = pp(R / gcd(R, R')) of a non-zero R in Z[x], primitive with a
+ * positive leading coefficient.  Host buffers.  out->c NULL: size query (upper bounds).
+ * Returns BS_ERR_ZERO for R = 0. */
+int bs_squarefree_part(bs_ctx *ctx, const bs_upoly *r, bs_upoly *out);
+
+/* ---------------------------------------------------------------------------------
+ * Measurement
+ * ------------------------------------------------------------------------------ */
+
+/* Throughput of one integer-multiply instruction kind on every SM of the context's
+ * device, in operations per second: kind 0 mad.lo.u32, 1 mad.hi.u32, 2 mad.wide.u32,
+ * 3 one Montgomery multiplication mod a 31-bit prime as the kernels perform it.  Runs a
+ * few short kernels on the context's stream and waits for them. */
+int bs_alu_probe(bs_ctx *ctx, int kind, double *ops_per_s);
+
+/* Turn per-stage timing on or off.  When on, resultant calls record CUDA events on the
+ * context's stream around the stages (and do not use CUDA graphs). */
+int bs_profile(bs_ctx *ctx, int enable);
+
+/* Milliseconds of the stages of the most recent resultant call, measured with CUDA
+ * events on the context's stream: ms[0] plan, ms[1] reduce + evaluate, ms[2] univariate
+ * resultants, ms[3] interpolation, ms[4] reconstruction (n entries are written, n <= 5).
+ * Waits for the call to finish.  BS_ERR_ARG if profiling is off. */
+int bs_stage_times(bs_ctx *ctx, float *ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSRES_H */

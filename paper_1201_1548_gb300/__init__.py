@@ -1,0 +1,31 @@
+"""GB300 multi-modular resultant / gcd library: Python binding of the C ABI (include/bsres.h).
+
+The binding only marshals arguments (Python integers <-> two's complement uint32 limbs)
+and calls ``libbsres.so``; every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: if the shared library has not been built, or no GPU
+is present, the calls raise.
+
+Names follow the C ABI: ``bs_resultant``, ``bs_resultant_batch``, ``bs_resultant_device``,
+``bs_uni_resultant_modp``, ``bs_gcd_modp``, ``bs_squarefree_part``, ``bs_prime_table``.
+"""
+
+from ._abi import (  # noqa: F401
+    BsError,
+    Context,
+    bipoly_to_limbs,
+    limbs_to_ints,
+    ints_to_limbs,
+    load_library,
+    library_path,
+    bs_prime_table,
+    bs_plan,
+    bs_resultant,
+    bs_resultant_batch,
+    bs_resultant_bounds,
+    bs_resultant_device,
+    bs_device_status,
+    bs_uni_resultant_modp,
+    bs_gcd_modp,
+    bs_squarefree_part,
+    EXPORTED_SYMBOLS,
+)

@@ -1,0 +1,353 @@
+"""ctypes binding of libbsres.so (argument marshalling only)."""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libbsres.so")
+_LIB = None
+
+# every symbol that include/bsres.h declares
+EXPORTED_SYMBOLS = [
+    "bs_init", "bs_free", "bs_set_stream", "bs_error_string", "bs_last_error_detail",
+    "bs_last_stats", "bs_resultant_bounds", "bs_resultant", "bs_resultant_device",
+    "bs_device_status", "bs_resultant_batch", "bs_uni_resultant_modp", "bs_prime_table",
+    "bs_gcd_modp", "bs_squarefree_part", "bs_plan", "bs_alu_probe", "bs_profile",
+    "bs_stage_times",
+]
+
+
+class BsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bsres error {code}: {msg}")
+        self.code = code
+
+
+class _Bipoly(C.Structure):
+    _fields_ = [("deg_x", C.c_int32), ("deg_y", C.c_int32), ("limbs", C.c_int32),
+                ("c", C.c_void_p)]
+
+
+class _Upoly(C.Structure):
+    _fields_ = [("deg", C.c_int32), ("limbs", C.c_int32), ("c", C.c_void_p)]
+
+
+class _PlanInfo(C.Structure):
+    _fields_ = [("trivial", C.c_int32), ("m_e", C.c_int32), ("n_e", C.c_int32),
+                ("D", C.c_int32), ("N", C.c_int32), ("k_need", C.c_int32),
+                ("k_total", C.c_int32), ("out_limbs", C.c_int32), ("log2B_q16", C.c_int64)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("jobs", C.c_int32), ("primes_needed", C.c_int64),
+                ("primes_evaluated", C.c_int64), ("primes_rejected", C.c_int64),
+                ("instances", C.c_int64), ("mulmods_alg", C.c_int64),
+                ("max_points", C.c_int32), ("max_primes", C.c_int32)]
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libbsres.so; raise if it has not been built (no fallback path exists)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_LIB_PATH):
+        raise BsError(-1, f"{_LIB_PATH} is missing: build it with "
+                          "`python -m paper_1201_1548_gb300.build`")
+    lib = C.CDLL(_LIB_PATH)
+    P = C.c_void_p
+    I = C.c_int
+    lib.bs_init.argtypes = [I, C.c_size_t, C.POINTER(P)]
+    lib.bs_free.argtypes = [P]
+    lib.bs_free.restype = None
+    lib.bs_set_stream.argtypes = [P, P]
+    lib.bs_error_string.argtypes = [I]
+    lib.bs_error_string.restype = C.c_char_p
+    lib.bs_last_error_detail.argtypes = [P]
+    lib.bs_last_error_detail.restype = C.c_char_p
+    lib.bs_last_stats.argtypes = [P, C.POINTER(_Stats)]
+    lib.bs_resultant_bounds.argtypes = [C.POINTER(_Bipoly), C.POINTER(_Bipoly), I,
+                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.bs_resultant.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, C.POINTER(_Upoly)]
+    lib.bs_resultant_device.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I,
+                                        C.POINTER(_Upoly)]
+    lib.bs_device_status.argtypes = [P]
+    lib.bs_resultant_batch.argtypes = [P, I, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I,
+                                       C.POINTER(_Upoly)]
+    lib.bs_uni_resultant_modp.argtypes = [P, I, P, P, I, I, P, I, I, P]
+    lib.bs_prime_table.argtypes = [I, P]
+    lib.bs_gcd_modp.argtypes = [P, P, I, P, I, C.c_uint32, P, C.POINTER(C.c_int)]
+    lib.bs_squarefree_part.argtypes = [P, C.POINTER(_Upoly), C.POINTER(_Upoly)]
+    lib.bs_alu_probe.argtypes = [P, I, C.POINTER(C.c_double)]
+    lib.bs_profile.argtypes = [P, I]
+    lib.bs_stage_times.argtypes = [P, P, I]
+    lib.bs_plan.argtypes = [C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, C.POINTER(_PlanInfo)]
+    for name in EXPORTED_SYMBOLS:
+        getattr(lib, name)
+    _LIB = lib
+    return lib
+
+
+# --------------------------------------------------------------------------------------
+# marshalling
+# --------------------------------------------------------------------------------------
+
+def _limbs_for(values):
+    bits = 1
+    for v in values:
+        b = (v if v >= 0 else ~v).bit_length() + 1
+        if b > bits:
+            bits = b
+    return max(1, (bits + 31) // 32)
+
+
+def ints_to_limbs(values, limbs=None):
+    """Python ints -> (n, limbs) uint32 array of two's complement little-endian limbs."""
+    values = [int(v) for v in values]
+    L = limbs or _limbs_for(values)
+    mask = (1 << (32 * L)) - 1
+    raw = b"".join((v & mask).to_bytes(4 * L, "little") for v in values)
+    arr = np.frombuffer(raw, dtype="<u4").reshape(len(values), L) if values else \
+        np.zeros((0, L), dtype=np.uint32)
+    return np.ascontiguousarray(arr, dtype=np.uint32), L
+
+
+def limbs_to_ints(arr, ncoef, limbs):
+    a = np.ascontiguousarray(np.asarray(arr, dtype=np.uint32).reshape(-1)[: ncoef * limbs])
+    b = a.tobytes()
+    w = 4 * limbs
+    return [int.from_bytes(b[i * w:(i + 1) * w], "little", signed=True) for i in range(ncoef)]
+
+
+def bipoly_to_limbs(f, limbs=None):
+    """Grid f[j][i] (coefficient of x^i y^j) -> (uint32 array (deg_y+1, deg_x+1, L), dx, dy, L)."""
+    dy = len(f) - 1
+    dx = max(len(r) for r in f) - 1
+    flat = []
+    for row in f:
+        flat.extend(row)
+        flat.extend([0] * (dx + 1 - len(row)))
+    arr, L = ints_to_limbs(flat, limbs)
+    return arr.reshape(dy + 1, dx + 1, L), dx, dy, L
+
+
+def _bip(arr, dx, dy, L):
+    return _Bipoly(dx, dy, L, arr.ctypes.data)
+
+
+class Context:
+    """A library context on one CUDA device (owns device memory and a stream)."""
+
+    def __init__(self, device=0, mem_budget=0):
+        self.lib = load_library()
+        h = C.c_void_p()
+        rc = self.lib.bs_init(int(device), int(mem_budget), C.byref(h))
+        if rc != 0:
+            raise BsError(rc, self.lib.bs_error_string(rc).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bs_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc):
+        if rc != 0:
+            detail = self.lib.bs_last_error_detail(self.h).decode()
+            raise BsError(rc, f"{self.lib.bs_error_string(rc).decode()} ({detail})")
+
+    def set_stream(self, stream_ptr):
+        self._check(self.lib.bs_set_stream(self.h, C.c_void_p(stream_ptr or None)))
+
+    def last_stats(self):
+        s = _Stats()
+        self._check(self.lib.bs_last_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    # -- resultants -----------------------------------------------------------------
+    def resultant(self, f, g, var=1):
+        """res(f, g; y) (var=1) or res(f, g; x) (var=0) as a list of Python ints."""
+        return self.resultant_batch([(f, g)], var=var, graph=False)[0]
+
+    def resultant_batch(self, pairs, var=1, graph=True):
+        n = len(pairs)
+        keep = []
+        fs = (_Bipoly * n)()
+        gs = (_Bipoly * n)()
+        for i, (f, g) in enumerate(pairs):
+            af, dxf, dyf, Lf = bipoly_to_limbs(f)
+            ag, dxg, dyg, Lg = bipoly_to_limbs(g)
+            keep += [af, ag]
+            fs[i] = _bip(af, dxf, dyf, Lf)
+            gs[i] = _bip(ag, dxg, dyg, Lg)
+        outs = (_Upoly * n)()
+        for i in range(n):
+            outs[i] = _Upoly(0, 0, None)
+        fn = self.lib.bs_resultant_batch if graph else self.lib.bs_resultant
+        if graph:
+            self._check(fn(self.h, n, fs, gs, int(var), outs))
+        else:
+            for i in range(n):
+                self._check(fn(self.h, C.byref(fs[i]), C.byref(gs[i]), int(var), C.byref(outs[i])))
+        bufs = []
+        for i in range(n):
+            deg, L = outs[i].deg, outs[i].limbs
+            buf = np.zeros((max(deg, 0) + 1) * L, dtype=np.uint32)
+            bufs.append(buf)
+            outs[i] = _Upoly(max(deg, 0), L, buf.ctypes.data)
+        if graph:
+            self._check(fn(self.h, n, fs, gs, int(var), outs))
+        else:
+            for i in range(n):
+                self._check(fn(self.h, C.byref(fs[i]), C.byref(gs[i]), int(var), C.byref(outs[i])))
+        res = []
+        for i in range(n):
+            deg, L = outs[i].deg, outs[i].limbs
+            res.append(limbs_to_ints(bufs[i], deg + 1, L) if deg >= 0 else [])
+        return res
+
+    def resultant_bounds(self, f_meta, g_meta, var=1):
+        """f_meta = (deg_x, deg_y, limbs); returns (deg_cap, limbs_cap)."""
+        fb = _Bipoly(f_meta[0], f_meta[1], f_meta[2], None)
+        gb = _Bipoly(g_meta[0], g_meta[1], g_meta[2], None)
+        d = C.c_int32()
+        L = C.c_int32()
+        rc = self.lib.bs_resultant_bounds(C.byref(fb), C.byref(gb), int(var), C.byref(d), C.byref(L))
+        self._check(rc)
+        return d.value, L.value
+
+    def resultant_device(self, f_ptr, f_meta, g_ptr, g_meta, out_ptr, out_cap, var=1):
+        """Device-resident call: pointers are device addresses (ints); metas are
+        (deg_x, deg_y, limbs); out_cap = (deg_cap, limbs_cap).  Asynchronous."""
+        fb = _Bipoly(f_meta[0], f_meta[1], f_meta[2], f_ptr)
+        gb = _Bipoly(g_meta[0], g_meta[1], g_meta[2], g_ptr)
+        ob = _Upoly(out_cap[0], out_cap[1], out_ptr)
+        self._check(self.lib.bs_resultant_device(self.h, C.byref(fb), C.byref(gb), int(var),
+                                                 C.byref(ob)))
+
+    def alu_probe(self, kind):
+        v = C.c_double()
+        self._check(self.lib.bs_alu_probe(self.h, int(kind), C.byref(v)))
+        return v.value
+
+    def profile(self, enable=True):
+        self._check(self.lib.bs_profile(self.h, 1 if enable else 0))
+
+    def stage_times(self):
+        ms = np.zeros(5, dtype=np.float32)
+        self._check(self.lib.bs_stage_times(self.h, ms.ctypes.data, 5))
+        return [float(x) for x in ms]
+
+    def device_status(self):
+        self._check(self.lib.bs_device_status(self.h))
+
+    # -- univariate -----------------------------------------------------------------
+    def uni_resultant_modp(self, primes, a, b):
+        """Resultants mod p of equal-shape univariate images: a[i], b[i] ascending lists."""
+        n = len(primes)
+        da = len(a[0]) - 1
+        db = len(b[0]) - 1
+        A = np.ascontiguousarray(np.array(a, dtype=np.uint32).reshape(n, da + 1))
+        B = np.ascontiguousarray(np.array(b, dtype=np.uint32).reshape(n, db + 1))
+        Pm = np.ascontiguousarray(np.array(primes, dtype=np.uint32))
+        R = np.zeros(n, dtype=np.uint32)
+        self._check(self.lib.bs_uni_resultant_modp(self.h, n, Pm.ctypes.data, A.ctypes.data, da,
+                                                   da + 1, B.ctypes.data, db, db + 1,
+                                                   R.ctypes.data))
+        return [int(x) for x in R]
+
+    def gcd_modp(self, a, b, p):
+        """Monic gcd in Z_p[x] of ascending coefficient lists (values in [0, p))."""
+        da, db = len(a) - 1, len(b) - 1
+        A = np.ascontiguousarray(np.array(a if a else [0], dtype=np.uint32))
+        B = np.ascontiguousarray(np.array(b if b else [0], dtype=np.uint32))
+        G = np.zeros(max(da, db, 0) + 1, dtype=np.uint32)
+        dg = C.c_int()
+        self._check(self.lib.bs_gcd_modp(self.h, A.ctypes.data, da, B.ctypes.data, db,
+                                         C.c_uint32(p), G.ctypes.data, C.byref(dg)))
+        return [int(x) for x in G[: dg.value + 1]]
+
+    def squarefree_part(self, r):
+        arr, L = ints_to_limbs(r)
+        inp = _Upoly(len(r) - 1, L, arr.ctypes.data)
+        out = _Upoly(0, 0, None)
+        self._check(self.lib.bs_squarefree_part(self.h, C.byref(inp), C.byref(out)))
+        buf = np.zeros((max(out.deg, 0) + 1) * out.limbs, dtype=np.uint32)
+        out = _Upoly(out.deg, out.limbs, buf.ctypes.data)
+        self._check(self.lib.bs_squarefree_part(self.h, C.byref(inp), C.byref(out)))
+        return limbs_to_ints(buf, out.deg + 1, out.limbs) if out.deg >= 0 else []
+
+
+# module-level functions with the C names -------------------------------------------
+
+def bs_prime_table(count):
+    lib = load_library()
+    out = np.zeros(count, dtype=np.uint32)
+    rc = lib.bs_prime_table(int(count), out.ctypes.data)
+    if rc:
+        raise BsError(rc, lib.bs_error_string(rc).decode())
+    return [int(x) for x in out]
+
+
+def bs_plan(f, g, var=1):
+    """Host-only plan of res(f, g; var) as a dict (no GPU needed)."""
+    lib = load_library()
+    af, dxf, dyf, Lf = bipoly_to_limbs(f)
+    ag, dxg, dyg, Lg = bipoly_to_limbs(g)
+    fb, gb = _bip(af, dxf, dyf, Lf), _bip(ag, dxg, dyg, Lg)
+    info = _PlanInfo()
+    rc = lib.bs_plan(C.byref(fb), C.byref(gb), int(var), C.byref(info))
+    if rc:
+        raise BsError(rc, lib.bs_error_string(rc).decode())
+    return {k: getattr(info, k) for k, _ in _PlanInfo._fields_}
+
+
+def bs_resultant(ctx, f, g, var=1):
+    return ctx.resultant(f, g, var)
+
+
+def bs_resultant_batch(ctx, pairs, var=1):
+    return ctx.resultant_batch(pairs, var)
+
+
+def bs_resultant_bounds(ctx, f_meta, g_meta, var=1):
+    return ctx.resultant_bounds(f_meta, g_meta, var)
+
+
+def bs_resultant_device(ctx, *args, **kw):
+    return ctx.resultant_device(*args, **kw)
+
+
+def bs_device_status(ctx):
+    return ctx.device_status()
+
+
+def bs_uni_resultant_modp(ctx, primes, a, b):
+    return ctx.uni_resultant_modp(primes, a, b)
+
+
+def bs_gcd_modp(ctx, a, b, p):
+    return ctx.gcd_modp(a, b, p)
+
+
+def bs_squarefree_part(ctx, r):
+    return ctx.squarefree_part(r)

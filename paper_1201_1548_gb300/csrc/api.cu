@@ -1,0 +1,658 @@
+// C ABI of libbsres: context, workspace management and the resultant entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bsres.h"
+#include "common.cuh"
+#include "ctx.cuh"
+#include "resultant_kernels.cuh"
+#include "tables.cuh"
+
+using namespace bs;
+
+// ------------------------------------------------------------------------------------
+// context
+// ------------------------------------------------------------------------------------
+int ctx_fail(bs_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int ctx_cuda(bs_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return 0;
+  return ctx_fail(ctx, BS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int ensure_workspace(bs_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_cap) return 0;
+  if (bytes > ctx->budget) return ctx_fail(ctx, BS_ERR_NOMEM, "workspace exceeds the memory budget");
+  if (ctx->ws) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_cap = 0;
+  }
+  size_t cap = std::min(ctx->budget, bytes + bytes / 4);
+  if (cudaMalloc(&ctx->ws, cap) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return ctx_fail(ctx, BS_ERR_NOMEM, "cudaMalloc of the workspace failed");
+  }
+  ctx->ws_cap = cap;
+  ++ctx->ws_generation;
+  return 0;
+}
+
+int ensure_pinned(bs_ctx* ctx, size_t up, size_t down) {
+  if (up > ctx->h_up_cap) {
+    if (ctx->h_up) cudaFreeHost(ctx->h_up);
+    ctx->h_up_cap = up + up / 4 + 4096;
+    if (cudaMallocHost(&ctx->h_up, ctx->h_up_cap) != cudaSuccess) {
+      ctx->h_up = nullptr;
+      ctx->h_up_cap = 0;
+      return ctx_fail(ctx, BS_ERR_NOMEM, "pinned host allocation failed");
+    }
+  }
+  if (down > ctx->h_down_cap) {
+    if (ctx->h_down) cudaFreeHost(ctx->h_down);
+    ctx->h_down_cap = down + down / 4 + 4096;
+    if (cudaMallocHost(&ctx->h_down, ctx->h_down_cap) != cudaSuccess) {
+      ctx->h_down = nullptr;
+      ctx->h_down_cap = 0;
+      return ctx_fail(ctx, BS_ERR_NOMEM, "pinned host allocation failed");
+    }
+  }
+  return 0;
+}
+
+extern "C" int bs_init(int device, size_t mem_budget, bs_ctx** out) {
+  if (!out) return BS_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return BS_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return BS_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return BS_ERR_CUDA;
+  bs_ctx* ctx = new bs_ctx();
+  ctx->device = device;
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, device);
+  ctx->sms = prop.multiProcessorCount;
+  ctx->smem_optin = (int)prop.sharedMemPerBlockOptin;
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  ctx->budget = mem_budget ? mem_budget : (size_t)(freeb * 0.9);
+  if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete ctx;
+    return BS_ERR_CUDA;
+  }
+  ctx->stream = ctx->own_stream;
+  int rc = ctx->tabs.init(ctx->stream);
+  if (rc) {
+    bs_free(ctx);
+    return rc;
+  }
+  if (cudaMalloc(&ctx->d_status, sizeof(int32_t) * 4) != cudaSuccess) {
+    bs_free(ctx);
+    return BS_ERR_CUDA;
+  }
+  cudaMemset(ctx->d_status, 0, sizeof(int32_t) * 4);
+  for (int c = 0; c < kNumUniClasses; ++c) ctx->occ[c] = uni_occupancy(c);
+  set_stage_smem_limits(ctx->smem_optin);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    bs_free(ctx);
+    return BS_ERR_CUDA;
+  }
+  *out = ctx;
+  return BS_OK;
+}
+
+extern "C" void bs_free(bs_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
+  if (ctx->stream && ctx->stream != ctx->own_stream) cudaStreamSynchronize(ctx->stream);
+  ctx->tabs.release();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->dev_ws) cudaFree(ctx->dev_ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_up) cudaFreeHost(ctx->h_up);
+  if (ctx->h_down) cudaFreeHost(ctx->h_down);
+  ctx_release_extra(ctx);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+}
+
+extern "C" int bs_set_stream(bs_ctx* ctx, void* stream) {
+  if (!ctx) return BS_ERR_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  return BS_OK;
+}
+
+extern "C" const char* bs_error_string(int status) {
+  switch (status) {
+    case BS_OK: return "ok";
+    case BS_ERR_ARG: return "invalid argument";
+    case BS_ERR_NOMEM: return "device memory budget exceeded";
+    case BS_ERR_UNLUCKY: return "too many unlucky primes";
+    case BS_ERR_TIMEOUT: return "bounded device wait expired";
+    case BS_ERR_CUDA: return "CUDA runtime error";
+    case BS_ERR_ZERO: return "square-free part of the zero polynomial";
+    case BS_ERR_RANGE: return "problem exceeds the prime table or transform size";
+    case BS_ERR_INTERNAL: return "device-side consistency check failed";
+    case BS_ERR_CAPACITY: return "output capacity too small";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* bs_last_error_detail(const bs_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "no context";
+}
+
+extern "C" int bs_last_stats(const bs_ctx* ctx, bs_stats* out) {
+  if (!ctx || !out) return BS_ERR_ARG;
+  *out = ctx->stats;
+  return BS_OK;
+}
+
+extern "C" int bs_prime_table(int count, uint32_t* primes) {
+  const HostPrimes& H = host_primes();
+  if (count < 0 || count > (int)H.p.size() || (!primes && count)) return BS_ERR_ARG;
+  for (int i = 0; i < count; ++i) primes[i] = H.p[i];
+  return BS_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// shared helpers
+// ------------------------------------------------------------------------------------
+static int check_bipoly(bs_ctx* ctx, const bs_bipoly* p, const char* name) {
+  if (!p) return ctx_fail(ctx, BS_ERR_ARG, std::string(name) + " is null");
+  if (p->deg_x < 0 || p->deg_y < 0 || p->limbs < 1 || p->limbs > kMaxLimbs || !p->c)
+    return ctx_fail(ctx, BS_ERR_ARG, std::string(name) + ": bad extents, limbs or pointer");
+  return 0;
+}
+
+static Grid grid_of(const bs_bipoly* p) { return Grid{p->c, p->deg_x, p->deg_y, p->limbs}; }
+
+// upper bounds from extents and limb counts only
+static int meta_bounds(const bs_bipoly* f, const bs_bipoly* g, int var, MetaBounds* mb) {
+  const int fe = var ? f->deg_y : f->deg_x, fo = var ? f->deg_x : f->deg_y;
+  const int ge = var ? g->deg_y : g->deg_x, go = var ? g->deg_x : g->deg_y;
+  const int64_t d1 = (int64_t)(f->deg_x + f->deg_y) * (g->deg_x + g->deg_y);
+  const int64_t d2 = (int64_t)ge * fo + (int64_t)fe * go;
+  int64_t D = std::min(d1, d2);
+  if (D < 0) D = 0;
+  mb->D = (int32_t)D;
+  if (D + 1 > kNMax) return BS_ERR_RANGE;
+  int logN = 0;
+  while ((1ll << logN) < D + 1) ++logN;
+  mb->logN = logN;
+  mb->rows = (fe + 1) + (ge + 1);
+  mb->len = std::max(fe, ge) + 1;
+  // coefficient magnitudes below 2^(32 L - 1)
+  auto Sbound = [&](int rows, int cols, int L) {
+    UF c = uf_make(1, 32 * L - 1, false);
+    UF l1 = uf_mul(uf_make((uint64_t)cols, 0, false), c);
+    return uf_mul(uf_make((uint64_t)rows, 0, false), uf_mul(l1, l1));
+  };
+  const UF Sf = Sbound(fe + 1, fo + 1, f->limbs);
+  const UF Sg = Sbound(ge + 1, go + 1, g->limbs);
+  const HostPrimes& H = host_primes();
+  Plan P = finish_plan(Sf, fe, f->deg_x + f->deg_y, fo, 32 * f->limbs, Sg, ge, g->deg_x + g->deg_y,
+                       go, 32 * g->limbs, H.lg_prefix.data(), (int)H.p.size());
+  if (P.status) return P.status;
+  mb->k_total = std::max(P.k_total, 1);
+  mb->k_need = std::max(P.k_need, 1);
+  mb->out_limbs = P.out_limbs;
+  return 0;
+}
+
+extern "C" int bs_plan(const bs_bipoly* f, const bs_bipoly* g, int var, bs_plan_info* out) {
+  if (!out || (var != 0 && var != 1)) return BS_ERR_ARG;
+  if (check_bipoly(nullptr, f, "f") || check_bipoly(nullptr, g, "g")) return BS_ERR_ARG;
+  const HostPrimes& H = host_primes();
+  const Plan P = plan_host(grid_of(f), grid_of(g), var, H.lg_prefix.data(), (int)H.p.size());
+  out->trivial = P.trivial;
+  out->m_e = P.me;
+  out->n_e = P.ne;
+  out->D = P.trivial == 1 ? -1 : P.D;
+  out->N = P.N;
+  out->k_need = P.k_need;
+  out->k_total = P.k_total;
+  out->out_limbs = P.out_limbs;
+  out->log2B_q16 = P.log2B_q16;
+  return P.status;
+}
+
+extern "C" int bs_resultant_bounds(const bs_bipoly* f, const bs_bipoly* g, int var,
+                                   int32_t* deg_cap, int32_t* limbs_cap) {
+  if (!f || !g || !deg_cap || !limbs_cap || (var != 0 && var != 1)) return BS_ERR_ARG;
+  if (f->deg_x < 0 || f->deg_y < 0 || g->deg_x < 0 || g->deg_y < 0 || f->limbs < 1 ||
+      g->limbs < 1 || f->limbs > kMaxLimbs || g->limbs > kMaxLimbs)
+    return BS_ERR_ARG;
+  MetaBounds mb;
+  int rc = meta_bounds(f, g, var, &mb);
+  if (rc) return rc;
+  *deg_cap = mb.D;
+  *limbs_cap = mb.out_limbs;
+  return BS_OK;
+}
+
+// copy one result coefficient block (rows of src_limbs two's complement limbs) into a
+// caller buffer of dst_limbs, checking that each value fits
+static bool copy_coeffs(const uint32_t* src, int src_limbs, int ncoef, uint32_t* dst, int dst_limbs) {
+  for (int i = 0; i < ncoef; ++i) {
+    const uint32_t* s = src + (size_t)i * src_limbs;
+    uint32_t* d = dst + (size_t)i * dst_limbs;
+    const uint32_t ext = (s[src_limbs - 1] >> 31) ? 0xffffffffu : 0u;
+    for (int l = 0; l < dst_limbs; ++l) d[l] = l < src_limbs ? s[l] : ext;
+    // the dropped limbs must be pure sign extension of the kept ones
+    const uint32_t kept_ext = (d[dst_limbs - 1] >> 31) ? 0xffffffffu : 0u;
+    for (int l = dst_limbs; l < src_limbs; ++l)
+      if (s[l] != kept_ext) return false;
+  }
+  return true;
+}
+
+static bool coeff_is_zero(const uint32_t* s, int limbs) {
+  for (int l = 0; l < limbs; ++l)
+    if (s[l]) return false;
+  return true;
+}
+
+// ------------------------------------------------------------------------------------
+// batch of host-resident jobs (also serves bs_resultant with n = 1)
+// ------------------------------------------------------------------------------------
+int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int var,
+                   bs_upoly* out, bool use_graph) {
+  if (!ctx || n < 0 || !out || (n && (!f || !g)) || (var != 0 && var != 1))
+    return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
+  if (n == 0) return BS_OK;
+  cudaSetDevice(ctx->device);
+  const HostPrimes& H = host_primes();
+  const int T = (int)H.p.size();
+  std::vector<Plan> plans(n);
+  bool query = false;
+  for (int i = 0; i < n; ++i) {
+    int rc = check_bipoly(ctx, f + i, "f");
+    if (rc) return rc;
+    rc = check_bipoly(ctx, g + i, "g");
+    if (rc) return rc;
+    plans[i] = plan_host(grid_of(f + i), grid_of(g + i), var, H.lg_prefix.data(), T);
+    if (plans[i].status)
+      return ctx_fail(ctx, plans[i].status, "planning failed for job " + std::to_string(i));
+    if (!out[i].c) query = true;
+  }
+  if (query) {
+    for (int i = 0; i < n; ++i) {
+      const Plan& P = plans[i];
+      out[i].deg = P.trivial == 1 ? -1 : P.D;
+      out[i].limbs = P.out_limbs;
+    }
+    return BS_OK;
+  }
+  for (int i = 0; i < n; ++i)
+    if (out[i].limbs < 1 || out[i].deg < -1)
+      return ctx_fail(ctx, BS_ERR_ARG, "bad output capacity");
+  // tables
+  int needT = 1, needLog = 0, kmax = 1, lmax = 1, maxN = 1, class_mask = 0;
+  for (const Plan& P : plans) {
+    if (P.trivial) continue;
+    needT = std::max(needT, P.k_total);
+    needLog = std::max(needLog, P.logN);
+    kmax = std::max(kmax, P.k_need);
+    lmax = std::max(lmax, P.out_limbs);
+    maxN = std::max(maxN, P.N);
+    const int c = uni_class_of(std::max(P.me, P.ne) + 1);
+    if (c < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
+    class_mask |= 1 << c;
+  }
+  int rc = ctx->tabs.ensure(needT, needLog, ctx->stream);
+  if (rc) return ctx_fail(ctx, rc, "table setup failed");
+  // ---- layout: [upload | compute | download]
+  std::vector<int64_t> in_f(n), in_g(n);  // limb counts
+  size_t in_words = 0;
+  for (int i = 0; i < n; ++i) {
+    in_f[i] = (int64_t)(f[i].deg_y + 1) * (f[i].deg_x + 1) * f[i].limbs;
+    in_g[i] = (int64_t)(g[i].deg_y + 1) * (g[i].deg_x + 1) * g[i].limbs;
+    in_words += in_f[i] + in_g[i];
+  }
+  int cls_count[kNumUniClasses] = {0};
+  for (int i = 0; i < n; ++i)
+    if (!plans[i].trivial) ++cls_count[uni_class_of(std::max(plans[i].me, plans[i].ne) + 1)];
+  size_t pstat_words = 0;
+  for (const Plan& P : plans)
+    if (!P.trivial) pstat_words += P.k_total;
+  Layout up;
+  const size_t o_jobs = up.take(sizeof(Job) * n);
+  const size_t o_eoff = up.take(sizeof(int64_t) * (n + 1));
+  const size_t o_ioff = up.take(sizeof(int64_t) * (n + 1));
+  const size_t o_coff = up.take(sizeof(int64_t) * (n + 1));
+  size_t o_cids[kNumUniClasses], o_coffs[kNumUniClasses];
+  for (int c = 0; c < kNumUniClasses; ++c) {
+    o_cids[c] = up.take(sizeof(int32_t) * std::max(cls_count[c], 1));
+    o_coffs[c] = up.take(sizeof(int64_t) * (cls_count[c] + 1));
+  }
+  const size_t o_status = up.take(sizeof(int32_t) * 4);
+  const size_t o_pstat = up.take(sizeof(int32_t) * std::max<size_t>(pstat_words, 1));
+  const size_t o_in = up.take(sizeof(uint32_t) * std::max<size_t>(in_words, 1));
+  const size_t up_bytes = up.used;
+  Layout cmp;
+  cmp.used = up_bytes;
+  std::vector<size_t> o_ev(n), o_vals(n), o_rmod(n), o_sel(n);
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = plans[i];
+    if (P.trivial) continue;
+    const int rows = (P.me + 1) + (P.ne + 1);
+    o_ev[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_total * rows * P.N);
+    o_vals[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_total * P.N);
+    o_rmod[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_need * (P.D + 1));
+    o_sel[i] = cmp.take(sizeof(int32_t) * P.k_need);
+  }
+  Layout dn;
+  dn.used = cmp.used;
+  const size_t dn_start = dn.take(0);
+  std::vector<size_t> o_out(n);
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = plans[i];
+    const int cap_deg = std::max(P.D, 0);
+    o_out[i] = dn.take(sizeof(uint32_t) * (size_t)(cap_deg + 1) * P.out_limbs);
+  }
+  const size_t o_status_dn = dn.take(sizeof(int32_t) * 4);
+  const size_t total = dn.used;
+  const size_t dn_bytes = total - dn_start;
+  rc = ensure_workspace(ctx, total);
+  if (rc) return rc;
+  rc = ensure_pinned(ctx, up_bytes, dn_bytes);
+  if (rc) return rc;
+  char* base = (char*)ctx->ws;
+  char* hu = (char*)ctx->h_up;
+  std::memset(hu, 0, up_bytes);
+  // staged inputs
+  {
+    uint32_t* dst = (uint32_t*)(hu + o_in);
+    for (int i = 0; i < n; ++i) {
+      std::memcpy(dst, f[i].c, sizeof(uint32_t) * in_f[i]);
+      dst += in_f[i];
+      std::memcpy(dst, g[i].c, sizeof(uint32_t) * in_g[i]);
+      dst += in_g[i];
+    }
+  }
+  Job* hj = (Job*)(hu + o_jobs);
+  int64_t* eoff = (int64_t*)(hu + o_eoff);
+  int64_t* ioff = (int64_t*)(hu + o_ioff);
+  int64_t* coff = (int64_t*)(hu + o_coff);
+  int32_t* cids[kNumUniClasses];
+  int64_t* coffs[kNumUniClasses];
+  int cfill[kNumUniClasses] = {0};
+  for (int c = 0; c < kNumUniClasses; ++c) {
+    cids[c] = (int32_t*)(hu + o_cids[c]);
+    coffs[c] = (int64_t*)(hu + o_coffs[c]);
+    coffs[c][0] = 0;
+  }
+  eoff[0] = ioff[0] = coff[0] = 0;
+  size_t in_pos = 0, ps_pos = 0;
+  int64_t instances = 0, mulmods = 0, k_need_sum = 0, k_total_sum = 0;
+  int maxpts = 0, maxprimes = 0;
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = plans[i];
+    Job J;
+    std::memset(&J, 0, sizeof(J));
+    J.f = Grid{(const uint32_t*)(base + o_in) + in_pos, f[i].deg_x, f[i].deg_y, f[i].limbs};
+    in_pos += in_f[i];
+    J.g = Grid{(const uint32_t*)(base + o_in) + in_pos, g[i].deg_x, g[i].deg_y, g[i].limbs};
+    in_pos += in_g[i];
+    J.var = var;
+    J.plan = P;
+    J.cap_deg = std::max(P.D, 0);
+    J.cap_limbs = P.out_limbs;
+    J.out = (uint32_t*)(base + o_out[i]);
+    J.status = (int32_t*)(base + o_status);
+    J.rejected = (int32_t*)(base + o_status) + 1;
+    int64_t ne = 0, ni = 0, nu = 0;
+    if (!P.trivial) {
+      J.rows = (P.me + 1) + (P.ne + 1);
+      J.ev = (uint32_t*)(base + o_ev[i]);
+      J.vals = (uint32_t*)(base + o_vals[i]);
+      J.rmod = (uint32_t*)(base + o_rmod[i]);
+      J.sel = (int32_t*)(base + o_sel[i]);
+      J.pstat = (int32_t*)(base + o_pstat) + ps_pos;
+      ps_pos += P.k_total;
+      ne = (int64_t)P.k_total * J.rows;
+      ni = P.k_total;
+      nu = (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile;
+      const int c = uni_class_of(std::max(P.me, P.ne) + 1);
+      cids[c][cfill[c]] = i;
+      coffs[c][cfill[c] + 1] = coffs[c][cfill[c]] + nu;
+      ++cfill[c];
+      instances += (int64_t)P.k_total << P.logN;
+      mulmods += ((int64_t)P.k_total << P.logN) * (int64_t)P.me * P.ne;
+      k_need_sum += P.k_need;
+      k_total_sum += P.k_total;
+      maxpts = std::max(maxpts, P.N);
+      maxprimes = std::max(maxprimes, P.k_total);
+    }
+    hj[i] = J;
+    eoff[i + 1] = eoff[i] + ne;
+    ioff[i + 1] = ioff[i] + ni;
+    coff[i + 1] = coff[i] + J.cap_deg + 1;
+  }
+  cudaStream_t s = ctx->stream;
+  rc = ctx_cuda(ctx, cudaMemcpyAsync(base, hu, up_bytes, cudaMemcpyHostToDevice, s), "upload");
+  if (rc) return rc;
+  // ---- device stages
+  const Tables Tv = ctx->tabs.view();
+  const Job* dj = (const Job*)(base + o_jobs);
+  StageLaunch L;
+  L.jobs = dj;
+  L.eval = WorkList{nullptr, (const int64_t*)(base + o_eoff), n};
+  L.intt = WorkList{nullptr, (const int64_t*)(base + o_ioff), n};
+  L.crt = WorkList{nullptr, (const int64_t*)(base + o_coff), n};
+  for (int c = 0; c < kNumUniClasses; ++c) {
+    L.uni[c] = WorkList{(const int32_t*)(base + o_cids[c]), (const int64_t*)(base + o_coffs[c]),
+                        cls_count[c]};
+    L.uni_items[c] = cls_count[c] ? coffs[c][cls_count[c]] : 0;
+  }
+  L.eval_items = eoff[n];
+  L.intt_items = ioff[n];
+  L.crt_items = coff[n];
+  L.maxN = maxN;
+  L.kmax = kmax;
+  L.lmax = lmax;
+  rc = launch_stages(ctx, L, Tv, use_graph);
+  if (rc) return rc;
+  rc = ctx_cuda(ctx, cudaMemcpyAsync(base + o_status_dn, base + o_status, sizeof(int32_t) * 4,
+                                     cudaMemcpyDeviceToDevice, s),
+                "status copy");
+  if (rc) return rc;
+  rc = ctx_cuda(ctx, cudaMemcpyAsync(ctx->h_down, base + dn_start, dn_bytes, cudaMemcpyDeviceToHost, s),
+                "download");
+  if (rc) return rc;
+  rc = ctx_cuda(ctx, cudaStreamSynchronize(s), "stream");
+  if (rc) return rc;
+  const char* hd = (const char*)ctx->h_down;
+  const int32_t* st = (const int32_t*)(hd + (o_status_dn - dn_start));
+  ctx->stats = bs_stats{};
+  ctx->stats.jobs = n;
+  ctx->stats.primes_needed = k_need_sum;
+  ctx->stats.primes_evaluated = k_total_sum;
+  ctx->stats.primes_rejected = st[1];
+  ctx->stats.instances = instances;
+  ctx->stats.mulmods_alg = mulmods;
+  ctx->stats.max_points = maxpts;
+  ctx->stats.max_primes = maxprimes;
+  if (st[0]) return ctx_fail(ctx, st[0], "device stage reported a failure");
+  // ---- format outputs
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = plans[i];
+    const uint32_t* src = (const uint32_t*)(hd + (o_out[i] - dn_start));
+    const int ncoef = std::max(P.D, 0) + 1;
+    int deg = -1;
+    for (int c = ncoef - 1; c >= 0; --c)
+      if (!coeff_is_zero(src + (size_t)c * P.out_limbs, P.out_limbs)) {
+        deg = c;
+        break;
+      }
+    if (deg > out[i].deg) return ctx_fail(ctx, BS_ERR_CAPACITY, "output degree capacity too small");
+    const int cap = out[i].deg;
+    if (deg >= 0 && !copy_coeffs(src, P.out_limbs, deg + 1, out[i].c, out[i].limbs))
+      return ctx_fail(ctx, BS_ERR_CAPACITY, "output limb capacity too small");
+    for (int c = deg + 1; c <= cap; ++c)
+      std::memset(out[i].c + (size_t)c * out[i].limbs, 0, sizeof(uint32_t) * out[i].limbs);
+    out[i].deg = deg;
+  }
+  return BS_OK;
+}
+
+extern "C" int bs_resultant(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var,
+                            bs_upoly* out) {
+  if (!ctx) return BS_ERR_ARG;
+  return run_host_batch(ctx, 1, f, g, var, out, false);
+}
+
+extern "C" int bs_resultant_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g,
+                                  int var, bs_upoly* out) {
+  if (!ctx) return BS_ERR_ARG;
+  return run_host_batch(ctx, n, f, g, var, out, true);
+}
+
+// ------------------------------------------------------------------------------------
+// device-resident single job
+// ------------------------------------------------------------------------------------
+extern "C" int bs_resultant_device(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var,
+                                   bs_upoly* out) {
+  if (!ctx) return BS_ERR_ARG;
+  if (!out || !out->c || (var != 0 && var != 1)) return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
+  int rc = check_bipoly(ctx, f, "f");
+  if (rc) return rc;
+  rc = check_bipoly(ctx, g, "g");
+  if (rc) return rc;
+  cudaSetDevice(ctx->device);
+  MetaBounds mb;
+  rc = meta_bounds(f, g, var, &mb);
+  if (rc) return ctx_fail(ctx, rc, "problem exceeds the supported range");
+  if (out->deg < mb.D || out->limbs < mb.out_limbs)
+    return ctx_fail(ctx, BS_ERR_CAPACITY, "output capacity below bs_resultant_bounds()");
+  const int cls = uni_class_of(mb.len);
+  if (cls < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
+  rc = ctx->tabs.ensure(mb.k_total, mb.logN, ctx->stream);
+  if (rc) return ctx_fail(ctx, rc, "table setup failed");
+  const int N = 1 << mb.logN;
+  Layout lay;
+  const size_t o_job = lay.take(sizeof(Job));
+  const size_t o_offs = lay.take(sizeof(int64_t) * 8);
+  const size_t o_pstat = lay.take(sizeof(int32_t) * mb.k_total);
+  const size_t o_ev = lay.take(sizeof(uint32_t) * (size_t)mb.k_total * mb.rows * N);
+  const size_t o_vals = lay.take(sizeof(uint32_t) * (size_t)mb.k_total * N);
+  const size_t o_rmod = lay.take(sizeof(uint32_t) * (size_t)mb.k_need * (mb.D + 1));
+  const size_t o_sel = lay.take(sizeof(int32_t) * mb.k_need);
+  if (lay.used > ctx->dev_ws_cap) {
+    if (lay.used > ctx->budget) return ctx_fail(ctx, BS_ERR_NOMEM, "workspace exceeds the memory budget");
+    if (ctx->dev_ws) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->dev_ws);
+    }
+    ctx->dev_ws = nullptr;
+    ctx->dev_ws_cap = 0;
+    if (cudaMalloc(&ctx->dev_ws, lay.used) != cudaSuccess) {
+      cudaGetLastError();
+      return ctx_fail(ctx, BS_ERR_NOMEM, "cudaMalloc of the workspace failed");
+    }
+    ctx->dev_ws_cap = lay.used;
+  }
+  char* base = (char*)ctx->dev_ws;
+  Job J;
+  std::memset(&J, 0, sizeof(J));
+  J.f = grid_of(f);
+  J.g = grid_of(g);
+  J.var = var;
+  J.ev = (uint32_t*)(base + o_ev);
+  J.vals = (uint32_t*)(base + o_vals);
+  J.rmod = (uint32_t*)(base + o_rmod);
+  J.pstat = (int32_t*)(base + o_pstat);
+  J.sel = (int32_t*)(base + o_sel);
+  J.out = out->c;
+  J.cap_deg = out->deg;
+  J.cap_limbs = out->limbs;
+  J.status = ctx->d_status;
+  J.rejected = ctx->d_status + 1;
+  cudaStream_t s = ctx->stream;
+  // the job descriptor travels as a kernel argument into device memory (no host copy
+  // in flight that could be overwritten by the next call)
+  rc = launch_device_job(ctx, J, (Job*)(base + o_job), (int64_t*)(base + o_offs), mb, cls);
+  if (rc) return rc;
+  ctx->stats = bs_stats{};
+  ctx->stats.jobs = 1;
+  (void)s;
+  return BS_OK;
+}
+
+extern "C" int bs_device_status(bs_ctx* ctx) {
+  if (!ctx) return BS_ERR_ARG;
+  int32_t st[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return ctx_fail(ctx, BS_ERR_CUDA, "status read failed");
+  cudaMemsetAsync(ctx->d_status, 0, sizeof(st), ctx->stream);
+  ctx->stats.primes_rejected = st[1];
+  if (st[0]) return ctx_fail(ctx, st[0], "device stage reported a failure");
+  return BS_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// univariate resultants of given images
+// ------------------------------------------------------------------------------------
+extern "C" int bs_uni_resultant_modp(bs_ctx* ctx, int n, const uint32_t* p, const uint32_t* a,
+                                     int da, int lda, const uint32_t* b, int db, int ldb,
+                                     uint32_t* res) {
+  if (!ctx) return BS_ERR_ARG;
+  if (n < 0 || da < 0 || db < 0 || lda < da + 1 || ldb < db + 1 || (n && (!p || !a || !b || !res)))
+    return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
+  if (n == 0) return BS_OK;
+  const int cls = uni_class_of(std::max(da, db) + 1);
+  if (cls < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree above 64");
+  cudaSetDevice(ctx->device);
+  const HostPrimes& H = host_primes();
+  std::vector<int32_t> idx(n);
+  for (int i = 0; i < n; ++i) {
+    // the table is decreasing: binary search
+    auto it = std::lower_bound(H.p.begin(), H.p.end(), p[i], std::greater<uint32_t>());
+    if (it == H.p.end() || *it != p[i]) return ctx_fail(ctx, BS_ERR_ARG, "not a table prime");
+    idx[i] = (int32_t)(it - H.p.begin());
+    for (int j = 0; j <= da; ++j)
+      if (a[(size_t)i * lda + j] >= p[i]) return ctx_fail(ctx, BS_ERR_ARG, "input not reduced");
+    for (int j = 0; j <= db; ++j)
+      if (b[(size_t)i * ldb + j] >= p[i]) return ctx_fail(ctx, BS_ERR_ARG, "input not reduced");
+  }
+  Layout lay;
+  const size_t o_idx = lay.take(sizeof(int32_t) * n);
+  const size_t o_a = lay.take(sizeof(uint32_t) * (size_t)n * lda);
+  const size_t o_b = lay.take(sizeof(uint32_t) * (size_t)n * ldb);
+  const size_t o_r = lay.take(sizeof(uint32_t) * n);
+  int rc = ensure_workspace(ctx, lay.used);
+  if (rc) return rc;
+  char* base = (char*)ctx->ws;
+  cudaStream_t s = ctx->stream;
+  rc |= ctx_cuda(ctx, cudaMemcpyAsync(base + o_idx, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "h2d");
+  rc |= ctx_cuda(ctx, cudaMemcpyAsync(base + o_a, a, sizeof(uint32_t) * (size_t)n * lda, cudaMemcpyHostToDevice, s), "h2d");
+  rc |= ctx_cuda(ctx, cudaMemcpyAsync(base + o_b, b, sizeof(uint32_t) * (size_t)n * ldb, cudaMemcpyHostToDevice, s), "h2d");
+  if (rc) return rc;
+  const Tables Tv = ctx->tabs.view();
+  launch_uni_direct(cls, n, s, (const int32_t*)(base + o_idx), (const uint32_t*)(base + o_a), da, lda,
+                    (const uint32_t*)(base + o_b), db, ldb, (uint32_t*)(base + o_r), Tv);
+  uint32_t* dR = (uint32_t*)(base + o_r);
+  rc = ctx_cuda(ctx, cudaGetLastError(), "launch");
+  if (rc) return rc;
+  rc = ctx_cuda(ctx, cudaMemcpyAsync(res, dR, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s), "d2h");
+  if (rc) return rc;
+  return ctx_cuda(ctx, cudaStreamSynchronize(s), "stream");
+}

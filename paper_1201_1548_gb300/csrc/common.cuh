@@ -1,0 +1,93 @@
+// Device-side data structures shared by the resultant kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "modarith.cuh"
+#include "plan.cuh"
+
+namespace bs {
+
+enum Status : int32_t {
+  kOk = 0,
+  kErrArg = 1,
+  kErrNoMem = 2,
+  kErrUnlucky = 3,
+  kErrTimeout = 4,
+  kErrCuda = 5,
+  kErrZero = 6,
+  kErrRange = 7,
+  kErrInternal = 8,
+  kErrCapacity = 9,
+};
+
+// per-prime constants (indexed by the prime's position in the table)
+struct PrimeConst {
+  uint32_t p;
+  uint32_t pinv;   // p^-1 mod 2^32
+  uint32_t one_m;  // 2^32 mod p   (Montgomery form of 1)
+  uint32_t r2;     // 2^64 mod p
+  uint32_t g;      // smallest primitive root (standard form)
+  uint32_t g_m;    // its Montgomery form
+  uint32_t half;   // (p - 1) / 2
+  uint32_t pad;
+};
+
+// device tables owned by a context
+struct Tables {
+  const PrimeConst* pc;  // [T]
+  const uint32_t* pw;    // [T][kMaxLimbs + 1]: 2^(32 l) * 2^64 mod p
+  const uint32_t* mpw;   // [T][kMaxLimbs + 1]: Montgomery form of 2^(32 l)
+  const int64_t* lg_prefix;  // [T + 1]: sums of lower bounds of log2 p (Q16)
+  // transform tables for the first Tt primes, row length NT
+  const uint32_t* tw;    // [Tt][NT/2] omega^i, omega of order NT (Montgomery)
+  const uint32_t* itw;   // [Tt][NT/2] omega^-i (Montgomery)
+  const uint32_t* cp;    // [Tt][NT] g^i (Montgomery)
+  const uint32_t* icp;   // [Tt][NT] g^-i (standard form)
+  const uint32_t* ninv;  // [Tt][kLogNMax + 1] 2^-s (Montgomery form)
+  // Garner table for the first Tg primes: ginv[a * Tg + b] = p_a^-1 mod p_b (Montgomery)
+  const uint32_t* ginv;
+  int32_t T, Tt, NT, logNT, Tg;
+};
+
+// one resultant job as the kernels see it
+struct Job {
+  Grid f, g;
+  int32_t var;
+  int32_t rows;   // (me + 1) + (ne + 1)
+  Plan plan;
+  uint32_t* ev;    // [k_total][rows][N] evaluations (Montgomery form)
+  uint32_t* vals;  // [k_total][N] univariate resultants (Montgomery form, bit-reversed order)
+  uint32_t* rmod;  // [k_need][D + 1] residues of the result coefficients (standard form)
+  int32_t* pstat;  // [k_total] 0 = good prime, 1 = rejected
+  int32_t* sel;    // [k_need] table index of the j-th selected prime
+  uint32_t* out;   // [cap_deg + 1][cap_limbs]
+  int32_t cap_deg, cap_limbs;
+  int32_t* status;  // sticky device status word of the call
+  int32_t* rejected;  // counter of rejected primes (may be null)
+};
+
+// work lists: stage work of job ids[i] occupies [off[i], off[i+1]) of a flat index space
+struct WorkList {
+  const int32_t* ids;  // may be null: identity
+  const int64_t* off;  // n + 1 entries
+  int32_t n;
+};
+
+__device__ __forceinline__ int find_item(const int64_t* off, int n, int64_t item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void set_status(int32_t* st, int32_t code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+}  // namespace bs

@@ -1,0 +1,83 @@
+// Host-side context of libbsres.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/bsres.h"
+#include "common.cuh"
+#include "resultant_kernels.cuh"
+#include "tables.cuh"
+
+struct bs_ctx {
+  int device = 0;
+  int sms = 0;
+  int smem_optin = 48 * 1024;
+  size_t budget = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  bs::DeviceTables tabs;
+  // workspace of host-planned calls
+  void* ws = nullptr;
+  size_t ws_cap = 0;
+  int ws_generation = 0;
+  // workspace of device-planned calls
+  void* dev_ws = nullptr;
+  size_t dev_ws_cap = 0;
+  // pinned staging
+  void* h_up = nullptr;
+  size_t h_up_cap = 0;
+  void* h_down = nullptr;
+  size_t h_down_cap = 0;
+  int32_t* d_status = nullptr;  // [status, rejected, -, -] of device-planned calls
+  int occ[bs::kNumUniClasses] = {1, 1, 1, 1, 1, 1};
+  // cached executable graph of the batched stages
+  cudaGraphExec_t graph_exec = nullptr;
+  // square-free / gcd scratch
+  void* extra = nullptr;
+  size_t extra_cap = 0;
+  std::string err;
+  bs_stats stats{};
+  // per-stage timing: events 0..5 bracket plan | eval | unires | intt | crt
+  bool profile = false;
+  cudaEvent_t prof_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool prof_rec[6] = {false, false, false, false, false, false};
+};
+
+constexpr int kProfEvents = 6;
+
+namespace bs {
+
+// bump layout with 256-byte alignment
+struct Layout {
+  size_t used = 0;
+  size_t take(size_t bytes) {
+    size_t off = (used + 255) & ~(size_t)255;
+    used = off + bytes;
+    return off;
+  }
+};
+
+struct MetaBounds {
+  int32_t D, logN, rows, len, k_total, k_need, out_limbs;
+};
+
+struct StageLaunch {
+  const Job* jobs;
+  WorkList eval, intt, crt;
+  WorkList uni[kNumUniClasses];
+  int64_t eval_items, intt_items, crt_items;
+  int64_t uni_items[kNumUniClasses];
+  int maxN, kmax, lmax;
+};
+
+int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_graph);
+int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const MetaBounds& mb,
+                      int cls);
+
+}  // namespace bs
+
+int ctx_fail(bs_ctx* ctx, int code, const std::string& msg);
+int ctx_cuda(bs_ctx* ctx, cudaError_t e, const char* what);
+int ensure_workspace(bs_ctx* ctx, size_t bytes);
+void ctx_release_extra(bs_ctx* ctx);

@@ -1,0 +1,114 @@
+// Arithmetic in Z_p for 31-bit primes 2^30 < p < 2^31.
+//
+// Multiplication uses Montgomery's reduction (P. L. Montgomery, "Modular multiplication
+// without trial division", Math. Comp. 44 (1985)) with R = 2^32, in the variant that
+// subtracts m*p instead of adding it:  for t < p * 2^32 and m = (t mod 2^32) * p^-1
+// mod 2^32, the low words of t and m*p agree, so (t - m*p) / 2^32 = hi(t) - hi(m*p),
+// which lies in (-p, p) and needs one conditional correction.
+//
+// Values are kept in [0, p).  "Montgomery form" of x is x * 2^32 mod p.
+#pragma once
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define BS_HD __host__ __device__ __forceinline__
+#else
+#define BS_HD inline
+#endif
+
+namespace bs {
+
+struct Mod {
+  uint32_t p;     // the prime
+  uint32_t pinv;  // p^-1 mod 2^32
+};
+
+BS_HD uint32_t umulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+// t < p * 2^32  ->  t * 2^-32 mod p in [0, p)
+BS_HD uint32_t redc(uint64_t t, uint32_t p, uint32_t pinv) {
+  uint32_t tl = (uint32_t)t;
+  uint32_t th = (uint32_t)(t >> 32);
+  uint32_t m = tl * pinv;
+  uint32_t h = umulhi32(m, p);
+  uint32_t r = th - h;
+  return (th < h) ? r + p : r;
+}
+
+// t < 2^32 * 1.5p (e.g. a sum of three products of values < p): fold the high word
+// once, then reduce.
+BS_HD uint32_t redc_wide(uint64_t t, uint32_t p, uint32_t pinv) {
+  uint32_t tl = (uint32_t)t;
+  uint32_t th = (uint32_t)(t >> 32);
+  uint32_t th2 = th - p;
+  th = th2 < th ? th2 : th;  // th >= p ? th - p : th
+  uint32_t m = tl * pinv;
+  uint32_t h = umulhi32(m, p);
+  uint32_t r = th - h;
+  return (th < h) ? r + p : r;
+}
+
+BS_HD uint32_t mmul(uint32_t a, uint32_t b, const Mod& M) {
+  return redc((uint64_t)a * b, M.p, M.pinv);
+}
+
+BS_HD uint32_t madd(uint32_t a, uint32_t b, uint32_t p) {
+  uint32_t s = a + b;  // < 2^32 since a, b < 2^31
+  uint32_t s2 = s - p;
+  return s2 < s ? s2 : s;
+}
+
+BS_HD uint32_t msub(uint32_t a, uint32_t b, uint32_t p) {
+  uint32_t d = a - b;
+  return (a < b) ? d + p : d;
+}
+
+BS_HD uint32_t mneg(uint32_t a, uint32_t p) { return a ? p - a : 0; }
+
+// a^e in Montgomery form (one_m = 2^32 mod p is the Montgomery form of 1)
+BS_HD uint32_t mpow(uint32_t a, uint32_t e, uint32_t one_m, const Mod& M) {
+  uint32_t r = one_m;
+  while (e) {
+    if (e & 1u) r = mmul(r, a, M);
+    e >>= 1;
+    if (e) a = mmul(a, a, M);
+  }
+  return r;
+}
+
+// inverse of a non-zero Montgomery-form value by Fermat's little theorem
+BS_HD uint32_t minv(uint32_t a, uint32_t one_m, const Mod& M) {
+  return mpow(a, M.p - 2, one_m, M);
+}
+
+// ------------------------------------------------------------------------------------
+// host-side helpers (plain 64-bit arithmetic)
+// ------------------------------------------------------------------------------------
+inline uint32_t host_pinv(uint32_t p) {
+  // Newton iteration for p^-1 mod 2^32 (p odd): x <- x * (2 - p x), doubling the
+  // number of correct low bits each step, starting from x = p (correct to 3 bits).
+  uint32_t x = p;
+  for (int i = 0; i < 5; ++i) x *= 2u - p * x;
+  return x;
+}
+
+inline uint32_t host_powmod(uint64_t a, uint64_t e, uint64_t p) {
+  uint64_t r = 1 % p;
+  a %= p;
+  while (e) {
+    if (e & 1) r = r * a % p;
+    a = a * a % p;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+
+inline uint32_t host_to_mont(uint64_t x, uint64_t p) { return (uint32_t)(((x % p) << 32) % p); }
+
+}  // namespace bs

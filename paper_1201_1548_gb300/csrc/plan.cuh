@@ -1,0 +1,335 @@
+// Planning of one resultant job: actual degrees, the degree bound D, the transform size
+// N, the coefficient bound B, the number of primes, spare primes and output limbs.
+// The same code runs on the host (host-resident inputs) and in a one-block-per-job
+// device kernel (device-resident inputs).  No floating point is used: magnitudes are
+// carried as "upper floats" (a 32-bit mantissa and a binary exponent, always rounded
+// up), so every derived quantity is a guaranteed upper bound.
+//
+// Degree bound (Sec. 2, below the Sylvester matrix): deg R <= m * n for total degrees
+// m, n; every term of det S also has degree <= n_e deg_o f + m_e deg_o g, where e is
+// the eliminated variable and o the other one.  D is the smaller of the two.
+//
+// Coefficient bound: |coef R| <= B = (sum_j ||f_j||_1^2)^(n_e/2) (sum_j ||g_j||_1^2)^(m_e/2)
+// (Hadamard's inequality on the unit circle); primes are taken until prod p > 4B,
+// one bit more than symmetric residues need.
+#pragma once
+#include <stdint.h>
+
+#include "modarith.cuh"
+
+namespace bs {
+
+constexpr int kLogNMax = 14;             // transform sizes up to 2^14 (p = 1 mod 2^14)
+constexpr int kNMax = 1 << kLogNMax;
+constexpr int kMaxLimbs = 64;            // input coefficients up to 2048 bits
+constexpr int kUniMaxLen = 129;          // univariate stage: degrees up to 128
+
+BS_HD int clz64(uint64_t v) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)v);
+#else
+  return v ? __builtin_clzll(v) : 64;
+#endif
+}
+BS_HD int clz32(uint32_t v) {
+#ifdef __CUDA_ARCH__
+  return __clz((int)v);
+#else
+  return v ? __builtin_clz(v) : 32;
+#endif
+}
+
+// value <= m * 2^e ; m == 0 encodes 0, otherwise 2^31 <= m < 2^32
+struct UF {
+  uint32_t m;
+  int32_t e;
+};
+
+// an upper bound of v * 2^e (plus one unit of 2^e when `inexact`)
+BS_HD UF uf_make(uint64_t v, int32_t e, bool inexact) {
+  if (inexact) v += 1;
+  if (v == 0) return UF{0u, 0};
+  int lz = clz64(v);
+  int sh = 32 - lz;
+  if (sh > 0) {
+    uint64_t lost = v & ((1ull << sh) - 1ull);
+    uint64_t m = v >> sh;
+    if (lost) m += 1;
+    if (m >> 32) {
+      m >>= 1;
+      sh += 1;
+    }
+    return UF{(uint32_t)m, e + sh};
+  }
+  return UF{(uint32_t)(v << (-sh)), e + sh};
+}
+
+BS_HD UF uf_add(UF a, UF b) {
+  if (!a.m) return b;
+  if (!b.m) return a;
+  if (a.e < b.e) {
+    UF t = a;
+    a = b;
+    b = t;
+  }
+  int d = a.e - b.e;
+  uint64_t A = (uint64_t)a.m << 31;
+  uint64_t B = 0;
+  bool inexact = false;
+  if (d <= 31) {
+    B = (uint64_t)b.m << (31 - d);
+  } else if (d < 63) {
+    int s = d - 31;
+    B = (uint64_t)b.m >> s;
+    inexact = ((uint64_t)b.m & ((1ull << s) - 1ull)) != 0;
+  } else {
+    inexact = true;
+  }
+  return uf_make(A + B, a.e - 31, inexact);
+}
+
+BS_HD UF uf_mul(UF a, UF b) {
+  if (!a.m || !b.m) return UF{0u, 0};
+  return uf_make((uint64_t)a.m * b.m, a.e + b.e, false);
+}
+
+// ceil-ish upper bound of log2(a) in Q16 fixed point (a > 0)
+BS_HD int64_t uf_log2_q16_up(UF a) {
+  // a <= m 2^e with m in [2^31, 2^32): log2 = e + 31 + log2(m / 2^31)
+  uint32_t y = a.m;  // Q31 value in [1, 2)
+  int32_t frac = 0;
+  for (int i = 0; i < 16; ++i) {
+    uint64_t sq = (uint64_t)y * y;  // Q62 in [1, 4)
+    frac <<= 1;
+    if (sq >> 63) {  // >= 2
+      frac |= 1;
+      uint64_t t = sq >> 32;
+      if (sq & 0xffffffffull) t += 1;
+      if (t >> 32) t = 0xffffffffull;  // stays an upper bound of y, < 2
+      y = (uint32_t)t;
+    } else {
+      uint64_t t = sq >> 31;
+      if (sq & 0x7fffffffull) t += 1;
+      if (t >> 32) {  // rounded up to exactly 2: treat as the >= 2 branch next time
+        t = 0xffffffffull;
+      }
+      y = (uint32_t)t;
+    }
+  }
+  return (int64_t)(a.e + 31) * 65536 + frac + 1;
+}
+
+// floor-ish lower bound of log2(p) in Q16 for 2^30 < p < 2^31 (host)
+inline int64_t log2_q16_down_u31(uint32_t p) {
+  uint32_t y = p << 1;  // Q31 in [1, 2)
+  int32_t frac = 0;
+  for (int i = 0; i < 16; ++i) {
+    uint64_t sq = (uint64_t)y * y;
+    frac <<= 1;
+    if (sq >> 63) {
+      frac |= 1;
+      y = (uint32_t)(sq >> 32);
+    } else {
+      y = (uint32_t)(sq >> 31);
+    }
+  }
+  return (int64_t)30 * 65536 + frac;
+}
+
+// ------------------------------------------------------------------------------------
+// coefficient access
+// ------------------------------------------------------------------------------------
+struct Grid {
+  const uint32_t* c;
+  int32_t dx, dy, L;
+};
+
+// pointer to the limbs of the coefficient with power e of the eliminated variable and
+// power o of the other variable (var = 1: eliminate y, so e = j, o = i)
+BS_HD const uint32_t* coef_ptr(const Grid& g, int var, int e, int o) {
+  int i = var ? o : e;
+  int j = var ? e : o;
+  return g.c + ((int64_t)j * (g.dx + 1) + i) * g.L;
+}
+BS_HD int ext_e(const Grid& g, int var) { return var ? g.dy : g.dx; }
+BS_HD int ext_o(const Grid& g, int var) { return var ? g.dx : g.dy; }
+
+// magnitude of a two's complement multi-limb integer as an upper float; nonzero flag;
+// bit length of the magnitude
+BS_HD UF mag_uf(const uint32_t* c, int L, bool* nonzero, int* bits) {
+  bool neg = (c[L - 1] >> 31) != 0;
+  // walk limbs from the bottom, negating on the fly when negative
+  uint32_t carry = 1;
+  int top = -1;
+  uint32_t v1 = 0, v0 = 0;  // magnitude limbs at top and top-1
+  bool sticky = false;      // any nonzero limb below top-1
+  for (int l = 0; l < L; ++l) {
+    uint32_t x = c[l];
+    if (neg) {
+      uint32_t nx = ~x + carry;
+      carry = (carry && nx == 0) ? 1u : 0u;
+      x = nx;
+    }
+    if (x) {
+      // limbs strictly between old top and l are zero
+      if (top >= 0) {
+        if (top == l - 1) {
+          sticky = sticky || (v0 != 0);
+          v0 = v1;
+        } else {
+          sticky = sticky || (v0 != 0) || (v1 != 0);
+          v0 = 0;
+        }
+      }
+      v1 = x;
+      top = l;
+    }
+  }
+  if (top < 0) {
+    *nonzero = false;
+    *bits = 0;
+    return UF{0u, 0};
+  }
+  *nonzero = true;
+  *bits = 32 * top + (32 - clz32(v1));
+  if (top == 0) return uf_make((uint64_t)v1, 0, false);
+  return uf_make(((uint64_t)v1 << 32) | v0, 32 * (top - 1), sticky);
+}
+
+// per-row statistics of row e (eliminated-variable power e)
+struct RowStat {
+  UF l1;          // >= sum_o |coef|
+  int32_t max_o;  // highest o with a nonzero coefficient, -1 if the row is zero
+  int32_t min_bits;  // bit length of the smallest nonzero magnitude (0 if zero row)
+};
+
+BS_HD RowStat row_stat(const Grid& g, int var, int e) {
+  RowStat s{UF{0u, 0}, -1, 0};
+  int eo = ext_o(g, var);
+  for (int o = 0; o <= eo; ++o) {
+    bool nz;
+    int bits;
+    UF u = mag_uf(coef_ptr(g, var, e, o), g.L, &nz, &bits);
+    if (nz) {
+      s.l1 = uf_add(s.l1, u);
+      s.max_o = o;
+      if (s.min_bits == 0 || bits < s.min_bits) s.min_bits = bits;
+    }
+  }
+  return s;
+}
+
+// the plan of one job
+struct Plan {
+  int32_t status;     // BS_OK or an error code
+  int32_t trivial;    // 0 general, 1 result is the zero polynomial, 2 result is 1
+  int32_t me, ne;     // degrees of f and g in the eliminated variable
+  int32_t D;          // degree bound of the result (-1 for the zero polynomial)
+  int32_t logN, N;    // transform size (N >= D + 1)
+  int32_t k_need;     // primes needed: prod p > 4B
+  int32_t k_total;    // primes evaluated (k_need plus spares)
+  int32_t out_limbs;  // limbs that hold every coefficient (two's complement)
+  int64_t log2B_q16;  // upper bound of log2 B in Q16
+};
+
+// assemble the plan from per-polynomial summaries.
+//   S*: sum over rows of l1^2 (upper float); m*: degree in eliminated var (-1: zero poly)
+//   tdeg*: total degree; dego*: degree in the other variable; lcbits*: min nonzero
+//   magnitude bits of the leading row; lg_prefix[k] = sum of lower bounds of log2 p_i,
+//   i < k (Q16), for k = 0..table_size.
+BS_HD Plan finish_plan(UF Sf, int mf, int tdf, int dof, int lcbf, UF Sg, int mg, int tdg,
+                       int dog, int lcbg, const int64_t* lg_prefix, int table_size) {
+  Plan P;
+  P.status = 0;
+  P.trivial = 0;
+  P.me = mf;
+  P.ne = mg;
+  P.D = -1;
+  P.logN = 0;
+  P.N = 1;
+  P.k_need = 0;
+  P.k_total = 0;
+  P.out_limbs = 1;
+  P.log2B_q16 = 0;
+  if (mf < 0 || mg < 0) {
+    P.trivial = 1;
+    return P;
+  }
+  if (mf == 0 && mg == 0) {
+    P.trivial = 2;
+    P.D = 0;
+    return P;
+  }
+  int64_t d1 = (int64_t)tdf * tdg;
+  int64_t d2 = (int64_t)mg * dof + (int64_t)mf * dog;
+  int64_t D = d1 < d2 ? d1 : d2;
+  if (D + 1 > kNMax) {
+    P.status = 7;  // BS_ERR_RANGE
+    return P;
+  }
+  P.D = (int32_t)D;
+  int logN = 0;
+  while ((1ll << logN) < D + 1) ++logN;
+  P.logN = logN;
+  P.N = 1 << logN;
+  int64_t lf = Sf.m ? uf_log2_q16_up(Sf) : 0;
+  int64_t lg = Sg.m ? uf_log2_q16_up(Sg) : 0;
+  int64_t l2b = ((int64_t)mg * lf + (int64_t)mf * lg + 1) / 2 + 1;  // Q16, rounded up
+  if (l2b < 0) l2b = 0;
+  P.log2B_q16 = l2b;
+  int64_t need = l2b + 2 * 65536;  // prod p > 4B
+  int lo = 0, hi = table_size;
+  if (lg_prefix[table_size] < need) {
+    P.status = 7;
+    return P;
+  }
+  while (lo < hi) {  // smallest k with prefix[k] >= need
+    int mid = (lo + hi) / 2;
+    if (lg_prefix[mid] >= need)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  P.k_need = lo < 1 ? 1 : lo;
+  // a prime p > 2^30 can divide every coefficient of a leading row only if it divides
+  // the smallest one: at most (bits - 1) / 30 such primes; two more cover evaluation
+  // sets that happen to contain a root of a leading coefficient
+  int spare = (lcbf > 0 ? (lcbf - 1) / 30 : 0) + (lcbg > 0 ? (lcbg - 1) / 30 : 0) + 2;
+  P.k_total = P.k_need + spare;
+  if (P.k_total > table_size) {
+    P.status = 7;
+    return P;
+  }
+  int64_t bits = (l2b + 65535) / 65536 + 2;
+  P.out_limbs = (int32_t)((bits + 31) / 32);
+  return P;
+}
+
+// host version: scan both grids
+inline Plan plan_host(const Grid& f, const Grid& g, int var, const int64_t* lg_prefix,
+                      int table_size) {
+  auto summarise = [&](const Grid& h, UF* S, int* m, int* td, int* dego, int* lcb) {
+    *S = UF{0u, 0};
+    *m = -1;
+    *td = -1;
+    *dego = -1;
+    *lcb = 0;
+    int ee = ext_e(h, var);
+    for (int e = 0; e <= ee; ++e) {
+      RowStat rs = row_stat(h, var, e);
+      if (rs.max_o < 0) continue;
+      *S = uf_add(*S, uf_mul(rs.l1, rs.l1));
+      *m = e;
+      *lcb = rs.min_bits;
+      if (e + rs.max_o > *td) *td = e + rs.max_o;
+      if (rs.max_o > *dego) *dego = rs.max_o;
+    }
+  };
+  UF Sf, Sg;
+  int mf, tf, df, lf, mg, tg, dg, lgb;
+  summarise(f, &Sf, &mf, &tf, &df, &lf);
+  summarise(g, &Sg, &mg, &tg, &dg, &lgb);
+  return finish_plan(Sf, mf, tf, df, lf, Sg, mg, tg, dg, lgb, lg_prefix, table_size);
+}
+
+}  // namespace bs

@@ -1,0 +1,33 @@
+// Launch-side declarations of the resultant stage kernels.
+#pragma once
+#include "common.cuh"
+
+namespace bs {
+
+constexpr int kUniTile = 128;     // instances per univariate-resultant tile (one block)
+constexpr int kEvalThreads = 256; // threads of a transform block
+constexpr int kCrtWarps = 8;      // coefficients per reconstruction block
+
+// launchers (defined next to the kernels)
+int uni_occupancy(int cls);
+void launch_uni(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const uint32_t* a, int da,
+                       int lda, const uint32_t* b, int db, int ldb, uint32_t* res, Tables T);
+void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
+                Tables T, int kmax, int lmax);
+void launch_plan_single(cudaStream_t s, Job* job, int64_t* offs, Tables T);
+void set_stage_smem_limits(int bytes);
+
+// degree classes of the univariate stage: max(m_e, n_e) + 1 <= class length
+constexpr int kUniClasses[] = {8, 16, 24, 33, 48, 65};
+constexpr int kNumUniClasses = 6;
+
+inline int uni_class_of(int len) {
+  for (int i = 0; i < kNumUniClasses; ++i)
+    if (len <= kUniClasses[i]) return i;
+  return -1;
+}
+
+}  // namespace bs

@@ -1,0 +1,273 @@
+// The prime table and the per-context device tables.
+//
+// Prime table: every prime 2^30 < p < 2^31 with p = 1 (mod 2^14), in decreasing order,
+// found with a deterministic Miller-Rabin test (bases 2, 7, 61 are sufficient below
+// 4,759,123,141 -- G. Jaeschke, Math. Comp. 61 (1993)).  p = 1 mod 2^14 gives every prime
+// a multiplicative subgroup of order 2^14, so each prime evaluates on a coset g * <omega>
+// of up to 16384 points (g its smallest primitive root), which never contains 0, +1 or -1.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "tables.cuh"
+
+namespace bs {
+
+static uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) { return (a * b) % m; }  // m < 2^32
+
+static bool is_prime_u32(uint32_t n) {
+  if (n < 2) return false;
+  static const uint32_t small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  for (uint32_t q : small) {
+    if (n == q) return true;
+    if (n % q == 0) return false;
+  }
+  uint32_t d = n - 1;
+  int s = 0;
+  while ((d & 1) == 0) {
+    d >>= 1;
+    ++s;
+  }
+  for (uint32_t a : {2u, 7u, 61u}) {
+    if (a % n == 0) continue;
+    uint64_t x = host_powmod(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int r = 1; r < s; ++r) {
+      x = mulmod64(x, x, n);
+      if (x == n - 1) {
+        comp = false;
+        break;
+      }
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+static uint32_t primitive_root(uint32_t p) {
+  std::vector<uint32_t> fs;
+  uint32_t n = p - 1;
+  for (uint32_t d = 2; (uint64_t)d * d <= n; d += (d == 2 ? 1 : 2)) {
+    if (n % d == 0) {
+      fs.push_back(d);
+      while (n % d == 0) n /= d;
+    }
+  }
+  if (n > 1) fs.push_back(n);
+  for (uint32_t g = 2;; ++g) {
+    bool ok = true;
+    for (uint32_t q : fs)
+      if (host_powmod(g, (p - 1) / q, p) == 1) {
+        ok = false;
+        break;
+      }
+    if (ok) return g;
+  }
+}
+
+const HostPrimes& host_primes() {
+  static HostPrimes H;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const uint32_t step = 1u << kLogNMax;
+    for (uint32_t q = ((1u << 31) - 2) / step;; --q) {
+      uint64_t p = (uint64_t)q * step + 1;
+      if (p <= (1ull << 30)) break;
+      if (p < (1ull << 31) && is_prime_u32((uint32_t)p)) H.p.push_back((uint32_t)p);
+    }
+    const int T = (int)H.p.size();
+    H.pc.resize(T);
+    H.pw.resize((size_t)T * (kMaxLimbs + 1));
+    H.mpw.resize((size_t)T * (kMaxLimbs + 1));
+    H.lg_prefix.resize(T + 1);
+    H.lg_prefix[0] = 0;
+    for (int i = 0; i < T; ++i) {
+      const uint32_t p = H.p[i];
+      PrimeConst c;
+      c.p = p;
+      c.pinv = host_pinv(p);
+      c.one_m = (uint32_t)((1ull << 32) % p);
+      c.r2 = (uint32_t)(((uint64_t)c.one_m << 32) % p);
+      c.g = primitive_root(p);
+      c.g_m = host_to_mont(c.g, p);
+      c.half = (p - 1) / 2;
+      c.pad = 0;
+      H.pc[i] = c;
+      // pw[l] = 2^(32 l + 64) mod p, mpw[l] = 2^(32 l + 32) mod p
+      uint64_t m = c.one_m;  // 2^32
+      for (int l = 0; l <= kMaxLimbs; ++l) {
+        H.mpw[(size_t)i * (kMaxLimbs + 1) + l] = (uint32_t)m;
+        H.pw[(size_t)i * (kMaxLimbs + 1) + l] = (uint32_t)((m << 32) % p);
+        m = (m << 32) % p;
+      }
+      H.lg_prefix[i + 1] = H.lg_prefix[i] + log2_q16_down_u31(p);
+    }
+  });
+  return H;
+}
+
+// ------------------------------------------------------------------------------------
+// device tables
+// ------------------------------------------------------------------------------------
+__global__ void k_init_transform(const PrimeConst* pc, const uint32_t* omega_m,
+                                 const uint32_t* ginv_m, int Tt, int NT, int logNT,
+                                 uint32_t* tw, uint32_t* itw, uint32_t* cp, uint32_t* icp,
+                                 uint32_t* ninv) {
+  const int64_t total = (int64_t)Tt * NT;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / NT);
+    const int i = (int)(idx - (int64_t)q * NT);
+    const PrimeConst c = pc[q];
+    const Mod M{c.p, c.pinv};
+    if (i < NT / 2) {
+      const uint32_t w = omega_m[q];
+      const uint32_t wi = mpow(w, (uint32_t)i, c.one_m, M);
+      tw[(int64_t)q * (NT / 2) + i] = wi;
+      // omega^-i = omega^(NT - i)
+      itw[(int64_t)q * (NT / 2) + i] = i ? mpow(w, (uint32_t)(NT - i), c.one_m, M) : c.one_m;
+    }
+    cp[idx] = mpow(c.g_m, (uint32_t)i, c.one_m, M);
+    // standard form of g^-i: REDC of its Montgomery form
+    icp[idx] = redc((uint64_t)mpow(ginv_m[q], (uint32_t)i, c.one_m, M), c.p, c.pinv);
+    if (i <= kLogNMax) {
+      // 2^-i in Montgomery form: (2^-1)^i with 2^-1 = (p + 1) / 2
+      const uint32_t half_m = redc((uint64_t)((c.p + 1) / 2) * c.r2, c.p, c.pinv);
+      ninv[q * (kLogNMax + 1) + i] = mpow(half_m, (uint32_t)i, c.one_m, M);
+    }
+  }
+}
+
+__global__ void k_init_garner(const PrimeConst* pc, int Tg, uint32_t* ginv) {
+  const int64_t total = (int64_t)Tg * Tg;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / Tg);
+    const int b = (int)(idx - (int64_t)a * Tg);
+    if (a == b) {
+      ginv[idx] = 0;
+      continue;
+    }
+    const PrimeConst cb = pc[b];
+    const Mod M{cb.p, cb.pinv};
+    const uint32_t pa = pc[a].p % cb.p;
+    const uint32_t pa_m = redc((uint64_t)pa * cb.r2, cb.p, cb.pinv);
+    ginv[idx] = minv(pa_m, cb.one_m, M);
+  }
+}
+
+static int cu_fail(cudaError_t e) { return e == cudaSuccess ? 0 : kErrCuda; }
+
+int DeviceTables::init(cudaStream_t s) {
+  const HostPrimes& H = host_primes();
+  T = (int)H.p.size();
+  if (cudaMalloc(&pc, sizeof(PrimeConst) * T) != cudaSuccess) return kErrCuda;
+  if (cudaMalloc(&pw, sizeof(uint32_t) * H.pw.size()) != cudaSuccess) return kErrCuda;
+  if (cudaMalloc(&mpw, sizeof(uint32_t) * H.mpw.size()) != cudaSuccess) return kErrCuda;
+  if (cudaMalloc(&lgp, sizeof(int64_t) * H.lg_prefix.size()) != cudaSuccess) return kErrCuda;
+  int rc = 0;
+  rc |= cu_fail(cudaMemcpyAsync(pc, H.pc.data(), sizeof(PrimeConst) * T, cudaMemcpyHostToDevice, s));
+  rc |= cu_fail(cudaMemcpyAsync(pw, H.pw.data(), sizeof(uint32_t) * H.pw.size(), cudaMemcpyHostToDevice, s));
+  rc |= cu_fail(cudaMemcpyAsync(mpw, H.mpw.data(), sizeof(uint32_t) * H.mpw.size(), cudaMemcpyHostToDevice, s));
+  rc |= cu_fail(cudaMemcpyAsync(lgp, H.lg_prefix.data(), sizeof(int64_t) * H.lg_prefix.size(),
+                                cudaMemcpyHostToDevice, s));
+  if (rc) return kErrCuda;
+  return cu_fail(cudaStreamSynchronize(s));
+}
+
+void DeviceTables::release() {
+  for (void* p : {(void*)pc, (void*)pw, (void*)mpw, (void*)lgp, (void*)tw, (void*)itw,
+                  (void*)cp, (void*)icp, (void*)ninv, (void*)ginv})
+    if (p) cudaFree(p);
+  pc = nullptr;
+  pw = mpw = tw = itw = cp = icp = ninv = ginv = nullptr;
+  lgp = nullptr;
+  Tt = NT = logNT = Tg = 0;
+}
+
+int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
+  if (needT > T || needLogN > kLogNMax) return kErrRange;
+  if (needT <= Tt && needLogN <= logNT && needT <= Tg) return 0;
+  const HostPrimes& H = host_primes();
+  int newT = Tt;
+  if (needT > newT) {
+    newT = needT + needT / 2 + 32;
+    if (newT > T) newT = T;
+  }
+  int newLog = needLogN > logNT ? needLogN : logNT;
+  if (newLog < 6) newLog = 6;
+  const int newNT = 1 << newLog;
+  // finish any work that may still read the old tables
+  if (cudaStreamSynchronize(s) != cudaSuccess) return kErrCuda;
+  uint32_t *ntw = nullptr, *nitw = nullptr, *ncp = nullptr, *nicp = nullptr, *nninv = nullptr,
+           *nginv = nullptr, *omega = nullptr, *gi = nullptr;
+  int rc = 0;
+  rc |= cu_fail(cudaMalloc(&ntw, sizeof(uint32_t) * (size_t)newT * (newNT / 2)));
+  rc |= cu_fail(cudaMalloc(&nitw, sizeof(uint32_t) * (size_t)newT * (newNT / 2)));
+  rc |= cu_fail(cudaMalloc(&ncp, sizeof(uint32_t) * (size_t)newT * newNT));
+  rc |= cu_fail(cudaMalloc(&nicp, sizeof(uint32_t) * (size_t)newT * newNT));
+  rc |= cu_fail(cudaMalloc(&nninv, sizeof(uint32_t) * (size_t)newT * (kLogNMax + 1)));
+  rc |= cu_fail(cudaMalloc(&nginv, sizeof(uint32_t) * (size_t)newT * newT));
+  rc |= cu_fail(cudaMalloc(&omega, sizeof(uint32_t) * newT));
+  rc |= cu_fail(cudaMalloc(&gi, sizeof(uint32_t) * newT));
+  if (rc) {
+    for (void* p : {(void*)ntw, (void*)nitw, (void*)ncp, (void*)nicp, (void*)nninv, (void*)nginv,
+                    (void*)omega, (void*)gi})
+      if (p) cudaFree(p);
+    return kErrNoMem;
+  }
+  std::vector<uint32_t> om(newT), gim(newT);
+  for (int q = 0; q < newT; ++q) {
+    const uint32_t p = H.p[q];
+    const uint32_t g = H.pc[q].g;
+    om[q] = host_to_mont(host_powmod(g, (p - 1) / newNT, p), p);
+    gim[q] = host_to_mont(host_powmod(g, p - 2, p), p);
+  }
+  rc |= cu_fail(cudaMemcpyAsync(omega, om.data(), sizeof(uint32_t) * newT, cudaMemcpyHostToDevice, s));
+  rc |= cu_fail(cudaMemcpyAsync(gi, gim.data(), sizeof(uint32_t) * newT, cudaMemcpyHostToDevice, s));
+  k_init_transform<<<1024, 256, 0, s>>>(pc, omega, gi, newT, newNT, newLog, ntw, nitw, ncp, nicp, nninv);
+  rc |= cu_fail(cudaGetLastError());
+  k_init_garner<<<1024, 256, 0, s>>>(pc, newT, nginv);
+  rc |= cu_fail(cudaGetLastError());
+  rc |= cu_fail(cudaStreamSynchronize(s));
+  cudaFree(omega);
+  cudaFree(gi);
+  for (void* p : {(void*)tw, (void*)itw, (void*)cp, (void*)icp, (void*)ninv, (void*)ginv})
+    if (p) cudaFree(p);
+  tw = ntw;
+  itw = nitw;
+  cp = ncp;
+  icp = nicp;
+  ninv = nninv;
+  ginv = nginv;
+  Tt = Tg = newT;
+  NT = newNT;
+  logNT = newLog;
+  ++generation;
+  return rc ? kErrCuda : 0;
+}
+
+Tables DeviceTables::view() const {
+  Tables t;
+  t.pc = pc;
+  t.pw = pw;
+  t.mpw = mpw;
+  t.lg_prefix = lgp;
+  t.tw = tw;
+  t.itw = itw;
+  t.cp = cp;
+  t.icp = icp;
+  t.ninv = ninv;
+  t.ginv = ginv;
+  t.T = T;
+  t.Tt = Tt;
+  t.NT = NT;
+  t.logNT = logNT;
+  t.Tg = Tg;
+  return t;
+}
+
+}  // namespace bs

@@ -1,0 +1,144 @@
+// Univariate resultant mod p with formal degrees, one instance per thread (step (c) of
+// the modular algorithm, Sec. 5.1).
+//
+// Both polynomials live in registers, top-aligned (index 0 holds the formal leading
+// coefficient).  The longer one is reduced by the shorter with division-free
+// elimination; when the length difference is at least one, two elimination steps are
+// fused into one pass over the coefficients (a pseudo-remainder by a quadratic
+// multiplier).  Every identity used keeps the result equal to the determinant of the
+// formal-shape Sylvester matrix:
+//
+//   Res_{n,m}(A + hB, B)  = Res_{n,m}(A, B)                      (deg hB <= n)
+//   Res_{n,m}(cA, B)      = c^m Res_{n,m}(A, B),   Res_{n,m}(A, cB) = c^n Res_{n,m}(A, B)
+//   Res_{n,m}(A, B)       = (-1)^m b_m Res_{n-1,m}(A, B)         (a_n = 0)
+//   Res_{n,m}(A, B)       = a_n Res_{n,m-1}(A, B)                (b_m = 0)
+//   Res_{n,0}(A, b_0) = b_0^n,  Res_{0,m}(a_0, B) = a_0^m.
+//
+// The scaling factors form a product prod_i x_i^{e_i} with non-increasing exponents
+// e_i = (degree of the pivot polynomial) - 1; it is accumulated with one running prefix
+// product (prod_i x_i^{e_i} = prod_j (x_0 ... x_j)^{e_j - e_{j+1}}), so the generic
+// step costs two multiplications instead of a power.  One inversion at the end divides
+// it out.
+#pragma once
+#include "modarith.cuh"
+
+namespace bs {
+
+// P[u] = c2 P[u+2] + nc1 Q[u+2] + nc0 Q[u+1] for u < lp (entries >= length are zero, so
+// the last two computed entries come out zero and keep that invariant)
+template <int L>
+__device__ __forceinline__ void fused_pass(uint32_t (&P)[L + 2], int lp, const uint32_t (&Q)[L + 2],
+                                           uint32_t c2, uint32_t nc1, uint32_t nc0, uint32_t p,
+                                           uint32_t pinv) {
+#pragma unroll
+  for (int u = 0; u < L; ++u) {
+    if (u >= lp) break;
+    uint64_t t = (uint64_t)c2 * P[u + 2] + (uint64_t)nc1 * Q[u + 2] + (uint64_t)nc0 * Q[u + 1];
+    P[u] = redc_wide(t, p, pinv);
+  }
+}
+
+// P[u] = b0 P[u+1] + na0 Q[u+1] for u < lp
+template <int L>
+__device__ __forceinline__ void single_pass(uint32_t (&P)[L + 2], int lp, const uint32_t (&Q)[L + 2],
+                                            uint32_t b0, uint32_t na0, uint32_t p, uint32_t pinv) {
+#pragma unroll
+  for (int u = 0; u < L; ++u) {
+    if (u >= lp) break;
+    uint64_t t = (uint64_t)b0 * P[u + 1] + (uint64_t)na0 * Q[u + 1];
+    P[u] = redc(t, p, pinv);
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void shift_pass(uint32_t (&P)[L + 2], int lp) {
+#pragma unroll
+  for (int u = 0; u < L; ++u) {
+    if (u >= lp) break;
+    P[u] = P[u + 1];
+  }
+}
+
+// Returns num (Montgomery form, sign applied) and stores den so that the resultant is
+// num / den.  A and B hold la and lb coefficients (la, lb >= 1), zero beyond.
+template <int L>
+__device__ __forceinline__ uint32_t unires_numden(uint32_t (&A)[L + 2], int la, uint32_t (&B)[L + 2],
+                                                  int lb, const Mod M, uint32_t one_m,
+                                                  uint32_t* den_out) {
+  const uint32_t p = M.p, pinv = M.pinv;
+  uint32_t num = one_m, den = one_m, pre = one_m;
+  int eprev = -1;
+  uint32_t neg = 0;
+  while (la > 1 && lb > 1) {
+    if (la >= lb) {
+      const uint32_t b0 = B[0];
+      if (b0 == 0) {  // drop the formal degree of B
+        num = mmul(num, A[0], M);
+        shift_pass<L>(B, lb);
+        lb -= 1;
+        continue;
+      }
+      const int e = lb - 2;
+      if (eprev >= 0) {
+        int d = eprev - e;
+        if (d == 1)
+          den = mmul(den, pre, M);
+        else if (d > 1)
+          den = mmul(den, mpow(pre, (uint32_t)d, one_m, M), M);
+      }
+      eprev = e;
+      const uint32_t a0 = A[0];
+      if (la > lb) {
+        const uint32_t a1 = A[1], b1 = B[1];
+        const uint32_t c2 = mmul(b0, b0, M);
+        const uint32_t c1 = mmul(b0, a0, M);
+        const uint32_t c0 = redc((uint64_t)b0 * a1 + (uint64_t)(p - a0) * b1, p, pinv);
+        fused_pass<L>(A, la, B, c2, p - c1, p - c0, p, pinv);
+        la -= 2;
+        pre = mmul(pre, c2, M);
+      } else {
+        single_pass<L>(A, la, B, b0, p - a0, p, pinv);
+        la -= 1;
+        pre = mmul(pre, b0, M);
+        neg ^= (uint32_t)(lb - 1) & 1u;
+      }
+    } else {
+      const uint32_t a0 = A[0];
+      if (a0 == 0) {  // drop the formal degree of A
+        num = mmul(num, B[0], M);
+        neg ^= (uint32_t)(lb - 1) & 1u;
+        shift_pass<L>(A, la);
+        la -= 1;
+        continue;
+      }
+      const int e = la - 2;
+      if (eprev >= 0) {
+        int d = eprev - e;
+        if (d == 1)
+          den = mmul(den, pre, M);
+        else if (d > 1)
+          den = mmul(den, mpow(pre, (uint32_t)d, one_m, M), M);
+      }
+      eprev = e;
+      const uint32_t b0 = B[0], b1 = B[1], a1 = A[1];
+      const uint32_t c2 = mmul(a0, a0, M);
+      const uint32_t c1 = mmul(a0, b0, M);
+      const uint32_t c0 = redc((uint64_t)a0 * b1 + (uint64_t)(p - b0) * a1, p, pinv);
+      fused_pass<L>(B, lb, A, c2, p - c1, p - c0, p, pinv);
+      lb -= 2;
+      pre = mmul(pre, c2, M);
+    }
+  }
+  uint32_t r;
+  if (lb == 1)
+    r = mpow(B[0], (uint32_t)(la - 1), one_m, M);
+  else
+    r = mpow(A[0], (uint32_t)(lb - 1), one_m, M);
+  num = mmul(num, r, M);
+  if (eprev > 0) den = mmul(den, mpow(pre, (uint32_t)eprev, one_m, M), M);
+  if (neg) num = mneg(num, p);
+  *den_out = den;
+  return num;
+}
+
+}  // namespace bs

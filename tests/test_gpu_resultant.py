@@ -1,0 +1,148 @@
+"""Parity of the full modular resultant (steps (a)-(e)) with the oracle, bit-exact."""
+
+import random
+
+import numpy as np
+import pytest
+
+from oracle import numtheory as nt
+from oracle import poly as P
+from oracle import resultant as R
+from workloads import bimul, cfg1_pair, cfg2_pair, cfg3_batch, cfg4_cases, d_dy, dense_curve
+
+pytestmark = pytest.mark.gpu
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("var", [1, 0])
+def test_cfg1_exact(ctx, seed, var):
+    f, g = cfg1_pair(seed)
+    assert ctx.resultant(f, g, var) == R.resultant(f, g, var)
+
+
+def test_small_random_pairs_both_variables(ctx):
+    rng = _rng(11)
+    for t in range(40):
+        f = dense_curve(rng, int(rng.integers(1, 7)), int(rng.integers(2, 90)),
+                        zero_prob=0.2 if t % 2 else 0.0, keep_top=t % 3 != 0)
+        g = dense_curve(rng, int(rng.integers(1, 7)), int(rng.integers(2, 90)),
+                        zero_prob=0.2 if t % 2 else 0.0, keep_top=t % 3 != 1)
+        for var in (1, 0):
+            assert ctx.resultant(f, g, var) == R.resultant(f, g, var), (t, var)
+
+
+def test_trivial_and_constant_cases(ctx):
+    zero = [[0, 0], [0, 0]]
+    g = [[1, 2], [3, 0]]
+    assert ctx.resultant(zero, g) == []
+    assert ctx.resultant(g, zero) == []
+    assert ctx.resultant([[5]], [[7, 1]]) == [1]                 # both constant in y
+    f0 = [[2, -3, 1]]                                              # f = f_0(x), m_y = 0
+    h = [[1, 1], [0, 2], [5, 0]]
+    assert ctx.resultant(f0, h) == R.res_y(f0, h)                  # f_0^{n_y}
+    assert ctx.resultant(h, f0) == R.res_y(h, f0)
+    # high-degree x with y-degree 1 (degree bound from n_y deg_x f + m_y deg_x g)
+    f = [[1] + [0] * 40 + [3], [0] * 41 + [0, ]]
+    f[1][0] = 1
+    gg = [[2, 1], [1, 0]]
+    assert ctx.resultant(f, gg) == R.res_y(f, gg)
+
+
+def test_wide_coefficients_and_high_bits(ctx):
+    rng = _rng(12)
+    from workloads import highbit_variant
+    f = highbit_variant(dense_curve(rng, 4, 20), 512)
+    g = d_dy(f)
+    assert ctx.resultant(f, g) == R.res_y(f, g)
+    f = dense_curve(rng, 3, 1500)
+    g = dense_curve(rng, 3, 700)
+    assert ctx.resultant(f, g) == R.res_y(f, g)
+
+
+def test_cfg2_sampled_points(ctx):
+    """Discriminant-type resultant of a degree-32 curve with 32-bit coefficients: the
+    oracle evaluates R exactly at sampled integer points and mod p at sampled points."""
+    f, g = cfg2_pair(1)
+    r = ctx.resultant(f, g)
+    assert 0 <= P.deg(r) <= R.degree_bound(f, g) == 992
+    b2 = R.bound_sq(f, g)
+    assert all(c * c <= b2 for c in r)
+    for x0 in (0, 1, -1, 3):
+        assert P.evaluate(r, x0) == R.res_at_point(f, g, x0), x0
+    rng = random.Random(3)
+    for p in nt.prime_table(3):
+        for _ in range(2):
+            a = rng.randrange(p)
+            assert P.evaluate(r, a) % p == R.res_at_point_modp(f, g, a, p)
+
+
+def test_device_path_matches_host_path(ctx):
+    torch = pytest.importorskip("torch")
+    import paper_1201_1548_gb300 as bs
+    for f, g in [cfg1_pair(1), cfg2_pair(2)] + cfg3_batch(seed=9, count=3):
+        host = ctx.resultant(f, g)
+        af, dxf, dyf, Lf = bs.bipoly_to_limbs(f)
+        ag, dxg, dyg, Lg = bs.bipoly_to_limbs(g)
+        df = torch.from_numpy(af.view(np.int32).copy()).cuda()
+        dg = torch.from_numpy(ag.view(np.int32).copy()).cuda()
+        dcap, lcap = ctx.resultant_bounds((dxf, dyf, Lf), (dxg, dyg, Lg))
+        out = torch.zeros((dcap + 1) * lcap, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        ctx.resultant_device(df.data_ptr(), (dxf, dyf, Lf), dg.data_ptr(), (dxg, dyg, Lg),
+                             out.data_ptr(), (dcap, lcap))
+        ctx.device_status()
+        vals = bs.limbs_to_ints(out.cpu().numpy().view(np.uint32), dcap + 1, lcap)
+        while vals and vals[-1] == 0:
+            vals.pop()
+        assert vals == host
+
+
+def test_degenerate_cfg4(ctx):
+    cases = cfg4_cases(seed=1, deg=5, bits=12, poison_prime=nt.prime_table(1)[0])
+    # square factors: res_y(f, f_y) vanishes identically
+    assert ctx.resultant(*cases["4b"]) == []
+    assert ctx.resultant(*cases["4b2"]) == []
+    # f = f1 f2: exact against the oracle
+    fa, ga = cases["4a"]
+    assert ctx.resultant(fa, ga) == R.res_y(fa, ga)
+    # vertical asymptotes at x in {-2, -1, 0, 1, 3}: both leading coefficients vanish
+    fc, gc = cases["4c"]
+    rc = ctx.resultant(fc, gc)
+    assert rc == R.res_y(fc, gc)
+    for a in (-2, -1, 0, 1, 3):
+        assert P.evaluate(rc, a) == 0
+    # a table prime divides lc_y f: that prime is rejected, the result stays exact
+    fd, gd = cases["4d"]
+    assert ctx.resultant(fd, gd) == R.res_y(fd, gd)
+    assert ctx.last_stats()["primes_rejected"] >= 1
+
+
+def test_point_rejection_on_coset(ctx):
+    """lc_y f has a root at a point of the first prime's evaluation set: that prime is
+    rejected and the result is still exact."""
+    f0, g0 = cfg1_pair(5)
+    plan_n = 64                       # N for total degrees 7 x 6 (D <= 42)
+    p = nt.prime_table(1)[0]
+    pts = nt.coset_points(p, plan_n)
+    a = pts[5]
+    # f = (x - a) y^6 + (random lower rows)
+    f = [row + [0] for row in f0]
+    f[6] = [-a, 1] + [0] * (len(f[0]) - 2)
+    g = d_dy(f)
+    import paper_1201_1548_gb300 as bs
+    assert bs.bs_plan(f, g)["N"] == plan_n
+    r = ctx.resultant(f, g)
+    assert r == R.res_y(f, g)
+    assert ctx.last_stats()["primes_rejected"] >= 1
+
+
+def test_batch_matches_single_and_oracle(ctx):
+    pairs = cfg3_batch(seed=21, count=48, deg_lo=2, deg_hi=7, bits_lo=8, bits_hi=64)
+    got = ctx.resultant_batch(pairs)
+    for (f, g), r in zip(pairs, got):
+        assert r == R.res_y(f, g)
+        assert r == ctx.resultant(f, g)
