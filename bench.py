@@ -211,7 +211,10 @@ def run_ours(args):
     f, g = cfg2_pair(SEED)
     plan = bs.bs_plan(f, g)
     ctx = bs.Context(local)
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream shared by torch and the library, so that the CUDA
+    # events below bracket exactly the library's work
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx.set_stream(stream.cuda_stream)
     af, dxf, dyf, Lf = bs.bipoly_to_limbs(f)
     ag, dxg, dyg, Lg = bs.bipoly_to_limbs(g)

@@ -105,7 +105,11 @@ extern "C" int bs_init(int device, size_t mem_budget, bs_ctx** out) {
   }
   cudaMemset(ctx->d_status, 0, sizeof(int32_t) * 4);
   for (int c = 0; c < kNumUniClasses; ++c) ctx->occ[c] = uni_occupancy(c);
-  set_stage_smem_limits(ctx->smem_optin);
+  if (set_stage_smem_limits(ctx->smem_optin) != 0) {
+    cudaGetLastError();
+    bs_free(ctx);
+    return BS_ERR_CUDA;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     bs_free(ctx);
     return BS_ERR_CUDA;
@@ -584,6 +588,11 @@ extern "C" int bs_resultant_device(bs_ctx* ctx, const bs_bipoly* f, const bs_bip
   J.cap_limbs = out->limbs;
   J.status = ctx->d_status;
   J.rejected = ctx->d_status + 1;
+  J.cap_k_total = mb.k_total;
+  J.cap_k_need = mb.k_need;
+  J.cap_rows = mb.rows;
+  J.cap_logN = mb.logN;
+  J.cap_D = mb.D;
   cudaStream_t s = ctx->stream;
   // the job descriptor travels as a kernel argument into device memory (no host copy
   // in flight that could be overwritten by the next call)

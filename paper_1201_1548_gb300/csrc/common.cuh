@@ -65,6 +65,8 @@ struct Job {
   int32_t cap_deg, cap_limbs;
   int32_t* status;  // sticky device status word of the call
   int32_t* rejected;  // counter of rejected primes (may be null)
+  // workspace capacities (device-planned jobs): the plan must fit them
+  int32_t cap_k_total, cap_k_need, cap_rows, cap_logN, cap_D;
 };
 
 // work lists: stage work of job ids[i] occupies [off[i], off[i+1]) of a flat index space

@@ -134,7 +134,8 @@ extern "C" int bs_gcd_modp(bs_ctx* ctx, const uint32_t* a, int da, const uint32_
   rc |= ctx_cuda(ctx, cudaMemcpyAsync(base + o_job, &J, sizeof(J), cudaMemcpyHostToDevice, s), "h2d");
   if (rc) return rc;
   const size_t smem = (size_t)2 * cap * sizeof(uint32_t);
-  cudaFuncSetAttribute(k_gcd_modp, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->smem_optin);
+  if (smem > 48 * 1024 && set_dyn_smem_limit((const void*)k_gcd_modp, ctx->smem_optin) != 0)
+    return ctx_fail(ctx, BS_ERR_CUDA, "shared memory limit");
   const int threads = std::min(1024, std::max(32, ((cap + 31) / 32) * 32));
   k_gcd_modp<<<1, threads, smem, s>>>((const GcdJob*)(base + o_job), 1, cap);
   rc = ctx_cuda(ctx, cudaGetLastError(), "launch");

@@ -82,6 +82,9 @@ __global__ void k_plan_single(Job* job, int64_t* offs, Tables T) {
     if (P.status == 0 && P.trivial == 0) {
       if (P.k_total > T.Tt || P.k_need > T.Tg || P.N > T.NT) P.status = kErrInternal;
       if (P.D > J.cap_deg || P.out_limbs > J.cap_limbs) P.status = kErrInternal;
+      if (P.k_total > J.cap_k_total || P.k_need > J.cap_k_need || P.logN > J.cap_logN ||
+          P.D > J.cap_D || (P.me + 1) + (P.ne + 1) > J.cap_rows)
+        P.status = kErrInternal;
     }
     if (P.status) set_status(J.status, P.status);
     J.plan = P;
@@ -213,9 +216,9 @@ __global__ void __launch_bounds__(kUniTile) k_unires(const Job* jobs, WorkList w
     const Mod M{pc.p, pc.pinv};
     const uint32_t* bf = J->ev + (int64_t)q * rows * N + t;
     const uint32_t* bg = bf + (int64_t)(me + 1) * N;
-    uint32_t A[L + 2], B[L + 2];
+    uint32_t A[Arr<L>::N], B[Arr<L>::N];
 #pragma unroll
-    for (int s = 0; s < L + 2; ++s) {
+    for (int s = 0; s < Arr<L>::N; ++s) {
       A[s] = (s <= me) ? __ldg(bf + (int64_t)(me - s) * N) : 0u;
       B[s] = (s <= ne) ? __ldg(bg + (int64_t)(ne - s) * N) : 0u;
     }
@@ -404,9 +407,9 @@ __global__ void __launch_bounds__(kUniTile) k_unires_direct(int n, const int32_t
   if (i >= n) return;
   const PrimeConst pc = T.pc[pidx[i]];
   const Mod M{pc.p, pc.pinv};
-  uint32_t A[L + 2], B[L + 2];
+  uint32_t A[Arr<L>::N], B[Arr<L>::N];
 #pragma unroll
-  for (int s = 0; s < L + 2; ++s) {
+  for (int s = 0; s < Arr<L>::N; ++s) {
     A[s] = (s <= da) ? redc((uint64_t)a[(int64_t)i * lda + da - s] * pc.r2, M.p, M.pinv) : 0u;
     B[s] = (s <= db) ? redc((uint64_t)b[(int64_t)i * ldb + db - s] * pc.r2, M.p, M.pinv) : 0u;
   }
@@ -493,10 +496,21 @@ void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* j
 void launch_plan_single(cudaStream_t s, Job* job, int64_t* offs, Tables T) {
   k_plan_single<<<1, 256, 0, s>>>(job, offs, T);
 }
-void set_stage_smem_limits(int bytes) {
-  cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_intt, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+int set_dyn_smem_limit(const void* func, int optin) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, func) != cudaSuccess) return kErrCuda;
+  const int lim = optin - (int)a.sharedSizeBytes;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess)
+    return kErrCuda;
+  return 0;
+}
+
+int set_stage_smem_limits(int optin) {
+  int rc = 0;
+  rc |= set_dyn_smem_limit((const void*)k_eval, optin);
+  rc |= set_dyn_smem_limit((const void*)k_intt, optin);
+  rc |= set_dyn_smem_limit((const void*)k_crt, optin);
+  return rc;
 }
 
 }  // namespace bs

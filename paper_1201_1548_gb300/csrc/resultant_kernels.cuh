@@ -18,7 +18,10 @@ void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkLis
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
                 Tables T, int kmax, int lmax);
 void launch_plan_single(cudaStream_t s, Job* job, int64_t* offs, Tables T);
-void set_stage_smem_limits(int bytes);
+int set_stage_smem_limits(int optin);
+// raise a kernel's dynamic shared memory limit to what the opt-in size leaves next to its
+// static shared memory
+int set_dyn_smem_limit(const void* func, int optin);
 
 // degree classes of the univariate stage: max(m_e, n_e) + 1 <= class length
 constexpr int kUniClasses[] = {8, 16, 24, 33, 48, 65};

@@ -24,47 +24,64 @@
 
 namespace bs {
 
-// P[u] = c2 P[u+2] + nc1 Q[u+2] + nc0 Q[u+1] for u < lp (entries >= length are zero, so
-// the last two computed entries come out zero and keep that invariant)
+// Register arrays hold ceil4(L) + 2 entries; entries at or beyond a polynomial's length
+// are zero.  The passes below update four coefficients per exit test, so independent
+// updates overlap; updates past the length read only zeros and write zeros, which keeps
+// the invariant.
 template <int L>
-__device__ __forceinline__ void fused_pass(uint32_t (&P)[L + 2], int lp, const uint32_t (&Q)[L + 2],
-                                           uint32_t c2, uint32_t nc1, uint32_t nc0, uint32_t p,
-                                           uint32_t pinv) {
+struct Arr {
+  static constexpr int LL = (L + 3) / 4 * 4;  // rounded-up length
+  static constexpr int N = LL + 2;            // storage (two zeros of headroom)
+};
+
+// P[u] = c2 P[u+2] + nc1 Q[u+2] + nc0 Q[u+1] for u < lp
+template <int L>
+__device__ __forceinline__ void fused_pass(uint32_t (&P)[Arr<L>::N], int lp,
+                                           const uint32_t (&Q)[Arr<L>::N], uint32_t c2,
+                                           uint32_t nc1, uint32_t nc0, uint32_t p, uint32_t pinv) {
 #pragma unroll
-  for (int u = 0; u < L; ++u) {
-    if (u >= lp) break;
-    uint64_t t = (uint64_t)c2 * P[u + 2] + (uint64_t)nc1 * Q[u + 2] + (uint64_t)nc0 * Q[u + 1];
-    P[u] = redc_wide(t, p, pinv);
+  for (int u0 = 0; u0 < Arr<L>::LL; u0 += 4) {
+    if (u0 >= lp) break;
+#pragma unroll
+    for (int u = u0; u < u0 + 4; ++u) {
+      const uint64_t t = (uint64_t)c2 * P[u + 2] + (uint64_t)nc1 * Q[u + 2] + (uint64_t)nc0 * Q[u + 1];
+      P[u] = redc_wide(t, p, pinv);
+    }
   }
 }
 
 // P[u] = b0 P[u+1] + na0 Q[u+1] for u < lp
 template <int L>
-__device__ __forceinline__ void single_pass(uint32_t (&P)[L + 2], int lp, const uint32_t (&Q)[L + 2],
-                                            uint32_t b0, uint32_t na0, uint32_t p, uint32_t pinv) {
+__device__ __forceinline__ void single_pass(uint32_t (&P)[Arr<L>::N], int lp,
+                                            const uint32_t (&Q)[Arr<L>::N], uint32_t b0,
+                                            uint32_t na0, uint32_t p, uint32_t pinv) {
 #pragma unroll
-  for (int u = 0; u < L; ++u) {
-    if (u >= lp) break;
-    uint64_t t = (uint64_t)b0 * P[u + 1] + (uint64_t)na0 * Q[u + 1];
-    P[u] = redc(t, p, pinv);
+  for (int u0 = 0; u0 < Arr<L>::LL; u0 += 4) {
+    if (u0 >= lp) break;
+#pragma unroll
+    for (int u = u0; u < u0 + 4; ++u) {
+      const uint64_t t = (uint64_t)b0 * P[u + 1] + (uint64_t)na0 * Q[u + 1];
+      P[u] = redc(t, p, pinv);
+    }
   }
 }
 
 template <int L>
-__device__ __forceinline__ void shift_pass(uint32_t (&P)[L + 2], int lp) {
+__device__ __forceinline__ void shift_pass(uint32_t (&P)[Arr<L>::N], int lp) {
 #pragma unroll
-  for (int u = 0; u < L; ++u) {
-    if (u >= lp) break;
-    P[u] = P[u + 1];
+  for (int u0 = 0; u0 < Arr<L>::LL; u0 += 4) {
+    if (u0 >= lp) break;
+#pragma unroll
+    for (int u = u0; u < u0 + 4; ++u) P[u] = P[u + 1];
   }
 }
 
 // Returns num (Montgomery form, sign applied) and stores den so that the resultant is
 // num / den.  A and B hold la and lb coefficients (la, lb >= 1), zero beyond.
 template <int L>
-__device__ __forceinline__ uint32_t unires_numden(uint32_t (&A)[L + 2], int la, uint32_t (&B)[L + 2],
-                                                  int lb, const Mod M, uint32_t one_m,
-                                                  uint32_t* den_out) {
+__device__ __forceinline__ uint32_t unires_numden(uint32_t (&A)[Arr<L>::N], int la,
+                                                  uint32_t (&B)[Arr<L>::N], int lb, const Mod M,
+                                                  uint32_t one_m, uint32_t* den_out) {
   const uint32_t p = M.p, pinv = M.pinv;
   uint32_t num = one_m, den = one_m, pre = one_m;
   int eprev = -1;
