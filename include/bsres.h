@@ -152,6 +152,29 @@ int bs_resultant(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var,
 int bs_resultant_device(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var,
                         bs_upoly *out);
 
+/* res(f, g; var) with device-resident buffers, for callers that cannot allocate device
+ * memory while they run: code executing inside a CUDA stream capture (where cudaMalloc
+ * would synchronise or be refused), programs whose device memory is owned by another
+ * allocator or framework, and latency-critical loops that must not pay for an
+ * allocation.  The paper has no counterpart; this is a service of the library.
+ *
+ * Arguments, layout, capacities and the asynchronous behaviour are those of
+ * bs_resultant_device.  The call performs no cudaMalloc or cudaFree: all of its scratch
+ * is carved out of one static device array of 32 MiB (33554432 bytes) compiled into the
+ * library, which every GPU that loads the library holds until the process exits.  A
+ * problem whose scratch (sized from the grid extents and limb counts, like
+ * bs_resultant_bounds) exceeds 32 MiB is rejected with BS_ERR_RANGE; for example the
+ * degree-32 discriminant with 32-bit coefficients does not fit, a degree-12 one does.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.  Every call
+ * shares the one array and leaves its contents behind (the call clears what must start
+ * at zero), so calls whose GPU work overlaps -- on different streams or contexts of the
+ * same device -- race and corrupt each other's results.  The call does not grow the
+ * context's prime and transform tables: a problem larger than every earlier allocating
+ * resultant call on the context returns BS_ERR_RANGE until one such call has been made. */
+int bs_resultant_device_noalloc(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g,
+                                int var, bs_upoly *out);
+
 /* Wait for the context's stream and return the first device-side status recorded since
  * the previous call of this function (BS_OK if none), then clear it. */
 int bs_device_status(bs_ctx *ctx);

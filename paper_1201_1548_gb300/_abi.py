@@ -17,7 +17,7 @@ EXPORTED_SYMBOLS = [
     "bs_last_stats", "bs_resultant_bounds", "bs_resultant", "bs_resultant_device",
     "bs_device_status", "bs_resultant_batch", "bs_uni_resultant_modp", "bs_prime_table",
     "bs_gcd_modp", "bs_squarefree_part", "bs_plan", "bs_alu_probe", "bs_profile",
-    "bs_stage_times",
+    "bs_stage_times", "bs_resultant_device_noalloc",
 ]
 
 
@@ -79,6 +79,8 @@ def load_library():
     lib.bs_resultant_device.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I,
                                         C.POINTER(_Upoly)]
     lib.bs_device_status.argtypes = [P]
+    lib.bs_resultant_device_noalloc.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I,
+                                                C.POINTER(_Upoly)]
     lib.bs_resultant_batch.argtypes = [P, I, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I,
                                        C.POINTER(_Upoly)]
     lib.bs_uni_resultant_modp.argtypes = [P, I, P, P, I, I, P, I, I, P]
