@@ -313,7 +313,7 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
     needT = std::max(needT, P.k_total);
     needLog = std::max(needLog, P.logN);
     kmax = std::max(kmax, P.k_need);
-    lmax = std::max(lmax, P.out_limbs);
+    lmax = std::max(lmax, P.out_limbs + 1);
     maxN = std::max(maxN, P.N);
     const int c = uni_class_of(std::max(P.me, P.ne) + 1);
     if (c < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
@@ -339,6 +339,8 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
   const size_t o_jobs = up.take(sizeof(Job) * n);
   const size_t o_eoff = up.take(sizeof(int64_t) * (n + 1));
   const size_t o_ioff = up.take(sizeof(int64_t) * (n + 1));
+  const size_t o_ewoff = up.take(sizeof(int64_t) * (n + 1));
+  const size_t o_iwoff = up.take(sizeof(int64_t) * (n + 1));
   const size_t o_coff = up.take(sizeof(int64_t) * (n + 1));
   size_t o_cids[kNumUniClasses], o_coffs[kNumUniClasses];
   for (int c = 0; c < kNumUniClasses; ++c) {
@@ -393,6 +395,8 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
   Job* hj = (Job*)(hu + o_jobs);
   int64_t* eoff = (int64_t*)(hu + o_eoff);
   int64_t* ioff = (int64_t*)(hu + o_ioff);
+  int64_t* ewoff = (int64_t*)(hu + o_ewoff);
+  int64_t* iwoff = (int64_t*)(hu + o_iwoff);
   int64_t* coff = (int64_t*)(hu + o_coff);
   int32_t* cids[kNumUniClasses];
   int64_t* coffs[kNumUniClasses];
@@ -402,7 +406,7 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
     coffs[c] = (int64_t*)(hu + o_coffs[c]);
     coffs[c][0] = 0;
   }
-  eoff[0] = ioff[0] = coff[0] = 0;
+  eoff[0] = ioff[0] = coff[0] = ewoff[0] = iwoff[0] = 0;
   size_t in_pos = 0, ps_pos = 0;
   int64_t instances = 0, mulmods = 0, k_need_sum = 0, k_total_sum = 0;
   int maxpts = 0, maxprimes = 0;
@@ -421,7 +425,7 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
     J.out = (uint32_t*)(base + o_out[i]);
     J.status = (int32_t*)(base + o_status);
     J.rejected = (int32_t*)(base + o_status) + 1;
-    int64_t ne = 0, ni = 0, nu = 0;
+    int64_t ne = 0, ni = 0, nu = 0, new_ = 0, niw = 0;
     if (!P.trivial) {
       J.rows = (P.me + 1) + (P.ne + 1);
       J.ev = (uint32_t*)(base + o_ev[i]);
@@ -430,8 +434,11 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
       J.sel = (int32_t*)(base + o_sel[i]);
       J.pstat = (int32_t*)(base + o_pstat) + ps_pos;
       ps_pos += P.k_total;
-      ne = (int64_t)P.k_total * J.rows;
-      ni = P.k_total;
+      if (P.logN <= kWarpLogNMax)
+        new_ = (int64_t)P.k_total * ((J.rows + 7) / 8);
+      else
+        ne = (int64_t)P.k_total * J.rows;
+      ni = P.k_total;  // interpolation: one block per prime
       nu = (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile;
       const int c = uni_class_of(std::max(P.me, P.ne) + 1);
       cids[c][cfill[c]] = i;
@@ -447,7 +454,9 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
     hj[i] = J;
     eoff[i + 1] = eoff[i] + ne;
     ioff[i + 1] = ioff[i] + ni;
-    coff[i + 1] = coff[i] + J.cap_deg + 1;
+    ewoff[i + 1] = ewoff[i] + new_;
+    iwoff[i + 1] = iwoff[i] + niw;
+    coff[i + 1] = coff[i] + (J.cap_deg + kCrtTile) / kCrtTile;
   }
   cudaStream_t s = ctx->stream;
   rc = ctx_cuda(ctx, cudaMemcpyAsync(base, hu, up_bytes, cudaMemcpyHostToDevice, s), "upload");
@@ -465,12 +474,18 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
                         cls_count[c]};
     L.uni_items[c] = cls_count[c] ? coffs[c][cls_count[c]] : 0;
   }
+  L.eval_w = WorkList{nullptr, (const int64_t*)(base + o_ewoff), n};
+  L.intt_w = WorkList{nullptr, (const int64_t*)(base + o_iwoff), n};
   L.eval_items = eoff[n];
   L.intt_items = ioff[n];
+  L.eval_w_items = ewoff[n];
+  L.intt_w_items = iwoff[n];
   L.crt_items = coff[n];
   L.maxN = maxN;
   L.kmax = kmax;
   L.lmax = lmax;
+  L.kt_max = needT;
+  L.logN_max = needLog;
   rc = launch_stages(ctx, L, Tv, use_graph);
   if (rc) return rc;
   rc = ctx_cuda(ctx, cudaMemcpyAsync(base + o_status_dn, base + o_status, sizeof(int32_t) * 4,
@@ -552,7 +567,7 @@ extern "C" int bs_resultant_device(bs_ctx* ctx, const bs_bipoly* f, const bs_bip
   const int N = 1 << mb.logN;
   Layout lay;
   const size_t o_job = lay.take(sizeof(Job));
-  const size_t o_offs = lay.take(sizeof(int64_t) * 8);
+  const size_t o_offs = lay.take(sizeof(int64_t) * kNumOffs);
   const size_t o_pstat = lay.take(sizeof(int32_t) * mb.k_total);
   const size_t o_ev = lay.take(sizeof(uint32_t) * (size_t)mb.k_total * mb.rows * N);
   const size_t o_vals = lay.take(sizeof(uint32_t) * (size_t)mb.k_total * N);

@@ -47,6 +47,10 @@ struct Tables {
   const uint32_t* ninv;  // [Tt][kLogNMax + 1] 2^-s (Montgomery form)
   // Garner table for the first Tg primes: ginv[a * Tg + b] = p_a^-1 mod p_b (Montgomery)
   const uint32_t* ginv;
+  // prefix products of the table primes: pp[j * LPP + l] = limb l of p_0 ... p_{j-1}
+  // (j = 0..Tg), zero above the product's length
+  const uint32_t* pp;
+  int32_t LPP;
   int32_t T, Tt, NT, logNT, Tg;
 };
 

@@ -64,11 +64,12 @@ struct MetaBounds {
 
 struct StageLaunch {
   const Job* jobs;
-  WorkList eval, intt, crt;
+  WorkList eval, intt, crt, eval_w, intt_w;
   WorkList uni[kNumUniClasses];
-  int64_t eval_items, intt_items, crt_items;
+  int64_t eval_items, intt_items, crt_items, eval_w_items, intt_w_items;
   int64_t uni_items[kNumUniClasses];
   int maxN, kmax, lmax;
+  int kt_max, logN_max;  // largest prime count and transform size (L2 prefetch)
 };
 
 int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_graph);

@@ -7,21 +7,37 @@
 
 namespace bs {
 
-__global__ void k_store_job(Job J, Job* dst) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = J;
-}
-
 static int grid_for(int64_t items, int cap) {
   if (items <= 0) return 0;
   return (int)std::min<int64_t>(items, cap);
 }
 
-static int crt_warps(const bs_ctx* ctx, int kmax, int lmax, size_t* smem) {
-  const size_t per = (size_t)(4 * kmax + lmax) * sizeof(uint32_t);
-  int w = (int)std::min<size_t>(kCrtWarps, (size_t)ctx->smem_optin / per);
-  if (w < 1) w = 0;
-  *smem = per * (w > 0 ? w : 1);
-  return w;
+// shared memory of a reconstruction block: the digit tile, three per-prime arrays and
+// 3 words per limb and warp for the limb sums; when it fits, also the Garner inverses of
+// the job's primes and the prefix-product rows (staged = 1)
+static int crt_warps(const bs_ctx* ctx, int kmax, int lmax, size_t* smem, int* staged) {
+  const size_t avail = (size_t)ctx->smem_optin - 64;
+  const size_t per = (size_t)3 * lmax * sizeof(uint32_t);
+  for (int st = 1; st >= 0; --st) {
+    if (st && kmax > kCrtInvSmem) continue;
+    const size_t fixed = ((st ? (size_t)kmax * kmax + (size_t)(kmax + 1) * lmax : 0) +
+                          (size_t)kmax * kCrtTile + 3 * (size_t)kmax) * sizeof(uint32_t);
+    if (fixed + per > avail) continue;
+    const int w = (int)std::min<size_t>(kCrtWarps, (avail - fixed) / per);
+    if (st && w < 4) continue;  // prefer more warps over staging
+    *smem = fixed + per * w;
+    *staged = st;
+    return w;
+  }
+  *smem = 0;
+  *staged = 0;
+  return 0;
+}
+
+// shared memory of the warp-per-coefficient reconstruction block
+static size_t crt_warp_smem(int kmax, int lmax) {
+  return ((size_t)kmax * kmax + (size_t)kmax * lmax + (size_t)kmax * kCrtTile + 3 * (size_t)kmax +
+          (size_t)kCrtTile * kmax + (size_t)kCrtTile * lmax) * sizeof(uint32_t);
 }
 
 static inline void mark(bs_ctx* ctx, int i, cudaStream_t s) {
@@ -31,11 +47,13 @@ static inline void mark(bs_ctx* ctx, int i, cudaStream_t s) {
 }
 
 static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStream_t s, int crt_w,
-                    size_t crt_smem) {
+                    size_t crt_smem, int crt_staged) {
   const int sms = ctx->sms;
   const size_t tsmem = sizeof(uint32_t) * (size_t)L.maxN;
   mark(ctx, 1, s);
-  int g = grid_for(L.eval_items, (int64_t)sms * 8);
+  int g = grid_for(L.eval_w_items, (int64_t)sms * 8);
+  if (g) launch_eval_w(g, s, L.jobs, L.eval_w, Tv);
+  g = grid_for(L.eval_items, (int64_t)sms * 8);
   if (g) launch_eval(g, tsmem, s, L.jobs, L.eval, Tv);
   mark(ctx, 2, s);
   for (int c = 0; c < kNumUniClasses; ++c) {
@@ -43,11 +61,17 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
     if (g) launch_uni(c, g, s, L.jobs, L.uni[c], Tv);
   }
   mark(ctx, 3, s);
+  g = grid_for(L.intt_w_items, (int64_t)sms * 8);
+  if (g) launch_intt_w(g, s, L.jobs, L.intt_w, Tv);
   g = grid_for(L.intt_items, (int64_t)sms * 8);
   if (g) launch_intt(g, tsmem, s, L.jobs, L.intt, Tv);
   mark(ctx, 4, s);
-  g = grid_for((L.crt_items + crt_w - 1) / crt_w, (int64_t)sms * 4);
-  if (g) launch_crt(g, crt_w * 32, crt_smem, s, L.jobs, L.crt, Tv, L.kmax, L.lmax);
+  g = grid_for(L.crt_items, (int64_t)sms * 4);
+  const size_t wsm = crt_warp_smem(L.kmax, L.lmax);
+  if (g && L.kmax <= kCrtWarpMaxK && wsm <= (size_t)ctx->smem_optin - 64)
+    launch_crt_w(g, wsm, s, L.jobs, L.crt, Tv, L.kmax, L.lmax);
+  else if (g)
+    launch_crt(g, crt_w * 32, crt_smem, s, L.jobs, L.crt, Tv, L.kmax, L.lmax, crt_staged);
   mark(ctx, 5, s);
 }
 
@@ -56,20 +80,23 @@ int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_
   if ((size_t)L.maxN * sizeof(uint32_t) > (size_t)ctx->smem_optin)
     return ctx_fail(ctx, kErrRange, "transform size exceeds shared memory");
   size_t crt_smem = 0;
-  const int crt_w = crt_warps(ctx, L.kmax, L.lmax, &crt_smem);
+  int crt_staged = 0;
+  const int crt_w = crt_warps(ctx, L.kmax, L.lmax, &crt_smem, &crt_staged);
   if (crt_w == 0) return ctx_fail(ctx, kErrRange, "too many primes for the reconstruction stage");
   if (ctx->profile) {
     for (int i = 0; i < kProfEvents; ++i) ctx->prof_rec[i] = false;
     mark(ctx, 0, s);
   }
   if (!use_graph || ctx->profile) {
-    enqueue(ctx, L, Tv, s, crt_w, crt_smem);
+    launch_prefetch(s, Tv, L.kt_max, L.logN_max, L.kmax, L.lmax);
+    enqueue(ctx, L, Tv, s, crt_w, crt_smem, crt_staged);
     return ctx_cuda(ctx, cudaGetLastError(), "stage launch");
   }
   cudaGraph_t graph = nullptr;
   int rc = ctx_cuda(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
   if (rc) return rc;
-  enqueue(ctx, L, Tv, s, crt_w, crt_smem);
+  launch_prefetch(s, Tv, L.kt_max, L.logN_max, L.kmax, L.lmax);
+  enqueue(ctx, L, Tv, s, crt_w, crt_smem, crt_staged);
   cudaError_t le = cudaGetLastError();
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   if (le != cudaSuccess || ce != cudaSuccess) {
@@ -109,29 +136,35 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   if (ctx->profile)
     for (int i = 0; i < kProfEvents; ++i) ctx->prof_rec[i] = false;
   mark(ctx, 0, s);
-  k_store_job<<<1, 32, 0, s>>>(J, dj);
-  cudaMemsetAsync(J.pstat, 0, sizeof(int32_t) * mb.k_total, s);
-  launch_plan_single(s, dj, offs, Tv);
+  // the plan kernel receives the job by value, zeroes its prime flags and stores the
+  // planned job for the stage kernels
+  launch_plan_single(s, J, dj, offs, Tv);
   StageLaunch L;
   L.jobs = dj;
-  L.eval = WorkList{nullptr, offs + 0, 1};
+  const bool wsize = mb.logN <= kWarpLogNMax;  // the actual size is at most the bound
+  L.eval_w = WorkList{nullptr, offs + kOffEvalW, 1};
+  L.eval = WorkList{nullptr, offs + kOffEvalS, 1};
   for (int c = 0; c < kNumUniClasses; ++c) {
-    L.uni[c] = WorkList{nullptr, offs + 2, 1};
+    L.uni[c] = WorkList{nullptr, offs + kOffUni, 1};
     L.uni_items[c] = 0;
   }
   L.uni_items[cls] = (((int64_t)mb.k_total << mb.logN) + kUniTile - 1) / kUniTile;
-  L.intt = WorkList{nullptr, offs + 4, 1};
-  L.crt = WorkList{nullptr, offs + 6, 1};
-  L.eval_items = (int64_t)mb.k_total * mb.rows;
+  L.intt_w = WorkList{nullptr, offs + kOffInttW, 1};
+  L.intt = WorkList{nullptr, offs + kOffInttS, 1};
+  L.crt = WorkList{nullptr, offs + kOffCrt, 1};
+  L.eval_w_items = (int64_t)mb.k_total * ((mb.rows + 7) / 8);
+  L.eval_items = wsize ? 0 : (int64_t)mb.k_total * mb.rows;
+  L.intt_w_items = 0;
   L.intt_items = mb.k_total;
-  L.crt_items = (int64_t)J.cap_deg + 1;
+  L.crt_items = ((int64_t)J.cap_deg + kCrtTile) / kCrtTile;
   L.maxN = N;
   L.kmax = mb.k_need;
   L.lmax = J.cap_limbs;
   size_t crt_smem = 0;
-  const int crt_w = crt_warps(ctx, L.kmax, L.lmax, &crt_smem);
+  int crt_staged = 0;
+  const int crt_w = crt_warps(ctx, L.kmax, L.lmax, &crt_smem, &crt_staged);
   if (crt_w == 0) return ctx_fail(ctx, kErrRange, "too many primes for the reconstruction stage");
-  enqueue(ctx, L, Tv, s, crt_w, crt_smem);
+  enqueue(ctx, L, Tv, s, crt_w, crt_smem, crt_staged);
   return ctx_cuda(ctx, cudaGetLastError(), "stage launch");
 }
 

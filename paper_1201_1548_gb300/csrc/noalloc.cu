@@ -95,7 +95,7 @@ extern "C" int bs_resultant_device_noalloc(bs_ctx* ctx, const bs_bipoly* f, cons
   const int N = 1 << mb.logN;
   Layout lay;
   const size_t o_job = lay.take(sizeof(Job));
-  const size_t o_offs = lay.take(sizeof(int64_t) * 8);
+  const size_t o_offs = lay.take(sizeof(int64_t) * kNumOffs);
   const size_t o_pstat = lay.take(sizeof(int32_t) * mb.k_total);
   const size_t o_ev = lay.take(sizeof(uint32_t) * (size_t)mb.k_total * mb.rows * N);
   const size_t o_vals = lay.take(sizeof(uint32_t) * (size_t)mb.k_total * N);

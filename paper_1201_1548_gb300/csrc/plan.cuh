@@ -235,10 +235,11 @@ struct Plan {
 // assemble the plan from per-polynomial summaries.
 //   S*: sum over rows of l1^2 (upper float); m*: degree in eliminated var (-1: zero poly)
 //   tdeg*: total degree; dego*: degree in the other variable; lcbits*: min nonzero
-//   magnitude bits of the leading row; lg_prefix[k] = sum of lower bounds of log2 p_i,
-//   i < k (Q16), for k = 0..table_size.
-BS_HD Plan finish_plan(UF Sf, int mf, int tdf, int dof, int lcbf, UF Sg, int mg, int tdg,
-                       int dog, int lcbg, const int64_t* lg_prefix, int table_size) {
+//   magnitude bits of the leading row.  plan_head() fills everything but the prime
+//   count and returns the Q16 amount of log2(prod p) needed in *need (or a status);
+//   plan_tail() completes it from k_need.
+BS_HD Plan plan_head(UF Sf, int mf, int tdf, int dof, UF Sg, int mg, int tdg, int dog,
+                     int64_t* need) {
   Plan P;
   P.status = 0;
   P.trivial = 0;
@@ -251,6 +252,7 @@ BS_HD Plan finish_plan(UF Sf, int mf, int tdf, int dof, int lcbf, UF Sg, int mg,
   P.k_total = 0;
   P.out_limbs = 1;
   P.log2B_q16 = 0;
+  *need = 0;
   if (mf < 0 || mg < 0) {
     P.trivial = 1;
     return P;
@@ -277,20 +279,12 @@ BS_HD Plan finish_plan(UF Sf, int mf, int tdf, int dof, int lcbf, UF Sg, int mg,
   int64_t l2b = ((int64_t)mg * lf + (int64_t)mf * lg + 1) / 2 + 1;  // Q16, rounded up
   if (l2b < 0) l2b = 0;
   P.log2B_q16 = l2b;
-  int64_t need = l2b + 2 * 65536;  // prod p > 4B
-  int lo = 0, hi = table_size;
-  if (lg_prefix[table_size] < need) {
-    P.status = 7;
-    return P;
-  }
-  while (lo < hi) {  // smallest k with prefix[k] >= need
-    int mid = (lo + hi) / 2;
-    if (lg_prefix[mid] >= need)
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
-  P.k_need = lo < 1 ? 1 : lo;
+  *need = l2b + 2 * 65536;  // prod p > 4B
+  return P;
+}
+
+BS_HD void plan_tail(Plan& P, int k_need, int lcbf, int lcbg, int table_size) {
+  P.k_need = k_need < 1 ? 1 : k_need;
   // a prime p > 2^30 can divide every coefficient of a leading row only if it divides
   // the smallest one: at most (bits - 1) / 30 such primes; two more cover evaluation
   // sets that happen to contain a root of a leading coefficient
@@ -298,10 +292,43 @@ BS_HD Plan finish_plan(UF Sf, int mf, int tdf, int dof, int lcbf, UF Sg, int mg,
   P.k_total = P.k_need + spare;
   if (P.k_total > table_size) {
     P.status = 7;
+    return;
+  }
+  int64_t bits = (P.log2B_q16 + 65535) / 65536 + 2;
+  P.out_limbs = (int32_t)((bits + 31) / 32);
+}
+
+// smallest k with lg_prefix[k] >= need (host: binary search)
+inline int prime_count_host(const int64_t* lg_prefix, int table_size, int64_t need) {
+  int lo = 0, hi = table_size;
+  while (lo < hi) {
+    int mid = (lo + hi) / 2;
+    if (lg_prefix[mid] >= need)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+BS_HD Plan finish_plan(UF Sf, int mf, int tdf, int dof, int lcbf, UF Sg, int mg, int tdg,
+                       int dog, int lcbg, const int64_t* lg_prefix, int table_size) {
+  int64_t need;
+  Plan P = plan_head(Sf, mf, tdf, dof, Sg, mg, tdg, dog, &need);
+  if (P.status || P.trivial) return P;
+  if (lg_prefix[table_size] < need) {
+    P.status = 7;
     return P;
   }
-  int64_t bits = (l2b + 65535) / 65536 + 2;
-  P.out_limbs = (int32_t)((bits + 31) / 32);
+  int lo = 0, hi = table_size;
+  while (lo < hi) {
+    int mid = (lo + hi) / 2;
+    if (lg_prefix[mid] >= need)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  plan_tail(P, lo, lcbf, lcbg, table_size);
   return P;
 }
 

@@ -18,67 +18,207 @@
 #include "common.cuh"
 #include "resultant_kernels.cuh"
 #include "unires.cuh"
+#include "warp_ntt.cuh"
 
 namespace bs {
 
 // ------------------------------------------------------------------------------------
-// plan of a single device-resident job (one block)
+// L2 prefetch of the table ranges a job will read (the step may start with a cold L2):
+// one bulk prefetch per contiguous range, trimmed inward to 16-byte boundaries so that
+// every prefetched byte lies inside its allocation
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void l2_prefetch_range(const void* p, size_t bytes) {
+  uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  while (a < e) {
+    const uint32_t n = (uint32_t)((e - a) < (uintptr_t)65536 ? (e - a) : (uintptr_t)65536);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+    a += n;
+  }
+}
+
+// Per-prime tables are stored row after row, so the rows of the first kt primes form one
+// contiguous block per table: a handful of bulk prefetches (64 KiB each) covers them all.
+// kt primes, transforms up to 2^logN points, kn primes in reconstruction, lim limbs.
+__device__ void prefetch_tables(const Tables& T, int kt, int logN, int kn, int lim) {
+  kt = min(kt, T.Tt);
+  kn = min(kn, T.Tg);
+  (void)logN;
+  (void)lim;
+  if (threadIdx.x != 0) return;
+  l2_prefetch_range(T.pc, sizeof(PrimeConst) * kt);
+  l2_prefetch_range(T.pw, sizeof(uint32_t) * (size_t)kt * (kMaxLimbs + 1));
+  l2_prefetch_range(T.mpw, sizeof(uint32_t) * (size_t)kt * (kMaxLimbs + 1));
+  l2_prefetch_range(T.ninv, sizeof(uint32_t) * (size_t)kt * (kLogNMax + 1));
+  l2_prefetch_range(T.lg_prefix, sizeof(int64_t) * (size_t)(T.T + 1));
+  l2_prefetch_range(T.tw, sizeof(uint32_t) * (size_t)kt * (T.NT >> 1));
+  l2_prefetch_range(T.itw, sizeof(uint32_t) * (size_t)kt * (T.NT >> 1));
+  l2_prefetch_range(T.cp, sizeof(uint32_t) * (size_t)kt * T.NT);
+  l2_prefetch_range(T.icp, sizeof(uint32_t) * (size_t)kt * T.NT);
+  l2_prefetch_range(T.ginv, sizeof(uint32_t) * (size_t)kt * T.Tg);
+  l2_prefetch_range(T.pp, sizeof(uint32_t) * (size_t)(kn + 1) * T.LPP);
+}
+
+__global__ void k_prefetch(Tables T, int kt, int logN, int kn, int lim) {
+  // a single thread issues the prefetches
+  prefetch_tables(T, kt, logN, kn, lim);
+}
+
+// ------------------------------------------------------------------------------------
+// plan of a single device-resident job (one block of kPlanThreads)
 // ------------------------------------------------------------------------------------
 struct PolySummary {
   UF S;
   int m, td, dego, lcb;
 };
 
-__device__ void summarise_block(const Grid& h, int var, PolySummary* out, UF* sh_uf,
-                                int* sh_int) {
-  // per-thread partials over rows e = tid, tid + blockDim, ...
+__device__ __forceinline__ UF shfl_uf(UF a, int src_lane_xor) {
+  UF b;
+  b.m = __shfl_xor_sync(0xffffffffu, a.m, src_lane_xor);
+  b.e = __shfl_xor_sync(0xffffffffu, a.e, src_lane_xor);
+  return b;
+}
+
+// One half of the plan block (kPlanThreads / 2 threads) summarises one polynomial:
+// thread t takes row e = t / 8 (+ 32 per round) and the coefficients o = t % 8, +8, ...
+// of that row, so the loads of all rows are in flight together; the eight threads of a
+// row combine their partial sums with shuffles, and the rows are combined through
+// shared memory.
+__device__ void summarise_half(const Grid& h, int var, int tid, PolySummary* out, UF* sh_uf,
+                               int* sh_int) {
+  constexpr int kHalf = kPlanThreads / 2;
+  const int sub = tid & 7;
+  const int ee = ext_e(h, var), eo = ext_o(h, var);
   UF S{0u, 0};
-  int m = -1, td = -1, dego = -1;
-  int ee = ext_e(h, var);
-  for (int e = threadIdx.x; e <= ee; e += blockDim.x) {
-    RowStat rs = row_stat(h, var, e);
-    if (rs.max_o < 0) continue;
-    S = uf_add(S, uf_mul(rs.l1, rs.l1));
-    m = max(m, e);
-    td = max(td, e + rs.max_o);
-    dego = max(dego, rs.max_o);
-  }
-  // block reduction (upper floats added in any order stay upper bounds)
-  sh_uf[threadIdx.x] = S;
-  sh_int[3 * threadIdx.x + 0] = m;
-  sh_int[3 * threadIdx.x + 1] = td;
-  sh_int[3 * threadIdx.x + 2] = dego;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      sh_uf[threadIdx.x] = uf_add(sh_uf[threadIdx.x], sh_uf[threadIdx.x + s]);
-      for (int k = 0; k < 3; ++k)
-        sh_int[3 * threadIdx.x + k] = max(sh_int[3 * threadIdx.x + k], sh_int[3 * (threadIdx.x + s) + k]);
+  int m = -1, td = -1, dego = -1, lcb = 0;
+  for (int e0 = 0; e0 <= ee; e0 += kHalf / 8) {
+    const int e = e0 + tid / 8;
+    UF l1{0u, 0};
+    int mo = -1, mb = 0;
+    if (e <= ee) {
+      for (int o = sub; o <= eo; o += 8) {
+        bool nz;
+        int bits;
+        const UF u = mag_uf(coef_ptr(h, var, e, o), h.L, &nz, &bits);
+        if (nz) {
+          l1 = uf_add(l1, u);
+          mo = o;
+          mb = (mb == 0 || bits < mb) ? bits : mb;
+        }
+      }
     }
-    __syncthreads();
+#pragma unroll
+    for (int x = 4; x > 0; x >>= 1) {
+      l1 = uf_add(l1, shfl_uf(l1, x));
+      mo = max(mo, __shfl_xor_sync(0xffffffffu, mo, x));
+      const int ob = __shfl_xor_sync(0xffffffffu, mb, x);
+      mb = (mb == 0 || (ob != 0 && ob < mb)) ? ob : mb;
+    }
+    if (sub == 0 && mo >= 0) {
+      S = uf_add(S, uf_mul(l1, l1));
+      if (e > m) {
+        m = e;
+        lcb = mb;
+      }
+      td = max(td, e + mo);
+      dego = max(dego, mo);
+    }
   }
-  if (threadIdx.x == 0) {
-    out->S = sh_uf[0];
-    out->m = sh_int[0];
-    out->td = sh_int[1];
-    out->dego = sh_int[2];
-    out->lcb = 0;
-    if (out->m >= 0) out->lcb = row_stat(h, var, out->m).min_bits;
+  // combine the row leaders (sub == 0) through shared memory, then one warp reduces
+  // the slots with shuffles
+  const int slot = tid / 8;
+  if (sub == 0) {
+    sh_uf[slot] = S;
+    sh_int[5 * slot + 0] = m;
+    sh_int[5 * slot + 1] = td;
+    sh_int[5 * slot + 2] = dego;
+    sh_int[5 * slot + 3] = lcb;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    UF s{0u, 0};
+    int M = -1, TD = -1, DO = -1, LCB = 0;
+    for (int w = tid; w < kHalf / 8; w += 32) {
+      s = uf_add(s, sh_uf[w]);
+      if (sh_int[5 * w] > M) {
+        M = sh_int[5 * w];
+        LCB = sh_int[5 * w + 3];
+      }
+      TD = max(TD, sh_int[5 * w + 1]);
+      DO = max(DO, sh_int[5 * w + 2]);
+    }
+#pragma unroll
+    for (int x = 16; x > 0; x >>= 1) {
+      s = uf_add(s, shfl_uf(s, x));
+      const int oM = __shfl_xor_sync(0xffffffffu, M, x);
+      const int oL = __shfl_xor_sync(0xffffffffu, LCB, x);
+      if (oM > M) {
+        M = oM;
+        LCB = oL;
+      }
+      TD = max(TD, __shfl_xor_sync(0xffffffffu, TD, x));
+      DO = max(DO, __shfl_xor_sync(0xffffffffu, DO, x));
+    }
+    if (tid == 0) {
+      out->S = s;
+      out->m = M;
+      out->td = TD;
+      out->dego = DO;
+      out->lcb = LCB;
+    }
   }
   __syncthreads();
 }
 
-__global__ void k_plan_single(Job* job, int64_t* offs, Tables T) {
-  __shared__ UF sh_uf[256];
-  __shared__ int sh_int[3 * 256];
+// smallest k with lg_prefix[k] >= need, by one warp: every table prime has
+// 30 < log2 p < 31, so k lies in [need / 31, need / 30 + 1]; the window is scanned 32
+// entries per round (one round for all but very large bounds)
+__device__ int prime_count_warp(const int64_t* lg_prefix, int T, int64_t need) {
+  const int lane = threadIdx.x & 31;
+  int lo = (int)(need / (31ll * 65536));
+  int hi = (int)(need / (30ll * 65536)) + 2;
+  if (lo > T) lo = T;
+  if (hi > T) hi = T;
+  while (true) {
+    const int k = lo + lane;
+    const bool ok = (k <= hi) && lg_prefix[k] >= need;
+    const unsigned b = __ballot_sync(0xffffffffu, ok);
+    if (b) return lo + __ffs(b) - 1;
+    if (lo + 32 > hi) return hi + 1;  // not reachable for valid tables
+    lo += 32;
+  }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, int64_t* offs, Tables T) {
+  constexpr int kRows = kPlanThreads / 16;  // row slots per half
+  __shared__ UF sh_uf[2][kRows];
+  __shared__ int sh_int[2][5 * kRows];
   __shared__ PolySummary sf, sg;
-  Job& J = *job;
-  summarise_block(J.f, J.var, &sf, sh_uf, sh_int);
-  summarise_block(J.g, J.var, &sg, sh_uf, sh_int);
+  __shared__ Plan sP;
+  __shared__ int64_t s_need;
+  // warm L2 with the tables the later stages read (sizes bounded by the capacities)
+  prefetch_tables(T, J.cap_k_total, J.cap_logN, J.cap_k_need, J.cap_limbs);
+  // prime flags start at zero
+  for (int i = threadIdx.x; i < J.cap_k_total; i += blockDim.x) J.pstat[i] = 0;
+  // both halves run concurrently: threads [0, kPlanThreads/2) take f, the rest take g
+  const bool first = threadIdx.x < kPlanThreads / 2;
+  summarise_half(first ? J.f : J.g, J.var, threadIdx.x & (kPlanThreads / 2 - 1), first ? &sf : &sg,
+                 sh_uf[first ? 0 : 1], sh_int[first ? 0 : 1]);
   if (threadIdx.x == 0) {
-    Plan P = finish_plan(sf.S, sf.m, sf.td, sf.dego, sf.lcb, sg.S, sg.m, sg.td, sg.dego, sg.lcb,
-                         T.lg_prefix, T.T);
-    // capacity checks against what the host sized from the grid extents
+    int64_t need;
+    sP = plan_head(sf.S, sf.m, sf.td, sf.dego, sg.S, sg.m, sg.td, sg.dego, &need);
+    s_need = need;
+    if (sP.status == 0 && sP.trivial == 0 && T.lg_prefix[T.T] < need) sP.status = kErrRange;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32 && sP.status == 0 && sP.trivial == 0) {
+    const int k = prime_count_warp(T.lg_prefix, T.T, s_need);
+    if (threadIdx.x == 0) plan_tail(sP, k, sf.lcb, sg.lcb, T.T);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Plan P = sP;
+    // the plan must fit the capacities the host sized from the grid extents
     if (P.status == 0 && P.trivial == 0) {
       if (P.k_total > T.Tt || P.k_need > T.Tg || P.N > T.NT) P.status = kErrInternal;
       if (P.D > J.cap_deg || P.out_limbs > J.cap_limbs) P.status = kErrInternal;
@@ -89,16 +229,18 @@ __global__ void k_plan_single(Job* job, int64_t* offs, Tables T) {
     if (P.status) set_status(J.status, P.status);
     J.plan = P;
     J.rows = (P.trivial || P.status) ? 0 : (P.me + 1) + (P.ne + 1);
-    bool run = (P.status == 0 && P.trivial == 0);
-    // offsets for the four stages (one job each): eval, unires tiles, intt, crt
-    offs[0] = 0;
-    offs[1] = run ? (int64_t)P.k_total * J.rows : 0;
-    offs[2] = 0;
-    offs[3] = run ? (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile : 0;
-    offs[4] = 0;
-    offs[5] = run ? P.k_total : 0;
-    offs[6] = 0;
-    offs[7] = (int64_t)J.cap_deg + 1;
+    const bool run = (P.status == 0 && P.trivial == 0);
+    *dst = J;
+    // offsets of the stages (one job each): warp eval, smem eval, unires tiles,
+    // warp intt, smem intt, crt tiles
+    const bool wsize = P.logN <= kWarpLogNMax;
+    for (int s = 0; s < kNumOffs; s += 2) offs[s] = 0;
+    offs[kOffEvalW + 1] = (run && wsize) ? (int64_t)P.k_total * ((J.rows + 7) / 8) : 0;
+    offs[kOffEvalS + 1] = (run && !wsize) ? (int64_t)P.k_total * J.rows : 0;
+    offs[kOffUni + 1] = run ? (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile : 0;
+    offs[kOffInttW + 1] = 0;
+    offs[kOffInttS + 1] = run ? P.k_total : 0;
+    offs[kOffCrt + 1] = ((int64_t)J.cap_deg + kCrtTile) / kCrtTile;
   }
 }
 
@@ -191,6 +333,180 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(const Job* jobs, WorkList
     uint32_t* dst = J->ev + ((int64_t)q * rows + row) * N;
     for (int t = threadIdx.x; t < N; t += blockDim.x) dst[t] = sm[t];
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// (a) + (b) and (d) for N <= kWarpNMax: one warp per row / prime, no block barriers
+// ------------------------------------------------------------------------------------
+template <int R>
+__device__ __forceinline__ void eval_row_warp(const Job* J, int q, int row, const Tables& T,
+                                              uint32_t* sw) {
+  const int lane = threadIdx.x & 31;
+  const int me = J->plan.me;
+  const int N = J->plan.N;
+  const bool isf = row <= me;
+  const int e = isf ? row : row - me - 1;
+  const Grid G = isf ? J->f : J->g;
+  const int var = J->var;
+  const PrimeConst pc = T.pc[q];
+  const Mod M{pc.p, pc.pinv};
+  const uint32_t* pw = T.pw + (int64_t)q * (kMaxLimbs + 1);
+  const uint32_t* mpw = T.mpw + (int64_t)q * (kMaxLimbs + 1);
+  const uint32_t* cp = T.cp + (int64_t)q * T.NT;
+  const int eo = ext_o(G, var);
+  // residues times g^o, folded modulo N, staged in this warp's shared slice (rolled loop)
+  for (int t = lane; t < N; t += 32) {
+    uint32_t acc = 0;
+    for (int o = t; o <= eo; o += N) {
+      const uint32_t x = residue_m(coef_ptr(G, var, e, o), G.L, pw, mpw, M.p, M.pinv);
+      const uint32_t s = (o < T.NT) ? __ldg(cp + o) : mpow(pc.g_m, (uint32_t)o, pc.one_m, M);
+      acc = madd(acc, mmul(x, s, M), M.p);
+    }
+    sw[t] = acc;
+  }
+  __syncwarp();
+  uint32_t v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = (32 * r + lane < N) ? sw[32 * r + lane] : 0u;
+  __syncwarp();  // the transposes below reuse sw
+  const uint32_t* tw = T.tw + (int64_t)q * (T.NT >> 1);
+  if (R == 1 && N < 32) {
+    // short transform inside one register: only the stages below N
+    for (int lg = 4; lg >= 0; --lg) {
+      const int len = 1 << lg;
+      if (len >= N) continue;
+      const bool upper = (lane & len) != 0;
+      const int sh = T.logNT - (lg + 1);
+      const uint32_t w = upper ? __ldg(tw + ((lane & (len - 1)) << sh)) : pc.one_m;
+      const uint32_t x = v[0];
+      const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
+      v[0] = mmul(upper ? msub(y, x, M.p) : madd(x, y, M.p), w, M);
+    }
+  } else if constexpr (R == 32) {
+    warp_dif_1024(v, sw, tw, T.logNT, M);
+  } else {
+    warp_dif<R>(v, tw, T.logNT, M, pc.one_m);
+  }
+  uint32_t* dst = J->ev + ((int64_t)q * J->rows + row) * N;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (32 * r + lane < N) dst[32 * r + lane] = v[r];
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kEvalThreads) k_eval_w(const Job* jobs, WorkList wl, Tables T) {
+  __shared__ uint32_t s_stage[kEvalThreads / 32][33 * 32];
+  const int warp = threadIdx.x >> 5;
+  uint32_t* sw = s_stage[warp];
+  const int nw = blockDim.x >> 5;
+  const int64_t total = wl.off[wl.n];
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int ji = find_item(wl.off, wl.n, item);
+    const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
+    const int64_t local = item - wl.off[ji];
+    const int rows = J->rows;
+    const int groups = (rows + nw - 1) / nw;
+    const int q = (int)(local / groups);
+    const int row = (int)(local - (int64_t)q * groups) * nw + warp;
+    if (row >= rows) continue;
+    switch (J->plan.logN) {
+      case 0: case 1: case 2: case 3: case 4: case 5: eval_row_warp<1>(J, q, row, T, sw); break;
+      case 6: eval_row_warp<2>(J, q, row, T, sw); break;
+      case 7: eval_row_warp<4>(J, q, row, T, sw); break;
+      case 8: eval_row_warp<8>(J, q, row, T, sw); break;
+      case 9: eval_row_warp<16>(J, q, row, T, sw); break;
+      default: eval_row_warp<32>(J, q, row, T, sw); break;
+    }
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void intt_prime_warp(const Job* J, int q, int r, const Tables& T,
+                                                uint32_t* sw) {
+  const int lane = threadIdx.x & 31;
+  const int N = J->plan.N, logN = J->plan.logN, D = J->plan.D;
+  const PrimeConst pc = T.pc[q];
+  const Mod M{pc.p, pc.pinv};
+  const uint32_t* src = J->vals + ((int64_t)q << logN);
+  uint32_t v[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = (32 * i + lane < N) ? src[32 * i + lane] : 0u;
+  const uint32_t* itw = T.itw + (int64_t)q * (T.NT >> 1);
+  if (R == 1 && N < 32) {
+    for (int lg = 0; lg <= 4; ++lg) {
+      const int len = 1 << lg;
+      if (len >= N) break;
+      const bool upper = (lane & len) != 0;
+      const int sh = T.logNT - (lg + 1);
+      const uint32_t w = __ldg(itw + ((lane & (len - 1)) << sh));
+      const uint32_t x = v[0];
+      const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
+      const uint32_t t = mmul(upper ? x : y, w, M);
+      v[0] = upper ? msub(y, t, M.p) : madd(x, t, M.p);
+    }
+  } else if constexpr (R == 32) {
+    warp_dit_1024(v, sw, itw, T.logNT, M);
+  } else {
+    warp_dit<R>(v, itw, T.logNT, M, pc.one_m);
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+    if (32 * i + lane < N) sw[32 * i + lane] = v[i];
+  __syncwarp();
+  // unscale (N^-1 g^-c) in a rolled loop; coefficients above D must vanish
+  const uint32_t* icp = T.icp + (int64_t)q * T.NT;
+  const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
+  uint32_t* dst = J->rmod + (int64_t)r * (D + 1);
+  bool bad = false;
+  for (int c = lane; c < N; c += 32) {
+    const uint32_t val = mmul(mmul(sw[c], __ldg(icp + c), M), ni, M);
+    if (c <= D)
+      dst[c] = val;
+    else if (val != 0)
+      bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(J->status, kErrInternal);
+  if (lane == 0) J->sel[r] = q;
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kEvalThreads) k_intt_w(const Job* jobs, WorkList wl, Tables T) {
+  __shared__ uint32_t s_stage[kEvalThreads / 32][33 * 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* sw = s_stage[warp];
+  const int nw = blockDim.x >> 5;
+  const int64_t total = wl.off[wl.n];
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int ji = find_item(wl.off, wl.n, item);
+    const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
+    const int q = (int)(item - wl.off[ji]) * nw + warp;
+    const int k_need = J->plan.k_need, k_total = J->plan.k_total;
+    if (q >= k_total) continue;
+    // rank of prime q among the good primes
+    int cnt = 0;
+    for (int j = lane; j < q; j += 32) cnt += (J->pstat[j] == 0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (q == 0) {
+      int g = 0;
+      for (int j = lane; j < k_total; j += 32) g += (J->pstat[j] == 0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+      if (lane == 0) {
+        if (g < k_need) set_status(J->status, kErrUnlucky);
+        if (J->rejected) atomicAdd(J->rejected, k_total - g);
+      }
+    }
+    if (J->pstat[q] != 0 || cnt >= k_need) continue;
+    switch (J->plan.logN) {
+      case 0: case 1: case 2: case 3: case 4: case 5: intt_prime_warp<1>(J, q, cnt, T, sw); break;
+      case 6: intt_prime_warp<2>(J, q, cnt, T, sw); break;
+      case 7: intt_prime_warp<4>(J, q, cnt, T, sw); break;
+      case 8: intt_prime_warp<8>(J, q, cnt, T, sw); break;
+      case 9: intt_prime_warp<16>(J, q, cnt, T, sw); break;
+      default: intt_prime_warp<32>(J, q, cnt, T, sw); break;
+    }
   }
 }
 
@@ -292,78 +608,333 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
 }
 
 // ------------------------------------------------------------------------------------
-// (e): mixed-radix reconstruction, one warp per coefficient
+// (e): mixed-radix reconstruction, a tile of kCrtTile coefficients per block
 // ------------------------------------------------------------------------------------
+// Shared memory of one block (words): [inv k*k when k <= kCrtInvSmem][X k*kCrtTile]
+// [p k][pinv k][sel k][V 3*lmax per warp].  Garner's digits are computed for the whole
+// tile with the primes spread over the block; each warp then turns one coefficient's
+// digits d_j into c = sum_j d_j P_j (P_j = p_0 ... p_{j-1}, the context's prefix-product
+// table) -- an exact dot product per output limb -- and one lane propagates the carries.
+// Jobs that rejected a prime among their first k use their own prime order; for them
+// the warp runs Horner's rule c = c p_j + d_j from the top digit instead.
+__device__ __forceinline__ void crt_carry_out(const uint32_t* V, int nlimbs, int cap, bool neg,
+                                              uint32_t* out, bool* ovf) {
+  // V holds, per limb l, a 96-bit value (V[3l], V[3l+1], V[3l+2]) of weight 2^(32 l)
+  uint64_t carry_lo = 0;  // pending carry (up to 66 bits: lo 64 + hi 2)
+  uint32_t carry_hi = 0;
+  for (int l = 0; l < cap; ++l) {
+    uint64_t a = 0;
+    uint32_t ah = 0;
+    if (l < nlimbs) {
+      a = (uint64_t)V[3 * l] | ((uint64_t)V[3 * l + 1] << 32);
+      ah = V[3 * l + 2];
+    }
+    // s = a + carry (96-bit)
+    const uint64_t s = a + carry_lo;
+    const uint32_t sh = ah + carry_hi + (s < a ? 1u : 0u);
+    const uint32_t limb = (uint32_t)s;
+    out[l] = neg ? ~limb : limb;
+    carry_lo = (s >> 32) | ((uint64_t)sh << 32);
+    carry_hi = 0;
+  }
+  if (carry_lo != 0) *ovf = true;
+}
+
 __global__ void __launch_bounds__(kCrtWarps * 32) k_crt(const Job* jobs, WorkList wl, Tables T,
-                                                        int kmax, int lmax) {
+                                                        int kmax, int lmax, int staged) {
   extern __shared__ uint32_t smc[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
-  uint32_t* x = smc + (size_t)warp * (4 * kmax + lmax);
-  uint32_t* pq = x + kmax;
+  const int nthr = blockDim.x;
+  const bool inv_in_smem = staged != 0;
+  uint32_t* sinv = smc;
+  uint32_t* X = smc + (inv_in_smem ? (size_t)kmax * kmax : 0);
+  uint32_t* pq = X + (size_t)kmax * kCrtTile;
   uint32_t* pinvq = pq + kmax;
   uint32_t* selq = pinvq + kmax;
-  uint32_t* limb = selq + kmax;
+  uint32_t* spp = selq + kmax;  // [kmax + 1][lmax] prefix rows when staged (table order)
+  uint32_t* V = spp + (inv_in_smem ? (size_t)(kmax + 1) * lmax : 0) + (size_t)warp * 3 * lmax;
+  __shared__ int s_neg[kCrtTile];
   const int64_t total = wl.off[wl.n];
-  for (int64_t item = (int64_t)blockIdx.x * nwarps + warp; item < total;
-       item += (int64_t)gridDim.x * nwarps) {
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
     const int ji = find_item(wl.off, wl.n, item);
     const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
-    const int i = (int)(item - wl.off[ji]);
+    const int i0 = (int)(item - wl.off[ji]) * kCrtTile;
     const int cap = J->cap_limbs;
-    uint32_t* out = J->out + (int64_t)i * cap;
-    const Plan& P = J->plan;
-    if (P.status != 0 || P.trivial != 0 || i > P.D) {
-      const uint32_t v0 = (P.status == 0 && P.trivial == 2 && i == 0) ? 1u : 0u;
-      for (int l = lane; l < cap; l += 32) out[l] = (l == 0) ? v0 : 0u;
-      continue;
+    const Plan P = J->plan;
+    const int ncoef = min(kCrtTile, J->cap_deg + 1 - i0);
+    if (P.status != 0 || P.trivial != 0 || i0 > P.D) {
+      for (int t = threadIdx.x; t < ncoef * cap; t += nthr) {
+        const int c = t / cap, l = t - c * cap;
+        const uint32_t v0 = (P.status == 0 && P.trivial == 2 && i0 + c == 0 && l == 0) ? 1u : 0u;
+        J->out[(int64_t)(i0 + c) * cap + l] = v0;
+      }
+      continue;  // uniform across the block
     }
-    const int k = P.k_need;
-    const int D = P.D;
-    const int Tg = T.Tg;
-    // residues and constants of the selected primes
-    for (int j = lane; j < k; j += 32) {
+    const int k = P.k_need, D = P.D, Tg = T.Tg;
+    const int nvalid = min(ncoef, D + 1 - i0);  // coefficients of this tile that exist
+    // ---- stage residues, prime constants and (small k) the inverse table
+    for (int j = threadIdx.x; j < k; j += nthr) {
       const int s = J->sel[j];
       const PrimeConst pc = T.pc[s];
-      x[j] = J->rmod[(int64_t)j * (D + 1) + i];
       pq[j] = pc.p;
       pinvq[j] = pc.pinv;
       selq[j] = (uint32_t)s;
     }
-    __syncwarp();
-    // Garner: x_q <- (x_q - d_j) * p_j^-1 mod p_q for q > j; x_j is then digit d_j
-    for (int j = 0; j < k - 1; ++j) {
-      const uint32_t d = x[j];
-      const uint32_t* grow = T.ginv + (int64_t)selq[j] * Tg;
-      for (int q = j + 1 + lane; q < k; q += 32) {
-        const uint32_t p = pq[q];
-        const uint32_t dd = d >= p ? d - p : d;
-        const Mod M{p, pinvq[q]};
-        x[q] = mmul(msub(x[q], dd, p), grow[selq[q]], M);
+    for (int t = threadIdx.x; t < k * kCrtTile; t += nthr) {
+      const int j = t / kCrtTile, c = t - j * kCrtTile;
+      X[t] = (c < nvalid) ? J->rmod[(int64_t)j * (D + 1) + i0 + c] : 0u;
+    }
+    __syncthreads();
+    const bool table_order = (selq[k - 1] == (uint32_t)(k - 1));
+    const int nl = min(min(P.out_limbs, lmax), T.LPP);  // limbs of the magnitude
+    if (inv_in_smem) {
+      // all loads of the staging are independent: unrolled so many are in flight
+#pragma unroll 4
+      for (int t = threadIdx.x; t < k * k; t += nthr) {
+        const int a = t / k, b = t - a * k;
+        sinv[t] = __ldg(T.ginv + (int64_t)selq[a] * Tg + selq[b]);
       }
+      if (table_order) {
+#pragma unroll 4
+        for (int t = threadIdx.x; t < k * nl; t += nthr) {
+          const int j = t / nl, l = t - j * nl;
+          spp[j * nl + l] = __ldg(T.pp + (int64_t)j * T.LPP + l);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- Garner: x_q <- (x_q - d_j) p_j^-1 mod p_q for q > j, whole tile
+    {
+      const int c = threadIdx.x % kCrtTile;
+      const int grp = threadIdx.x / kCrtTile;
+      const int ngrp = nthr / kCrtTile;
+      for (int j = 0; j < k - 1; ++j) {
+        const uint32_t d = X[j * kCrtTile + c];
+        for (int q = j + 1 + grp; q < k; q += ngrp) {
+          const uint32_t p = pq[q];
+          const uint32_t dd = d >= p ? d - p : d;
+          const uint32_t w = inv_in_smem ? sinv[j * k + q] : T.ginv[(int64_t)selq[j] * Tg + selq[q]];
+          const Mod M{p, pinvq[q]};
+          X[q * kCrtTile + c] = mmul(msub(X[q * kCrtTile + c], dd, p), w, M);
+        }
+        __syncthreads();
+      }
+    }
+    // ---- per coefficient (warp c): sign, complement, conversion to limbs
+    for (int c = warp; c < ncoef; c += nthr / 32) {
+      uint32_t* out = J->out + (int64_t)(i0 + c) * cap;
+      if (c >= nvalid) {  // above the degree bound
+        for (int l = lane; l < cap; l += 32) out[l] = 0u;
+        continue;
+      }
+      int hi = -1;
+      for (int j = lane; j < k; j += 32)
+        if (X[j * kCrtTile + c] != (pq[j] - 1) / 2) hi = j;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      const bool neg = hi >= 0 && X[hi * kCrtTile + c] > (pq[hi] - 1) / 2;
+      __syncwarp();
+      if (neg)
+        for (int j = lane; j < k; j += 32) X[j * kCrtTile + c] = pq[j] - 1 - X[j * kCrtTile + c];
+      __syncwarp();
+      bool ovf = false;
+      if (table_order) {
+        // c = sum_j d_j P_j.  P_j < 2^(31 j), so limb l of P_j vanishes unless
+        // 31 j > 32 l; a 32-limb chunk starts at the first row its lowest limb needs, so
+        // all lanes read the same row (coalesced) and the rows' zero limbs add nothing
+        for (int l = lane; l < (nl + 31) / 32 * 32; l += 32) {
+          uint64_t acc = 0;
+          uint32_t ah = 0;
+          const int lb = l - lane;
+          const int j0 = max(0, (32 * lb - 31) / 31);
+          const int lc = min(l, T.LPP - 1);
+#pragma unroll 8
+          for (int j = j0; j < k; ++j) {
+            const uint32_t pl = inv_in_smem ? (l < nl ? spp[j * nl + l] : 0u)
+                                            : __ldg(T.pp + (int64_t)j * T.LPP + lc);
+            const uint64_t prod = (uint64_t)X[j * kCrtTile + c] * pl;
+            const uint64_t s = acc + prod;
+            ah += (s < acc) ? 1u : 0u;
+            acc = s;
+          }
+          if (l < nl) {
+            V[3 * l] = (uint32_t)acc;
+            V[3 * l + 1] = (uint32_t)(acc >> 32);
+            V[3 * l + 2] = ah;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) crt_carry_out(V, nl, cap, neg, out, &ovf);
+      } else {
+        // Horner from the top digit; limbs spread over lanes, ballot carries
+        uint32_t* limb = V;
+        for (int l = lane; l < cap; l += 32) limb[l] = 0;
+        __syncwarp();
+        int alen = 0;
+        for (int j = k - 1; j >= 0; --j) {
+          const uint32_t pj = pq[j];
+          alen = alen + 1 < cap ? alen + 1 : cap;
+          uint32_t cin = 0, hprev = X[j * kCrtTile + c];
+          for (int b = 0; b < alen; b += 32) {
+            const int l = b + lane;
+            const uint32_t v = l < alen ? limb[l] : 0u;
+            const uint64_t prod = (uint64_t)v * pj;
+            const uint32_t lo = (uint32_t)prod, hi32 = (uint32_t)(prod >> 32);
+            uint32_t hin = __shfl_up_sync(0xffffffffu, hi32, 1);
+            if (lane == 0) hin = hprev;
+            const uint32_t s = lo + hin;
+            const uint32_t G = __ballot_sync(0xffffffffu, s < lo);
+            const uint32_t Pm = __ballot_sync(0xffffffffu, s == 0xffffffffu) & ~G;
+            const uint32_t Xm = G | Pm;
+            const uint64_t S = (uint64_t)Xm + G + cin;
+            const uint32_t C = (uint32_t)S ^ Xm ^ G;
+            const uint32_t res = s + ((C >> lane) & 1u);
+            __syncwarp();
+            if (l < alen)
+              limb[l] = res;
+            else if (l == alen && res != 0)
+              ovf = true;
+            cin = (uint32_t)(S >> 32);
+            hprev = __shfl_sync(0xffffffffu, hi32, 31);
+          }
+          if ((alen & 31) == 0 && (cin != 0 || hprev != 0)) ovf = true;
+          __syncwarp();
+        }
+        for (int l = lane; l < cap; l += 32) out[l] = neg ? ~limb[l] : limb[l];
+      }
+      if (__any_sync(0xffffffffu, ovf) && lane == 0) set_status(J->status, kErrInternal);
       __syncwarp();
     }
-    // sign: the value exceeds (P-1)/2 iff its digits exceed ((p_j - 1)/2)_j from the top
-    int hi = -1;
-    for (int j = lane; j < k; j += 32)
-      if (x[j] != (pq[j] - 1) / 2) hi = j;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// (e) for up to kCrtWarpMaxK primes: one warp per coefficient, Garner in registers
+// ------------------------------------------------------------------------------------
+// Adds the three-word column sums V_l = a_l + b_l 2^32 + c_l 2^64 (weight 2^(32 l)) into
+// limbs: the result is A + (B shifted one limb) + (C shifted two limbs), two additions
+// whose one-bit carries are resolved per 32-limb chunk with generate/propagate ballots.
+__device__ __forceinline__ uint32_t ballot_add(uint32_t x, uint32_t y, uint32_t& cin, int lane) {
+  const uint32_t s = x + y;
+  const uint32_t G = __ballot_sync(0xffffffffu, s < x);
+  const uint32_t Pm = __ballot_sync(0xffffffffu, s == 0xffffffffu) & ~G;
+  const uint32_t X = G | Pm;
+  const uint64_t S = (uint64_t)X + G + cin;
+  const uint32_t C = (uint32_t)S ^ X ^ G;
+  cin = (uint32_t)(S >> 32);
+  return s + ((C >> lane) & 1u);
+}
+
+template <int S>
+__device__ __forceinline__ void crt_coef_warp(const Job* J, const Plan& P, int i, int c,
+                                              const uint32_t* Xt, const uint32_t* sinv,
+                                              const uint32_t* spp, int nl, const uint32_t* pq,
+                                              const uint32_t* pinvq, uint32_t* sd,
+                                              uint32_t* Vw, bool table_order) {
+  const int lane = threadIdx.x & 31;
+  const int k = P.k_need;
+  const int cap = J->cap_limbs;
+  uint32_t x[S], p[S], pinv[S];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    const bool neg = hi >= 0 && x[hi] > (pq[hi] - 1) / 2;
-    __syncwarp();
-    // negative values: u = P - 1 - c has digits p_j - 1 - d_j, and c - P = ~u
-    if (neg)
-      for (int j = lane; j < k; j += 32) x[j] = pq[j] - 1 - x[j];
+  for (int s = 0; s < S; ++s) {
+    const int q = 32 * s + lane;
+    x[s] = q < k ? Xt[q * kCrtTile + c] : 0u;
+    p[s] = q < k ? pq[q] : 3u;
+    pinv[s] = q < k ? pinvq[q] : 0u;
+  }
+  // Garner: x_q <- (x_q - d_j) p_j^-1 mod p_q for q > j; the digit d_j sits in lane j%32
+#pragma unroll
+  for (int s0 = 0; s0 < S; ++s0) {
+    const int jend = min(32, k - 1 - 32 * s0);
+    for (int jj = 0; jj < jend; ++jj) {
+      const int j = 32 * s0 + jj;
+      const uint32_t d = __shfl_sync(0xffffffffu, x[s0], jj);
+#pragma unroll
+      for (int s = s0; s < S; ++s) {
+        const int q = 32 * s + lane;
+        if (q > j && q < k) {
+          const uint32_t dd = d >= p[s] ? d - p[s] : d;
+          const Mod M{p[s], pinv[s]};
+          x[s] = mmul(msub(x[s], dd, p[s]), sinv[j * k + q], M);
+        }
+      }
+    }
+  }
+  // sign: digits above ((p_j - 1) / 2)_j from the top mean the value exceeds (P - 1) / 2
+  int hi = -1;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int q = 32 * s + lane;
+    const unsigned b = __ballot_sync(0xffffffffu, q < k && x[s] != (p[s] - 1) / 2);
+    if (b) hi = 32 * s + 31 - __clz((int)b);
+  }
+  uint32_t top = 0, tophalf = 0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const uint32_t xv = __shfl_sync(0xffffffffu, x[s], hi & 31);
+    const uint32_t pv = __shfl_sync(0xffffffffu, p[s], hi & 31);
+    if (hi >= 0 && (hi >> 5) == s) {
+      top = xv;
+      tophalf = (pv - 1) / 2;
+    }
+  }
+  const bool neg = hi >= 0 && top > tophalf;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int q = 32 * s + lane;
+    if (q < k) sd[q] = neg ? p[s] - 1 - x[s] : x[s];
+  }
+  __syncwarp();
+  uint32_t* out = J->out + (int64_t)i * cap;
+  bool ovf = false;
+  if (table_order) {
+    // column sums V_l = sum_j d_j P_j[l], kept as three words in registers per chunk
+    uint32_t cin1 = 0, cin2 = 0, bprev = 0, cprev1 = 0, cprev2 = 0;
+    for (int b0 = 0; b0 < cap; b0 += 32) {
+      const int l = b0 + lane;
+      uint64_t acc = 0;
+      uint32_t ah = 0;
+      if (b0 < nl) {
+        const int j0 = max(0, (32 * b0 - 31) / 31);
+#pragma unroll 8
+        for (int j = j0; j < k; ++j) {
+          const uint32_t pl = l < nl ? spp[j * nl + l] : 0u;
+          const uint64_t prod = (uint64_t)sd[j] * pl;
+          const uint64_t s = acc + prod;
+          ah += (s < acc) ? 1u : 0u;
+          acc = s;
+        }
+      }
+      const uint32_t a = (uint32_t)acc, bw = (uint32_t)(acc >> 32), cw = ah;
+      // B shifted by one limb, C by two (values of the previous chunk feed lanes 0, 1)
+      uint32_t bin = __shfl_up_sync(0xffffffffu, bw, 1);
+      uint32_t cin_w = __shfl_up_sync(0xffffffffu, cw, 2);
+      const uint32_t c31 = __shfl_sync(0xffffffffu, cw, 31), c30 = __shfl_sync(0xffffffffu, cw, 30);
+      const uint32_t b31 = __shfl_sync(0xffffffffu, bw, 31);
+      if (lane == 0) {
+        bin = bprev;
+        cin_w = cprev2;
+      }
+      if (lane == 1) cin_w = cprev1;
+      uint32_t r = ballot_add(a, bin, cin1, lane);
+      r = ballot_add(r, cin_w, cin2, lane);
+      if (l < cap) out[l] = neg ? ~r : r;
+      bprev = b31;
+      cprev2 = c30;
+      cprev1 = c31;
+    }
+    if (cin1 || cin2 || bprev || cprev1 || cprev2) ovf = true;
+  } else {
+    // Horner from the top digit (jobs that rejected a prime among their first k)
+    uint32_t* limb = Vw;
     for (int l = lane; l < cap; l += 32) limb[l] = 0;
     __syncwarp();
-    // Horner from the top digit, c = c * p_j + d_j, limbs spread over the lanes; the
-    // carries of a 32-limb chunk are resolved with two ballots (generate / propagate)
     int alen = 0;
-    bool ovf = false;
     for (int j = k - 1; j >= 0; --j) {
       const uint32_t pj = pq[j];
       alen = alen + 1 < cap ? alen + 1 : cap;
-      uint32_t cin = 0, hprev = x[j];
+      uint32_t cin = 0, hprev = sd[j];
       for (int b = 0; b < alen; b += 32) {
         const int l = b + lane;
         const uint32_t v = l < alen ? limb[l] : 0u;
@@ -371,28 +942,105 @@ __global__ void __launch_bounds__(kCrtWarps * 32) k_crt(const Job* jobs, WorkLis
         const uint32_t lo = (uint32_t)prod, hi32 = (uint32_t)(prod >> 32);
         uint32_t hin = __shfl_up_sync(0xffffffffu, hi32, 1);
         if (lane == 0) hin = hprev;
-        const uint32_t s = lo + hin;
-        const uint32_t G = __ballot_sync(0xffffffffu, s < lo);
-        const uint32_t Pm = __ballot_sync(0xffffffffu, s == 0xffffffffu) & ~G;
-        const uint32_t X = G | Pm;
-        const uint64_t S = (uint64_t)X + G + cin;
-        const uint32_t C = (uint32_t)S ^ X ^ G;
-        const uint32_t res = s + ((C >> lane) & 1u);
+        const uint32_t res = ballot_add(lo, hin, cin, lane);
         __syncwarp();
         if (l < alen)
           limb[l] = res;
         else if (l == alen && res != 0)
           ovf = true;
-        cin = (uint32_t)(S >> 32);
         hprev = __shfl_sync(0xffffffffu, hi32, 31);
       }
       if ((alen & 31) == 0 && (cin != 0 || hprev != 0)) ovf = true;
       __syncwarp();
     }
-    if (__any_sync(0xffffffffu, ovf) && lane == 0) set_status(J->status, kErrInternal);
     for (int l = lane; l < cap; l += 32) out[l] = neg ? ~limb[l] : limb[l];
-    __syncwarp();
   }
+  if (__any_sync(0xffffffffu, ovf) && lane == 0) set_status(J->status, kErrInternal);
+  __syncwarp();
+}
+
+// Block: kCrtTile coefficients of one job, one warp each.  Shared memory (words):
+// [inv k*k][pp k*nlmax][X k*kCrtTile][p k][pinv k][sel k][digits kCrtTile*k][limbs kCrtTile*lmax]
+__global__ void __launch_bounds__(kCrtTile * 32) k_crt_w(const Job* jobs, WorkList wl, Tables T,
+                                                         int kmax, int lmax) {
+  extern __shared__ uint32_t smc[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nthr = blockDim.x;
+  uint32_t* sinv = smc;
+  uint32_t* spp = sinv + (size_t)kmax * kmax;
+  uint32_t* X = spp + (size_t)kmax * lmax;
+  uint32_t* pq = X + (size_t)kmax * kCrtTile;
+  uint32_t* pinvq = pq + kmax;
+  uint32_t* selq = pinvq + kmax;
+  uint32_t* sd = selq + kmax + (size_t)warp * kmax;
+  uint32_t* Vw = selq + kmax + (size_t)kCrtTile * kmax + (size_t)warp * lmax;
+  const int64_t total = wl.off[wl.n];
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int ji = find_item(wl.off, wl.n, item);
+    const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
+    const int i0 = (int)(item - wl.off[ji]) * kCrtTile;
+    const int cap = J->cap_limbs;
+    const Plan P = J->plan;
+    const int ncoef = min(kCrtTile, J->cap_deg + 1 - i0);
+    if (P.status != 0 || P.trivial != 0 || i0 > P.D) {
+      for (int t = threadIdx.x; t < ncoef * cap; t += nthr) {
+        const int c = t / cap, l = t - c * cap;
+        const uint32_t v0 = (P.status == 0 && P.trivial == 2 && i0 + c == 0 && l == 0) ? 1u : 0u;
+        J->out[(int64_t)(i0 + c) * cap + l] = v0;
+      }
+      continue;  // uniform across the block
+    }
+    const int k = P.k_need, D = P.D, Tg = T.Tg;
+    const int nvalid = min(ncoef, D + 1 - i0);
+    const int nl = min(min(P.out_limbs, lmax), T.LPP);
+    for (int j = threadIdx.x; j < k; j += nthr) {
+      const int s = J->sel[j];
+      const PrimeConst pc = T.pc[s];
+      pq[j] = pc.p;
+      pinvq[j] = pc.pinv;
+      selq[j] = (uint32_t)s;
+    }
+#pragma unroll 4
+    for (int t = threadIdx.x; t < k * kCrtTile; t += nthr) {
+      const int j = t / kCrtTile, c = t - j * kCrtTile;
+      X[t] = (c < nvalid) ? J->rmod[(int64_t)j * (D + 1) + i0 + c] : 0u;
+    }
+    __syncthreads();
+    const bool table_order = (selq[k - 1] == (uint32_t)(k - 1));
+#pragma unroll 4
+    for (int t = threadIdx.x; t < k * k; t += nthr) {
+      const int a = t / k, b = t - a * k;
+      sinv[t] = __ldg(T.ginv + (int64_t)selq[a] * Tg + selq[b]);
+    }
+    if (table_order) {
+#pragma unroll 4
+      for (int t = threadIdx.x; t < k * nl; t += nthr) {
+        const int j = t / nl, l = t - j * nl;
+        spp[j * nl + l] = __ldg(T.pp + (int64_t)j * T.LPP + l);
+      }
+    }
+    __syncthreads();
+    for (int c = warp; c < ncoef; c += nthr / 32) {
+      if (c >= nvalid) {  // above the degree bound
+        uint32_t* out = J->out + (int64_t)(i0 + c) * cap;
+        for (int l = lane; l < cap; l += 32) out[l] = 0u;
+        continue;
+      }
+      switch ((k + 31) >> 5) {
+        case 1: crt_coef_warp<1>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
+        case 2: crt_coef_warp<2>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
+        case 3: crt_coef_warp<3>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
+        case 4: crt_coef_warp<4>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
+        default: crt_coef_warp<5>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_crt_w(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
+                  int kmax, int lmax) {
+  k_crt_w<<<grid, kCrtTile * 32, smem, s>>>(jobs, wl, T, kmax, lmax);
 }
 
 // ------------------------------------------------------------------------------------
@@ -486,15 +1134,24 @@ void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const
 void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   k_eval<<<grid, kEvalThreads, smem, s>>>(jobs, wl, T);
 }
+void launch_eval_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
+  k_eval_w<<<grid, kEvalThreads, 0, s>>>(jobs, wl, T);
+}
+void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
+  k_intt_w<<<grid, kEvalThreads, 0, s>>>(jobs, wl, T);
+}
 void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   k_intt<<<grid, kEvalThreads, smem, s>>>(jobs, wl, T);
 }
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
-                Tables T, int kmax, int lmax) {
-  k_crt<<<grid, threads, smem, s>>>(jobs, wl, T, kmax, lmax);
+                Tables T, int kmax, int lmax, int staged) {
+  k_crt<<<grid, threads, smem, s>>>(jobs, wl, T, kmax, lmax, staged);
 }
-void launch_plan_single(cudaStream_t s, Job* job, int64_t* offs, Tables T) {
-  k_plan_single<<<1, 256, 0, s>>>(job, offs, T);
+void launch_prefetch(cudaStream_t s, Tables T, int kt, int logN, int kn, int lim) {
+  k_prefetch<<<1, 32, 0, s>>>(T, kt, logN, kn, lim);
+}
+void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T) {
+  k_plan_single<<<1, kPlanThreads, 0, s>>>(J, dst, offs, T);
 }
 int set_dyn_smem_limit(const void* func, int optin) {
   cudaFuncAttributes a;
@@ -510,6 +1167,7 @@ int set_stage_smem_limits(int optin) {
   rc |= set_dyn_smem_limit((const void*)k_eval, optin);
   rc |= set_dyn_smem_limit((const void*)k_intt, optin);
   rc |= set_dyn_smem_limit((const void*)k_crt, optin);
+  rc |= set_dyn_smem_limit((const void*)k_crt_w, optin);
   return rc;
 }
 

@@ -6,7 +6,15 @@ namespace bs {
 
 constexpr int kUniTile = 128;     // instances per univariate-resultant tile (one block)
 constexpr int kEvalThreads = 256; // threads of a transform block
-constexpr int kCrtWarps = 8;      // coefficients per reconstruction block
+constexpr int kCrtWarps = 8;      // warps of a reconstruction block
+constexpr int kCrtTile = 8;       // coefficients per reconstruction block
+constexpr int kCrtInvSmem = 160;  // prime counts whose inverse table is staged in smem
+constexpr int kCrtWarpMaxK = 160; // prime counts handled by the warp-per-coefficient kernel
+constexpr int kPlanThreads = 512; // threads of the device plan block (two halves)
+constexpr int kWarpLogNMax = 10;  // transforms up to 2^10 points run one per warp
+// device-plan offset slots (pairs [start, end) of each stage's work list)
+constexpr int kOffEvalW = 0, kOffEvalS = 2, kOffUni = 4, kOffInttW = 6, kOffInttS = 8,
+              kOffCrt = 10, kNumOffs = 12;
 
 // launchers (defined next to the kernels)
 int uni_occupancy(int cls);
@@ -15,9 +23,14 @@ void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const
                        int lda, const uint32_t* b, int db, int ldb, uint32_t* res, Tables T);
 void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+void launch_crt_w(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
+                  int kmax, int lmax);
+void launch_eval_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
-                Tables T, int kmax, int lmax);
-void launch_plan_single(cudaStream_t s, Job* job, int64_t* offs, Tables T);
+                Tables T, int kmax, int lmax, int staged);
+void launch_prefetch(cudaStream_t s, Tables T, int kt, int logN, int kn, int lim);
+void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T);
 int set_stage_smem_limits(int optin);
 // raise a kernel's dynamic shared memory limit to what the opt-in size leaves next to its
 // static shared memory

@@ -159,6 +159,43 @@ __global__ void k_init_garner(const PrimeConst* pc, int Tg, uint32_t* ginv) {
   }
 }
 
+// prefix products P_j = p_0 ... p_{j-1} of the first Tg table primes, one warp: every
+// step multiplies the previous row by p_j, lanes own 32-limb chunks, carries between
+// lanes are resolved with generate/propagate ballots
+__global__ void k_init_prefix(const PrimeConst* pc, int Tg, int LPP, uint32_t* pp) {
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  for (int l = lane; l < LPP; l += 32) pp[l] = (l == 0) ? 1u : 0u;
+  __syncwarp();
+  int len = 1;  // limbs in use
+  for (int j = 0; j < Tg; ++j) {
+    const uint32_t p = pc[j].p;
+    const uint32_t* src = pp + (size_t)j * LPP;
+    uint32_t* dst = pp + (size_t)(j + 1) * LPP;
+    const int nlen = len + 1 < LPP ? len + 1 : LPP;
+    uint32_t cin = 0, hprev = 0;
+    for (int b = 0; b < LPP; b += 32) {
+      const int l = b + lane;
+      const uint32_t v = (l < len) ? src[l] : 0u;
+      const uint64_t prod = (uint64_t)v * p;
+      const uint32_t lo = (uint32_t)prod, hi = (uint32_t)(prod >> 32);
+      uint32_t hin = __shfl_up_sync(0xffffffffu, hi, 1);
+      if (lane == 0) hin = hprev;
+      const uint32_t s = lo + hin;
+      const uint32_t G = __ballot_sync(0xffffffffu, s < lo);
+      const uint32_t Pm = __ballot_sync(0xffffffffu, s == 0xffffffffu) & ~G;
+      const uint32_t X = G | Pm;
+      const uint64_t S = (uint64_t)X + G + cin;
+      const uint32_t C = (uint32_t)S ^ X ^ G;
+      if (l < LPP) dst[l] = (l < nlen) ? s + ((C >> lane) & 1u) : 0u;
+      cin = (uint32_t)(S >> 32);
+      hprev = __shfl_sync(0xffffffffu, hi, 31);
+    }
+    len = nlen;
+    __syncwarp();
+  }
+}
+
 static int cu_fail(cudaError_t e) { return e == cudaSuccess ? 0 : kErrCuda; }
 
 int DeviceTables::init(cudaStream_t s) {
@@ -180,8 +217,10 @@ int DeviceTables::init(cudaStream_t s) {
 
 void DeviceTables::release() {
   for (void* p : {(void*)pc, (void*)pw, (void*)mpw, (void*)lgp, (void*)tw, (void*)itw,
-                  (void*)cp, (void*)icp, (void*)ninv, (void*)ginv})
+                  (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp})
     if (p) cudaFree(p);
+  pp = nullptr;
+  LPP = 0;
   pc = nullptr;
   pw = mpw = tw = itw = cp = icp = ninv = ginv = nullptr;
   lgp = nullptr;
@@ -212,6 +251,9 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   rc |= cu_fail(cudaMalloc(&nninv, sizeof(uint32_t) * (size_t)newT * (kLogNMax + 1)));
   rc |= cu_fail(cudaMalloc(&nginv, sizeof(uint32_t) * (size_t)newT * newT));
   rc |= cu_fail(cudaMalloc(&omega, sizeof(uint32_t) * newT));
+  const int newLPP = (31 * newT + 31) / 32 + 2;
+  uint32_t* npp = nullptr;
+  rc |= cu_fail(cudaMalloc(&npp, sizeof(uint32_t) * (size_t)(newT + 1) * newLPP));
   rc |= cu_fail(cudaMalloc(&gi, sizeof(uint32_t) * newT));
   if (rc) {
     for (void* p : {(void*)ntw, (void*)nitw, (void*)ncp, (void*)nicp, (void*)nninv, (void*)nginv,
@@ -232,11 +274,15 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   rc |= cu_fail(cudaGetLastError());
   k_init_garner<<<1024, 256, 0, s>>>(pc, newT, nginv);
   rc |= cu_fail(cudaGetLastError());
+  k_init_prefix<<<1, 32, 0, s>>>(pc, newT, newLPP, npp);
+  rc |= cu_fail(cudaGetLastError());
   rc |= cu_fail(cudaStreamSynchronize(s));
   cudaFree(omega);
   cudaFree(gi);
-  for (void* p : {(void*)tw, (void*)itw, (void*)cp, (void*)icp, (void*)ninv, (void*)ginv})
+  for (void* p : {(void*)tw, (void*)itw, (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp})
     if (p) cudaFree(p);
+  pp = npp;
+  LPP = newLPP;
   tw = ntw;
   itw = nitw;
   cp = ncp;
@@ -262,6 +308,8 @@ Tables DeviceTables::view() const {
   t.icp = icp;
   t.ninv = ninv;
   t.ginv = ginv;
+  t.pp = pp;
+  t.LPP = LPP;
   t.T = T;
   t.Tt = Tt;
   t.NT = NT;

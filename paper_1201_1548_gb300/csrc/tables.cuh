@@ -25,6 +25,8 @@ struct DeviceTables {
   int64_t* lgp = nullptr;
   uint32_t *tw = nullptr, *itw = nullptr, *cp = nullptr, *icp = nullptr, *ninv = nullptr;
   uint32_t* ginv = nullptr;
+  uint32_t* pp = nullptr;
+  int LPP = 0;
   int T = 0, Tt = 0, NT = 0, logNT = 0, Tg = 0;
   int generation = 0;
 

@@ -146,3 +146,19 @@ def test_batch_matches_single_and_oracle(ctx):
     for (f, g), r in zip(pairs, got):
         assert r == R.res_y(f, g)
         assert r == ctx.resultant(f, g)
+
+
+@pytest.mark.parametrize("tdeg,bits", [(40, 8), (48, 6)])
+def test_large_transforms_sampled(ctx, tdeg, bits):
+    """D >= 1024 (2048- and 4096-point sets: the shared-memory transform path)."""
+    rng = _rng(100 + tdeg)
+    f = dense_curve(rng, tdeg, bits)
+    g = d_dy(f)
+    import paper_1201_1548_gb300 as bs
+    assert bs.bs_plan(f, g)["N"] >= 2048
+    r = ctx.resultant(f, g)
+    assert P.deg(r) <= R.degree_bound(f, g)
+    for x0 in (0, 1, -2):
+        assert P.evaluate(r, x0) == R.res_at_point(f, g, x0)
+    p = nt.prime_table(1)[0]
+    assert P.evaluate(r, 12345) % p == R.res_at_point_modp(f, g, 12345, p)
