@@ -51,8 +51,22 @@ struct Tables {
   // (j = 0..Tg), zero above the product's length
   const uint32_t* pp;
   int32_t LPP;
+  // weighted-sum reconstruction for the first k table primes, k = 1..WK:
+  //   ws_m + ws_moff[k] : M_k[i] = (p_0 ... p_{k-1}) / p_i, k rows of ws_len(k) limbs
+  //   ws_y + ws_yoff[k] : y_k[i] = M_k[i]^-1 mod p_i (standard form)
+  //   q62[i] = floor(2^62 / p_i)
+  const uint32_t* ws_m;
+  const int64_t* ws_moff;
+  const uint32_t* ws_y;
+  const int32_t* ws_yoff;
+  const uint32_t* q62;
+  int64_t ws_m_words;  // allocation size of ws_m in words
+  int32_t WK;
   int32_t T, Tt, NT, logNT, Tg;
 };
+
+// limbs of the weighted-sum tables for k primes (P_k < 2^(31 k))
+__host__ __device__ __forceinline__ int ws_len(int k) { return (31 * k + 31) / 32 + 1; }
 
 // one resultant job as the kernels see it
 struct Job {

@@ -52,7 +52,7 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   const size_t tsmem = sizeof(uint32_t) * (size_t)L.maxN;
   mark(ctx, 1, s);
   int g = grid_for(L.eval_w_items, (int64_t)sms * 8);
-  if (g) launch_eval_w(g, s, L.jobs, L.eval_w, Tv);
+  if (g) launch_eval_w(g, s, L.jobs, L.eval_w, Tv, PfHint{L.kt_max, 1 << L.logN_max, L.kmax});
   g = grid_for(L.eval_items, (int64_t)sms * 8);
   if (g) launch_eval(g, tsmem, s, L.jobs, L.eval, Tv);
   mark(ctx, 2, s);
@@ -64,7 +64,7 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   g = grid_for(L.intt_w_items, (int64_t)sms * 8);
   if (g) launch_intt_w(g, s, L.jobs, L.intt_w, Tv);
   g = grid_for(L.intt_items, (int64_t)sms * 8);
-  if (g) launch_intt(g, tsmem, s, L.jobs, L.intt, Tv);
+  if (g) launch_intt(g, tsmem + tsmem / 2, s, L.jobs, L.intt, Tv);  // values + twiddles
   mark(ctx, 4, s);
   g = grid_for(L.crt_items, (int64_t)sms * 4);
   const size_t wsm = crt_warp_smem(L.kmax, L.lmax);
@@ -88,14 +88,12 @@ int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_
     mark(ctx, 0, s);
   }
   if (!use_graph || ctx->profile) {
-    launch_prefetch(s, Tv, L.kt_max, L.logN_max, L.kmax, L.lmax);
     enqueue(ctx, L, Tv, s, crt_w, crt_smem, crt_staged);
     return ctx_cuda(ctx, cudaGetLastError(), "stage launch");
   }
   cudaGraph_t graph = nullptr;
   int rc = ctx_cuda(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
   if (rc) return rc;
-  launch_prefetch(s, Tv, L.kt_max, L.logN_max, L.kmax, L.lmax);
   enqueue(ctx, L, Tv, s, crt_w, crt_smem, crt_staged);
   cudaError_t le = cudaGetLastError();
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
@@ -158,6 +156,8 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   L.intt_items = mb.k_total;
   L.crt_items = ((int64_t)J.cap_deg + kCrtTile) / kCrtTile;
   L.maxN = N;
+  L.kt_max = -1;  // the evaluation kernel reads the device plan for its prefetch sizes
+  L.logN_max = 0;
   L.kmax = mb.k_need;
   L.lmax = J.cap_limbs;
   size_t crt_smem = 0;

@@ -23,6 +23,7 @@ constexpr int kLogNMax = 14;             // transform sizes up to 2^14 (p = 1 mo
 constexpr int kNMax = 1 << kLogNMax;
 constexpr int kMaxLimbs = 64;            // input coefficients up to 2048 bits
 constexpr int kUniMaxLen = 129;          // univariate stage: degrees up to 128
+constexpr int kWsMaxK = 256;             // weighted-sum reconstruction up to 256 primes
 
 BS_HD int clz64(uint64_t v) {
 #ifdef __CUDA_ARCH__

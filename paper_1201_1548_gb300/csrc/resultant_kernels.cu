@@ -38,30 +38,47 @@ __device__ __forceinline__ void l2_prefetch_range(const void* p, size_t bytes) {
 }
 
 // Per-prime tables are stored row after row, so the rows of the first kt primes form one
-// contiguous block per table: a handful of bulk prefetches (64 KiB each) covers them all.
-// kt primes, transforms up to 2^logN points, kn primes in reconstruction, lim limbs.
-__device__ void prefetch_tables(const Tables& T, int kt, int logN, int kn, int lim) {
+// contiguous block per table.  A bulk prefetch holds its thread and uses its SM's path
+// to L2, so the 64 KiB chunks are dealt out one per block over the first blocks of a
+// grid: `rank` is the caller's index among `ranks` issuers.  These are the tables the
+// stages after evaluation read (inverse transform, reconstruction).
+struct PfRange {
+  const void* p;
+  size_t bytes;
+};
+
+__device__ void prefetch_late_tables(const Tables& T, int kt, int N, int kn, int rank, int ranks) {
   kt = min(kt, T.Tt);
   kn = min(kn, T.Tg);
-  (void)logN;
-  (void)lim;
-  if (threadIdx.x != 0) return;
-  l2_prefetch_range(T.pc, sizeof(PrimeConst) * kt);
-  l2_prefetch_range(T.pw, sizeof(uint32_t) * (size_t)kt * (kMaxLimbs + 1));
-  l2_prefetch_range(T.mpw, sizeof(uint32_t) * (size_t)kt * (kMaxLimbs + 1));
-  l2_prefetch_range(T.ninv, sizeof(uint32_t) * (size_t)kt * (kLogNMax + 1));
-  l2_prefetch_range(T.lg_prefix, sizeof(int64_t) * (size_t)(T.T + 1));
-  l2_prefetch_range(T.tw, sizeof(uint32_t) * (size_t)kt * (T.NT >> 1));
-  l2_prefetch_range(T.itw, sizeof(uint32_t) * (size_t)kt * (T.NT >> 1));
-  l2_prefetch_range(T.cp, sizeof(uint32_t) * (size_t)kt * T.NT);
-  l2_prefetch_range(T.icp, sizeof(uint32_t) * (size_t)kt * T.NT);
-  l2_prefetch_range(T.ginv, sizeof(uint32_t) * (size_t)kt * T.Tg);
-  l2_prefetch_range(T.pp, sizeof(uint32_t) * (size_t)(kn + 1) * T.LPP);
-}
-
-__global__ void k_prefetch(Tables T, int kt, int logN, int kn, int lim) {
-  // a single thread issues the prefetches
-  prefetch_tables(T, kt, logN, kn, lim);
+  const int K = min(kn, T.WK);
+  int64_t mwords = 0;  // the M_k block of k = K
+  if (K >= 1) mwords = (int64_t)K * ws_len(K);
+  const PfRange R[6] = {
+      {T.itw, sizeof(uint32_t) * (size_t)kt * (T.NT >> 1)},
+      {T.icp, sizeof(uint32_t) * (size_t)kt * T.NT},
+      {T.ginv, sizeof(uint32_t) * (size_t)kt * T.Tg},
+      {T.pp, sizeof(uint32_t) * (size_t)(kn + 1) * T.LPP},
+      {T.ws_y, sizeof(uint32_t) * (size_t)K * (K + 1) / 2},
+      {T.ws_m, sizeof(uint32_t) * (size_t)min(mwords, T.ws_m_words)},
+  };
+  (void)N;
+  constexpr size_t kChunk = 65536;
+  int base = 0;
+  for (int r = 0; r < 6; ++r) {
+    const size_t bytes = R[r].bytes;
+    const char* p0 = (const char*)R[r].p;
+    if (r == 5 && K >= 1) {  // the block of k = K starts at ws_moff[K]: read it once
+      p0 = (const char*)(T.ws_m + T.ws_moff[K]);
+    }
+    const int nchunks = (int)((bytes + kChunk - 1) / kChunk);
+    for (int c = rank - base; c < nchunks; c += ranks) {
+      if (c < 0) continue;
+      const size_t off = (size_t)c * kChunk;
+      const size_t len = bytes - off < kChunk ? bytes - off : kChunk;
+      l2_prefetch_range(p0 + off, len);
+    }
+    base = (base + nchunks) % ranks;
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -196,8 +213,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
   __shared__ PolySummary sf, sg;
   __shared__ Plan sP;
   __shared__ int64_t s_need;
-  // warm L2 with the tables the later stages read (sizes bounded by the capacities)
-  prefetch_tables(T, J.cap_k_total, J.cap_logN, J.cap_k_need, J.cap_limbs);
+  // warm L2 with the input grids (read right below)
+  if (threadIdx.x == blockDim.x - 1)
+    l2_prefetch_range(J.f.c, sizeof(uint32_t) * (size_t)(J.f.dx + 1) * (J.f.dy + 1) * J.f.L);
+  if (threadIdx.x == blockDim.x - 2)
+    l2_prefetch_range(J.g.c, sizeof(uint32_t) * (size_t)(J.g.dx + 1) * (J.g.dy + 1) * J.g.L);
   // prime flags start at zero
   for (int i = threadIdx.x; i < J.cap_k_total; i += blockDim.x) J.pstat[i] = 0;
   // both halves run concurrently: threads [0, kPlanThreads/2) take f, the rest take g
@@ -341,7 +361,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(const Job* jobs, WorkList
 // ------------------------------------------------------------------------------------
 template <int R>
 __device__ __forceinline__ void eval_row_warp(const Job* J, int q, int row, const Tables& T,
-                                              uint32_t* sw) {
+                                              uint32_t* sw, const uint32_t* s_tw,
+                                              const uint32_t* s_cp) {
   const int lane = threadIdx.x & 31;
   const int me = J->plan.me;
   const int N = J->plan.N;
@@ -353,14 +374,13 @@ __device__ __forceinline__ void eval_row_warp(const Job* J, int q, int row, cons
   const Mod M{pc.p, pc.pinv};
   const uint32_t* pw = T.pw + (int64_t)q * (kMaxLimbs + 1);
   const uint32_t* mpw = T.mpw + (int64_t)q * (kMaxLimbs + 1);
-  const uint32_t* cp = T.cp + (int64_t)q * T.NT;
   const int eo = ext_o(G, var);
   // residues times g^o, folded modulo N, staged in this warp's shared slice (rolled loop)
   for (int t = lane; t < N; t += 32) {
     uint32_t acc = 0;
     for (int o = t; o <= eo; o += N) {
       const uint32_t x = residue_m(coef_ptr(G, var, e, o), G.L, pw, mpw, M.p, M.pinv);
-      const uint32_t s = (o < T.NT) ? __ldg(cp + o) : mpow(pc.g_m, (uint32_t)o, pc.one_m, M);
+      const uint32_t s = (o < N) ? s_cp[o] : mpow(pc.g_m, (uint32_t)o, pc.one_m, M);
       acc = madd(acc, mmul(x, s, M), M.p);
     }
     sw[t] = acc;
@@ -370,23 +390,26 @@ __device__ __forceinline__ void eval_row_warp(const Job* J, int q, int row, cons
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = (32 * r + lane < N) ? sw[32 * r + lane] : 0u;
   __syncwarp();  // the transposes below reuse sw
-  const uint32_t* tw = T.tw + (int64_t)q * (T.NT >> 1);
+  // twiddles of the transform of size N: s_tw[i] = omega_N^i, so stage len reads index
+  // j << (logN - lg - 1)
+  const uint32_t* tw = s_tw;
+  const int logN = J->plan.logN;
   if (R == 1 && N < 32) {
     // short transform inside one register: only the stages below N
     for (int lg = 4; lg >= 0; --lg) {
       const int len = 1 << lg;
       if (len >= N) continue;
       const bool upper = (lane & len) != 0;
-      const int sh = T.logNT - (lg + 1);
-      const uint32_t w = upper ? __ldg(tw + ((lane & (len - 1)) << sh)) : pc.one_m;
+      const int sh = logN - (lg + 1);
+      const uint32_t w = upper ? tw[(lane & (len - 1)) << sh] : pc.one_m;
       const uint32_t x = v[0];
       const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
       v[0] = mmul(upper ? msub(y, x, M.p) : madd(x, y, M.p), w, M);
     }
   } else if constexpr (R == 32) {
-    warp_dif_1024(v, sw, tw, T.logNT, M);
+    warp_dif_1024(v, sw, tw, logN, M);
   } else {
-    warp_dif<R>(v, tw, T.logNT, M, pc.one_m);
+    warp_dif<R>(v, tw, logN, M, pc.one_m);
   }
   uint32_t* dst = J->ev + ((int64_t)q * J->rows + row) * N;
 #pragma unroll
@@ -395,12 +418,28 @@ __device__ __forceinline__ void eval_row_warp(const Job* J, int q, int row, cons
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kEvalThreads) k_eval_w(const Job* jobs, WorkList wl, Tables T) {
+__global__ void __launch_bounds__(kEvalThreads) k_eval_w(const Job* jobs, WorkList wl, Tables T,
+                                                          PfHint pf) {
   __shared__ uint32_t s_stage[kEvalThreads / 32][33 * 32];
+  __shared__ uint32_t s_tw[1 << (kWarpLogNMax - 1)];  // omega_N^i, i < N/2, of this block's prime
+  __shared__ uint32_t s_cp[(1 << kWarpLogNMax)];      // g^o, o < N
   const int warp = threadIdx.x >> 5;
   uint32_t* sw = s_stage[warp];
   const int nw = blockDim.x >> 5;
   const int64_t total = wl.off[wl.n];
+  // the first blocks warm L2 with the tables of the later stages
+  if (threadIdx.x == 0 && blockIdx.x < kPfIssuers && total > 0) {
+    int kt = pf.kt, N = pf.N, kn = pf.kn;
+    if (kt < 0) {  // device-planned job: take the plan of the first job
+      const Plan& P0 = jobs[wl.ids ? wl.ids[0] : 0].plan;
+      kt = P0.k_total;
+      N = P0.N;
+      kn = P0.k_need;
+    }
+    prefetch_late_tables(T, kt, N, kn, blockIdx.x, min((int)gridDim.x, kPfIssuers));
+  }
+  int cur_q = -1, cur_logN = -1;
+  const Job* cur_J = nullptr;
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
     const int ji = find_item(wl.off, wl.n, item);
     const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
@@ -409,14 +448,29 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_w(const Job* jobs, WorkLi
     const int groups = (rows + nw - 1) / nw;
     const int q = (int)(local / groups);
     const int row = (int)(local - (int64_t)q * groups) * nw + warp;
+    // stage this prime's twiddles (stride NT/N) and coset powers once per prime
+    const int logN = J->plan.logN;
+    if (q != cur_q || logN != cur_logN || J != cur_J) {
+      __syncthreads();
+      const int N = 1 << logN;
+      const int st = T.logNT - logN;
+      const uint32_t* twq = T.tw + (int64_t)q * (T.NT >> 1);
+      const uint32_t* cpq = T.cp + (int64_t)q * T.NT;
+      for (int t = threadIdx.x; t < (N >> 1); t += blockDim.x) s_tw[t] = __ldg(twq + ((int64_t)t << st));
+      for (int t = threadIdx.x; t < N; t += blockDim.x) s_cp[t] = __ldg(cpq + t);
+      __syncthreads();
+      cur_q = q;
+      cur_logN = logN;
+      cur_J = J;
+    }
     if (row >= rows) continue;
     switch (J->plan.logN) {
-      case 0: case 1: case 2: case 3: case 4: case 5: eval_row_warp<1>(J, q, row, T, sw); break;
-      case 6: eval_row_warp<2>(J, q, row, T, sw); break;
-      case 7: eval_row_warp<4>(J, q, row, T, sw); break;
-      case 8: eval_row_warp<8>(J, q, row, T, sw); break;
-      case 9: eval_row_warp<16>(J, q, row, T, sw); break;
-      default: eval_row_warp<32>(J, q, row, T, sw); break;
+      case 0: case 1: case 2: case 3: case 4: case 5: eval_row_warp<1>(J, q, row, T, sw, s_tw, s_cp); break;
+      case 6: eval_row_warp<2>(J, q, row, T, sw, s_tw, s_cp); break;
+      case 7: eval_row_warp<4>(J, q, row, T, sw, s_tw, s_cp); break;
+      case 8: eval_row_warp<8>(J, q, row, T, sw, s_tw, s_cp); break;
+      case 9: eval_row_warp<16>(J, q, row, T, sw, s_tw, s_cp); break;
+      default: eval_row_warp<32>(J, q, row, T, sw, s_tw, s_cp); break;
     }
   }
 }
@@ -589,7 +643,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
     const uint32_t* src = J->vals + ((int64_t)q << logN);
     for (int t = threadIdx.x; t < N; t += blockDim.x) sm[t] = src[t];
     __syncthreads();
-    dit_intt(sm, logN, T.itw + (int64_t)q * (T.NT >> 1), T.logNT, M);
+    // this prime's inverse twiddles at stride NT / N, staged after the values
+    uint32_t* sit = sm + N;
+    {
+      const int st = T.logNT - logN;
+      const uint32_t* itq = T.itw + (int64_t)q * (T.NT >> 1);
+      for (int t = threadIdx.x; t < (N >> 1); t += blockDim.x) sit[t] = __ldg(itq + ((int64_t)t << st));
+    }
+    __syncthreads();
+    dit_intt(sm, logN, sit, logN, M);
     const uint32_t* icp = T.icp + (int64_t)q * T.NT;
     const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
     uint32_t* dst = J->rmod + (int64_t)r * (D + 1);
@@ -959,6 +1021,109 @@ __device__ __forceinline__ void crt_coef_warp(const Job* J, const Plan& P, int i
   __syncwarp();
 }
 
+// Weighted-sum reconstruction of one coefficient (table order, k <= WK): with
+// P = p_0 ... p_{k-1}, M_i = P / p_i and y_i = M_i^-1 mod p_i,
+//   c = sum_i t_i M_i - q P,  t_i = r_i y_i mod p_i,  q = round(sum_i t_i / p_i),
+// where sum_i t_i / p_i is taken in Q62 fixed point (t_i floor(2^62 / p_i)); its error is
+// below k 2^-31, far inside the 1/4 margin that prod p > 4B leaves around an integer, so
+// q is exact.  c comes out directly in two's complement.  Msm holds M_k (k rows of L
+// limbs), sd receives t_i.
+__device__ __forceinline__ uint32_t ballot_sub(uint32_t x, uint32_t y, uint32_t& bin, int lane) {
+  const uint32_t d = x - y;
+  const uint32_t G = __ballot_sync(0xffffffffu, x < y);            // generates a borrow
+  const uint32_t Pm = __ballot_sync(0xffffffffu, d == 0u) & ~G;   // propagates one
+  const uint32_t X = G | Pm;
+  const uint64_t S = (uint64_t)X + G + bin;
+  const uint32_t C = (uint32_t)S ^ X ^ G;
+  bin = (uint32_t)(S >> 32);
+  return d - ((C >> lane) & 1u);
+}
+
+template <int S>
+__device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, int c,
+                                            const uint32_t* Xt, const uint32_t* Msm, int L,
+                                            const uint32_t* pq, const uint32_t* pinvq,
+                                            uint32_t* sd, const Tables& T) {
+  const int lane = threadIdx.x & 31;
+  const int k = P.k_need;
+  const int cap = J->cap_limbs;
+  const uint32_t* yk = T.ws_y + T.ws_yoff[k];
+  uint64_t flo = 0;
+  uint32_t fhi = 0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int q = 32 * s + lane;
+    if (q < k) {
+      const Mod M{pq[q], pinvq[q]};
+      const uint32_t t = mmul(Xt[q * kCrtTile + c], __ldg(yk + q), M);
+      sd[q] = t;
+      const uint64_t prod = (uint64_t)t * __ldg(T.q62 + q);
+      flo += prod;
+      fhi += (flo < prod) ? 1u : 0u;
+    }
+  }
+#pragma unroll
+  for (int x = 16; x > 0; x >>= 1) {
+    const uint64_t olo = __shfl_xor_sync(0xffffffffu, flo, x);
+    const uint32_t ohi = __shfl_xor_sync(0xffffffffu, fhi, x);
+    const uint64_t nlo = flo + olo;
+    fhi = fhi + ohi + (nlo < flo ? 1u : 0u);
+    flo = nlo;
+  }
+  // round(S / 2^62) with S = fhi 2^64 + flo
+  const uint64_t half = 1ull << 61;
+  const uint64_t rlo = flo + half;
+  const uint32_t rhi = fhi + (rlo < flo ? 1u : 0u);
+  const uint32_t qr = (rhi << 2) | (uint32_t)(rlo >> 62);
+  __syncwarp();
+  const uint32_t* Pk = T.pp + (int64_t)k * T.LPP;
+  uint32_t* out = J->out + (int64_t)i * cap;
+  uint32_t cin1 = 0, cin2 = 0, cq = 0, bsub = 0;
+  uint32_t bprev = 0, cprev1 = 0, cprev2 = 0, qhprev = 0;
+  for (int b0 = 0; b0 < cap; b0 += 32) {
+    const int l = b0 + lane;
+    uint64_t acc = 0;
+    uint32_t ah = 0;
+    if (b0 < L) {
+#pragma unroll 8
+      for (int q = 0; q < k; ++q) {
+        const uint32_t ml = l < L ? Msm[q * L + l] : 0u;
+        const uint64_t prod = (uint64_t)sd[q] * ml;
+        const uint64_t s = acc + prod;
+        ah += (s < acc) ? 1u : 0u;
+        acc = s;
+      }
+    }
+    // c' = sum_i t_i M_i from the three-word column sums
+    const uint32_t a = (uint32_t)acc, bw = (uint32_t)(acc >> 32), cw = ah;
+    uint32_t bin = __shfl_up_sync(0xffffffffu, bw, 1);
+    uint32_t cin_w = __shfl_up_sync(0xffffffffu, cw, 2);
+    const uint32_t c31 = __shfl_sync(0xffffffffu, cw, 31), c30 = __shfl_sync(0xffffffffu, cw, 30);
+    const uint32_t b31 = __shfl_sync(0xffffffffu, bw, 31);
+    if (lane == 0) {
+      bin = bprev;
+      cin_w = cprev2;
+    }
+    if (lane == 1) cin_w = cprev1;
+    uint32_t r = ballot_add(a, bin, cin1, lane);
+    r = ballot_add(r, cin_w, cin2, lane);
+    bprev = b31;
+    cprev2 = c30;
+    cprev1 = c31;
+    // q P (q < 2^13): limb l = lo(q P_l) + hi(q P_{l-1}) + carry
+    const uint64_t qp = (uint64_t)qr * (l < L && l < T.LPP ? Pk[l] : 0u);
+    uint32_t qh = __shfl_up_sync(0xffffffffu, (uint32_t)(qp >> 32), 1);
+    const uint32_t qh31 = __shfl_sync(0xffffffffu, (uint32_t)(qp >> 32), 31);
+    if (lane == 0) qh = qhprev;
+    qhprev = qh31;
+    const uint32_t qpl = ballot_add((uint32_t)qp, qh, cq, lane);
+    // c = c' - q P, two's complement
+    const uint32_t res = ballot_sub(r, qpl, bsub, lane);
+    if (l < cap) out[l] = res;
+  }
+  __syncwarp();
+}
+
 // Block: kCrtTile coefficients of one job, one warp each.  Shared memory (words):
 // [inv k*k][pp k*nlmax][X k*kCrtTile][p k][pinv k][sel k][digits kCrtTile*k][limbs kCrtTile*lmax]
 __global__ void __launch_bounds__(kCrtTile * 32) k_crt_w(const Job* jobs, WorkList wl, Tables T,
@@ -1007,23 +1172,40 @@ __global__ void __launch_bounds__(kCrtTile * 32) k_crt_w(const Job* jobs, WorkLi
     }
     __syncthreads();
     const bool table_order = (selq[k - 1] == (uint32_t)(k - 1));
+    // weighted-sum path for table-ordered jobs with tabulated k; Garner otherwise
+    const bool ws = table_order && k <= T.WK;
+    const int L = ws_len(k);
+    if (ws) {
+      const uint32_t* Mk = T.ws_m + T.ws_moff[k];
+      for (int j = warp; j < k; j += nthr / 32)
 #pragma unroll 4
-    for (int t = threadIdx.x; t < k * k; t += nthr) {
-      const int a = t / k, b = t - a * k;
-      sinv[t] = __ldg(T.ginv + (int64_t)selq[a] * Tg + selq[b]);
-    }
-    if (table_order) {
+        for (int l = lane; l < L; l += 32) sinv[j * L + l] = __ldg(Mk + (int64_t)j * L + l);
+    } else {
+      for (int a = warp; a < k; a += nthr / 32) {
+        const int64_t rowa = (int64_t)selq[a] * Tg;
 #pragma unroll 4
-      for (int t = threadIdx.x; t < k * nl; t += nthr) {
-        const int j = t / nl, l = t - j * nl;
-        spp[j * nl + l] = __ldg(T.pp + (int64_t)j * T.LPP + l);
+        for (int b = lane; b < k; b += 32) sinv[a * k + b] = __ldg(T.ginv + rowa + selq[b]);
       }
+      if (table_order)
+        for (int j = warp; j < k; j += nthr / 32)
+#pragma unroll 4
+          for (int l = lane; l < nl; l += 32) spp[j * nl + l] = __ldg(T.pp + (int64_t)j * T.LPP + l);
     }
     __syncthreads();
     for (int c = warp; c < ncoef; c += nthr / 32) {
       if (c >= nvalid) {  // above the degree bound
         uint32_t* out = J->out + (int64_t)(i0 + c) * cap;
         for (int l = lane; l < cap; l += 32) out[l] = 0u;
+        continue;
+      }
+      if (ws) {
+        switch ((k + 31) >> 5) {
+          case 1: crt_ws_warp<1>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
+          case 2: crt_ws_warp<2>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
+          case 3: crt_ws_warp<3>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
+          case 4: crt_ws_warp<4>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
+          default: crt_ws_warp<5>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
+        }
         continue;
       }
       switch ((k + 31) >> 5) {
@@ -1134,8 +1316,8 @@ void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const
 void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   k_eval<<<grid, kEvalThreads, smem, s>>>(jobs, wl, T);
 }
-void launch_eval_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
-  k_eval_w<<<grid, kEvalThreads, 0, s>>>(jobs, wl, T);
+void launch_eval_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T, PfHint pf) {
+  k_eval_w<<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf);
 }
 void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   k_intt_w<<<grid, kEvalThreads, 0, s>>>(jobs, wl, T);
@@ -1146,9 +1328,6 @@ void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkLis
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
                 Tables T, int kmax, int lmax, int staged) {
   k_crt<<<grid, threads, smem, s>>>(jobs, wl, T, kmax, lmax, staged);
-}
-void launch_prefetch(cudaStream_t s, Tables T, int kt, int logN, int kn, int lim) {
-  k_prefetch<<<1, 32, 0, s>>>(T, kt, logN, kn, lim);
 }
 void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T) {
   k_plan_single<<<1, kPlanThreads, 0, s>>>(J, dst, offs, T);

@@ -25,11 +25,15 @@ void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkLis
 void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_crt_w(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
                   int kmax, int lmax);
-void launch_eval_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+// sizes for the L2 prefetch the evaluation kernel issues (kt < 0: read the first job's plan)
+struct PfHint {
+  int kt, N, kn;
+};
+constexpr int kPfIssuers = 128;   // blocks that issue one prefetch chunk each
+void launch_eval_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T, PfHint pf);
 void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
                 Tables T, int kmax, int lmax, int staged);
-void launch_prefetch(cudaStream_t s, Tables T, int kt, int logN, int kn, int lim);
 void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T);
 int set_stage_smem_limits(int optin);
 // raise a kernel's dynamic shared memory limit to what the opt-in size leaves next to its

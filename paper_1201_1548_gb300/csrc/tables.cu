@@ -7,6 +7,7 @@
 // of up to 16384 points (g its smallest primitive root), which never contains 0, +1 or -1.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -196,6 +197,35 @@ __global__ void k_init_prefix(const PrimeConst* pc, int Tg, int LPP, uint32_t* p
   }
 }
 
+// weighted-sum tables: block k - 1 handles k primes, its threads take i < k:
+// M_k[i] = P_k / p_i by exact long division of the prefix product P_k (row k of pp) by p_i,
+// and y_k[i] = (prod_{j<k, j!=i} p_j)^-1 mod p_i in Montgomery form
+__global__ void k_init_ws(const PrimeConst* pc, const uint32_t* pp, int LPP, int WK,
+                          const int64_t* moff, const int32_t* yoff, uint32_t* wsm, uint32_t* wsy) {
+  for (int k = blockIdx.x + 1; k <= WK; k += gridDim.x) {
+    const int L = ws_len(k);
+    const uint32_t* Pk = pp + (size_t)k * LPP;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      const uint32_t p = pc[i].p;
+      uint32_t* dst = wsm + moff[k] + (int64_t)i * L;
+      uint64_t rem = 0;
+      for (int l = L - 1; l >= 0; --l) {
+        const uint64_t cur = (rem << 32) | (l < LPP ? Pk[l] : 0u);
+        dst[l] = (uint32_t)(cur / p);
+        rem = cur % p;
+      }
+      const Mod M{p, pc[i].pinv};
+      uint32_t prod = pc[i].one_m;
+      for (int j = 0; j < k; ++j) {
+        if (j == i) continue;
+        const uint32_t pj = pc[j].p % p;
+        prod = mmul(prod, redc((uint64_t)pj * pc[i].r2, p, pc[i].pinv), M);
+      }
+      wsy[yoff[k] + i] = minv(prod, pc[i].one_m, M);
+    }
+  }
+}
+
 static int cu_fail(cudaError_t e) { return e == cudaSuccess ? 0 : kErrCuda; }
 
 int DeviceTables::init(cudaStream_t s) {
@@ -217,8 +247,13 @@ int DeviceTables::init(cudaStream_t s) {
 
 void DeviceTables::release() {
   for (void* p : {(void*)pc, (void*)pw, (void*)mpw, (void*)lgp, (void*)tw, (void*)itw,
-                  (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp})
+                  (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp, (void*)ws_m,
+                  (void*)ws_y, (void*)ws_moff, (void*)ws_yoff, (void*)q62})
     if (p) cudaFree(p);
+  ws_m = ws_y = q62 = nullptr;
+  ws_moff = nullptr;
+  ws_yoff = nullptr;
+  WK = 0;
   pp = nullptr;
   LPP = 0;
   pc = nullptr;
@@ -276,11 +311,45 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   rc |= cu_fail(cudaGetLastError());
   k_init_prefix<<<1, 32, 0, s>>>(pc, newT, newLPP, npp);
   rc |= cu_fail(cudaGetLastError());
+  // weighted-sum reconstruction tables for k <= newWK
+  const int newWK = newT < kWsMaxK ? newT : kWsMaxK;
+  std::vector<int64_t> moff(newWK + 2, 0);
+  std::vector<int32_t> yoff(newWK + 2, 0);
+  for (int kk = 1; kk <= newWK; ++kk) {
+    moff[kk + 1] = moff[kk] + (int64_t)kk * ws_len(kk);
+    yoff[kk + 1] = yoff[kk] + kk;
+  }
+  uint32_t *nwsm = nullptr, *nwsy = nullptr, *nq62 = nullptr;
+  int64_t* nmoff = nullptr;
+  int32_t* nyoff = nullptr;
+  rc |= cu_fail(cudaMalloc(&nwsm, sizeof(uint32_t) * std::max<int64_t>(moff[newWK + 1], 1)));
+  rc |= cu_fail(cudaMalloc(&nwsy, sizeof(uint32_t) * std::max(yoff[newWK + 1], 1)));
+  rc |= cu_fail(cudaMalloc(&nmoff, sizeof(int64_t) * (newWK + 2)));
+  rc |= cu_fail(cudaMalloc(&nyoff, sizeof(int32_t) * (newWK + 2)));
+  rc |= cu_fail(cudaMalloc(&nq62, sizeof(uint32_t) * newT));
+  if (!rc) {
+    std::vector<uint32_t> q(newT);
+    for (int i = 0; i < newT; ++i) q[i] = (uint32_t)((1ull << 62) / H.p[i]);
+    rc |= cu_fail(cudaMemcpyAsync(nmoff, moff.data(), sizeof(int64_t) * (newWK + 2), cudaMemcpyHostToDevice, s));
+    rc |= cu_fail(cudaMemcpyAsync(nyoff, yoff.data(), sizeof(int32_t) * (newWK + 2), cudaMemcpyHostToDevice, s));
+    rc |= cu_fail(cudaMemcpyAsync(nq62, q.data(), sizeof(uint32_t) * newT, cudaMemcpyHostToDevice, s));
+    rc |= cu_fail(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    k_init_ws<<<newWK > 0 ? newWK : 1, 128, 0, s>>>(pc, npp, newLPP, newWK, nmoff, nyoff, nwsm, nwsy);
+    rc |= cu_fail(cudaGetLastError());
+  }
   rc |= cu_fail(cudaStreamSynchronize(s));
   cudaFree(omega);
   cudaFree(gi);
-  for (void* p : {(void*)tw, (void*)itw, (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp})
+  for (void* p : {(void*)tw, (void*)itw, (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp,
+                  (void*)ws_m, (void*)ws_y, (void*)ws_moff, (void*)ws_yoff, (void*)q62})
     if (p) cudaFree(p);
+  ws_m = nwsm;
+  ws_y = nwsy;
+  ws_moff = nmoff;
+  ws_yoff = nyoff;
+  q62 = nq62;
+  WK = newWK;
+  ws_m_words = std::max<int64_t>(moff[newWK + 1], 1);
   pp = npp;
   LPP = newLPP;
   tw = ntw;
@@ -310,6 +379,13 @@ Tables DeviceTables::view() const {
   t.ginv = ginv;
   t.pp = pp;
   t.LPP = LPP;
+  t.ws_m = ws_m;
+  t.ws_moff = ws_moff;
+  t.ws_y = ws_y;
+  t.ws_yoff = ws_yoff;
+  t.q62 = q62;
+  t.ws_m_words = ws_m_words;
+  t.WK = WK;
   t.T = T;
   t.Tt = Tt;
   t.NT = NT;

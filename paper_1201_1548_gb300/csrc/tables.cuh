@@ -27,6 +27,13 @@ struct DeviceTables {
   uint32_t* ginv = nullptr;
   uint32_t* pp = nullptr;
   int LPP = 0;
+  uint32_t* ws_m = nullptr;
+  int64_t* ws_moff = nullptr;
+  uint32_t* ws_y = nullptr;
+  int32_t* ws_yoff = nullptr;
+  uint32_t* q62 = nullptr;
+  int64_t ws_m_words = 0;
+  int WK = 0;
   int T = 0, Tt = 0, NT = 0, logNT = 0, Tg = 0;
   int generation = 0;
 

@@ -26,7 +26,7 @@ __device__ __forceinline__ void warp_dif(uint32_t (&v)[R], const uint32_t* tw, i
     for (int r = 0; r < R; ++r) {
       if (r & h) continue;
       const int m = r & (h - 1);                // j = 32 m + lane
-      const uint32_t w = __ldg(tw + ((32 * m + lane) << sh));
+      const uint32_t w = tw[(32 * m + lane) << sh];
       const uint32_t a = v[r], b = v[r + h];
       v[r] = madd(a, b, M.p);
       v[r + h] = mmul(msub(a, b, M.p), w, M);
@@ -39,7 +39,7 @@ __device__ __forceinline__ void warp_dif(uint32_t (&v)[R], const uint32_t* tw, i
     const int len = 1 << lg;
     const bool upper = (lane & len) != 0;
     const int sh = logNT - (lg + 1);
-    const uint32_t w = upper ? __ldg(tw + ((lane & (len - 1)) << sh)) : one_m;
+    const uint32_t w = upper ? tw[(lane & (len - 1)) << sh] : one_m;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t x = v[r];
@@ -60,7 +60,7 @@ __device__ __forceinline__ void warp_dit(uint32_t (&v)[R], const uint32_t* itw, 
     const int len = 1 << lg;
     const bool upper = (lane & len) != 0;
     const int sh = logNT - (lg + 1);
-    const uint32_t w = __ldg(itw + ((lane & (len - 1)) << sh));
+    const uint32_t w = itw[(lane & (len - 1)) << sh];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t x = v[r];
@@ -79,7 +79,7 @@ __device__ __forceinline__ void warp_dit(uint32_t (&v)[R], const uint32_t* itw, 
     for (int r = 0; r < R; ++r) {
       if (r & h) continue;
       const int m = r & (h - 1);
-      const uint32_t w = __ldg(itw + ((32 * m + lane) << sh));
+      const uint32_t w = itw[(32 * m + lane) << sh];
       const uint32_t a = v[r];
       const uint32_t b = mmul(v[r + h], w, M);
       v[r] = madd(a, b, M.p);
@@ -130,7 +130,7 @@ __device__ __forceinline__ void warp_dif_1024(uint32_t (&v)[32], uint32_t* sw, c
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       if (r & h) continue;
-      const uint32_t w = __ldg(tw + ((32 * (r & (h - 1)) + lane) << sh));
+      const uint32_t w = tw[(32 * (r & (h - 1)) + lane) << sh];
       const uint32_t a = v[r], b = v[r + h];
       v[r] = madd(a, b, M.p);
       v[r + h] = mmul(msub(a, b, M.p), w, M);
@@ -144,7 +144,7 @@ __device__ __forceinline__ void warp_dif_1024(uint32_t (&v)[32], uint32_t* sw, c
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       if (r & len) continue;
-      const uint32_t w = __ldg(tw + ((r & (len - 1)) << sh));
+      const uint32_t w = tw[(r & (len - 1)) << sh];
       const uint32_t a = v[r], b = v[r + len];
       v[r] = madd(a, b, M.p);
       v[r + len] = mmul(msub(a, b, M.p), w, M);
@@ -165,7 +165,7 @@ __device__ __forceinline__ void warp_dit_1024(uint32_t (&v)[32], uint32_t* sw, c
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       if (r & len) continue;
-      const uint32_t w = __ldg(itw + ((r & (len - 1)) << sh));
+      const uint32_t w = itw[(r & (len - 1)) << sh];
       const uint32_t a = v[r];
       const uint32_t b = mmul(v[r + len], w, M);
       v[r] = madd(a, b, M.p);
@@ -180,7 +180,7 @@ __device__ __forceinline__ void warp_dit_1024(uint32_t (&v)[32], uint32_t* sw, c
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       if (r & h) continue;
-      const uint32_t w = __ldg(itw + ((32 * (r & (h - 1)) + lane) << sh));
+      const uint32_t w = itw[(32 * (r & (h - 1)) + lane) << sh];
       const uint32_t a = v[r];
       const uint32_t b = mmul(v[r + h], w, M);
       v[r] = madd(a, b, M.p);
