@@ -211,8 +211,22 @@ int bs_gcd_modp(bs_ctx *ctx, const uint32_t *a, int da, const uint32_t *b, int d
                 uint32_t p, uint32_t *g, int *dg);
 
 /* Square-free part R* = pp(R / gcd(R, R')) of a non-zero R in Z[x], primitive with a
- * positive leading coefficient.  Host buffers.  out->c NULL: size query (upper bounds).
- * Returns BS_ERR_ZERO for R = 0. */
+ * positive leading coefficient (Sec. 2.1: the projection's square-free factorisation
+ * starts from gcd(R, R'); Sec. 5.1: gcds in Z[x] by the modular route).
+ *
+ * r: host buffer, r->c[i * r->limbs + l] is limb l of the coefficient of x^i (two's
+ * complement, little-endian limbs); leading zero coefficients are ignored.
+ * out: host buffer owned by the caller.  With out->c == NULL the call only writes upper
+ * bounds to out->deg and out->limbs and returns BS_OK.  Otherwise out->deg and
+ * out->limbs give the capacity (out->deg must be at least the trimmed degree of r); on
+ * success out->deg is set to deg R* and the coefficients are written with out->limbs
+ * limbs each (sign-extended; positions above deg R* up to the capacity are zeroed).
+ *
+ * The work runs on the context's stream; the call waits for it.  Errors: BS_ERR_ARG,
+ * BS_ERR_ZERO for R = 0, BS_ERR_RANGE when 3 (deg r + 1) words exceed one block's shared
+ * memory or the coefficient bound exceeds the prime table, BS_ERR_CAPACITY when the
+ * output capacity is too small, BS_ERR_UNLUCKY when fewer than the needed primes agree on
+ * the minimal gcd degree. */
 int bs_squarefree_part(bs_ctx *ctx, const bs_upoly *r, bs_upoly *out);
 
 /* ---------------------------------------------------------------------------------
