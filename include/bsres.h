@@ -229,6 +229,26 @@ int bs_gcd_modp(bs_ctx *ctx, const uint32_t *a, int da, const uint32_t *b, int d
  * the minimal gcd degree. */
 int bs_squarefree_part(bs_ctx *ctx, const bs_upoly *r, bs_upoly *out);
 
+/* gcd of a and b in Z[x] (Sec. 5.1 "Computing gcds in Z[x]"): the primitive gcd times
+ * the gcd of the contents, with a positive leading coefficient; gcd(0, 0) is the zero
+ * polynomial (out->deg = -1) and gcd(0, u) is u with a positive leading coefficient.
+ * Primes dividing lc(a) lc(b) are skipped and only primes with the minimal gcd degree are
+ * used (Brown's rule); the images are lifted by Chinese remaindering up to Mignotte's
+ * bound 2^deg ||a||_2 for the input a of smaller norm.
+ *
+ * a, b, out: host buffers in the layout of bs_squarefree_part; out->c == NULL is a size
+ * query (upper bounds).  The call waits for the device.  Errors: BS_ERR_ARG,
+ * BS_ERR_RANGE (deg a + deg b + 3 words above one block's shared memory, or a bound above
+ * the prime table), BS_ERR_CAPACITY, BS_ERR_UNLUCKY. */
+int bs_gcd_z(bs_ctx *ctx, const bs_upoly *a, const bs_upoly *b, bs_upoly *out);
+
+/* n modular gcd jobs in one pass of launches: kind[j] = 0 computes gcd(a[j], b[j]) as
+ * bs_gcd_z, kind[j] = 1 the square-free part of a[j] as bs_squarefree_part (b may be
+ * NULL when every kind is 1).  If any out[j].c is NULL, every out[j] receives its upper
+ * bounds and nothing runs.  Returns the first failing job's status. */
+int bs_modgcd_batch(bs_ctx *ctx, int n, const int *kind, const bs_upoly *a, const bs_upoly *b,
+                    bs_upoly *out);
+
 /* ---------------------------------------------------------------------------------
  * Measurement
  * ------------------------------------------------------------------------------ */

@@ -17,7 +17,7 @@ EXPORTED_SYMBOLS = [
     "bs_last_stats", "bs_resultant_bounds", "bs_resultant", "bs_resultant_device",
     "bs_device_status", "bs_resultant_batch", "bs_uni_resultant_modp", "bs_prime_table",
     "bs_gcd_modp", "bs_squarefree_part", "bs_plan", "bs_alu_probe", "bs_profile",
-    "bs_stage_times", "bs_resultant_device_noalloc",
+    "bs_stage_times", "bs_resultant_device_noalloc", "bs_gcd_z", "bs_modgcd_batch",
 ]
 
 
@@ -287,6 +287,35 @@ class Context:
         self._check(self.lib.bs_gcd_modp(self.h, A.ctypes.data, da, B.ctypes.data, db,
                                          C.c_uint32(p), G.ctypes.data, C.byref(dg)))
         return [int(x) for x in G[: dg.value + 1]]
+
+    def gcd_z(self, a, b):
+        """gcd in Z[x] of ascending integer coefficient lists (positive leading coefficient)."""
+        return self.modgcd_batch([(0, a, b)])[0]
+
+    def modgcd_batch(self, jobs):
+        """jobs: list of (kind, a, b); kind 0 gcd(a, b), kind 1 square-free part of a."""
+        n = len(jobs)
+        kinds = (C.c_int * n)(*[int(k) for k, _, _ in jobs])
+        keep = []
+        A = (_Upoly * n)()
+        Bv = (_Upoly * n)()
+        for j, (k, a, b) in enumerate(jobs):
+            for arr_list, poly in ((A, a), (Bv, b if k == 0 else [])):
+                arr, L = ints_to_limbs(poly)
+                keep.append(arr)
+                arr_list[j] = _Upoly(len(poly) - 1, L, arr.ctypes.data)
+        out = (_Upoly * n)()
+        for j in range(n):
+            out[j] = _Upoly(0, 0, None)
+        self._check(self.lib.bs_modgcd_batch(self.h, n, kinds, A, Bv, out))
+        bufs = []
+        for j in range(n):
+            buf = np.zeros((max(out[j].deg, 0) + 1) * max(out[j].limbs, 1), dtype=np.uint32)
+            bufs.append(buf)
+            out[j] = _Upoly(out[j].deg, max(out[j].limbs, 1), buf.ctypes.data)
+        self._check(self.lib.bs_modgcd_batch(self.h, n, kinds, A, Bv, out))
+        return [limbs_to_ints(bufs[j], out[j].deg + 1, out[j].limbs) if out[j].deg >= 0 else []
+                for j in range(n)]
 
     def squarefree_part(self, r):
         arr, L = ints_to_limbs(r)

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/bsres.h"
+#include "batch.cuh"
 #include "common.cuh"
 #include "ctx.cuh"
 #include "resultant_kernels.cuh"
@@ -94,7 +95,7 @@ extern "C" int bs_init(int device, size_t mem_budget, bs_ctx** out) {
     return BS_ERR_CUDA;
   }
   ctx->stream = ctx->own_stream;
-  int rc = ctx->tabs.init(ctx->stream);
+  int rc = ctx->tabs->init(ctx->stream);
   if (rc) {
     bs_free(ctx);
     return rc;
@@ -123,7 +124,7 @@ extern "C" void bs_free(bs_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
   if (ctx->stream && ctx->stream != ctx->own_stream) cudaStreamSynchronize(ctx->stream);
-  ctx->tabs.release();
+  ctx->tabs->release();
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->dev_ws) cudaFree(ctx->dev_ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -275,164 +276,144 @@ static bool coeff_is_zero(const uint32_t* s, int limbs) {
 // ------------------------------------------------------------------------------------
 // batch of host-resident jobs (also serves bs_resultant with n = 1)
 // ------------------------------------------------------------------------------------
-int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int var,
-                   bs_upoly* out, bool use_graph) {
-  if (!ctx || n < 0 || !out || (n && (!f || !g)) || (var != 0 && var != 1))
-    return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
-  if (n == 0) return BS_OK;
-  cudaSetDevice(ctx->device);
+namespace bs {
+
+int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int var, HostBatch* hb) {
+  HostBatch& B = *hb;
+  B = HostBatch{};
+  B.n = n;
+  B.var = var;
   const HostPrimes& H = host_primes();
   const int T = (int)H.p.size();
-  std::vector<Plan> plans(n);
-  bool query = false;
+  B.plans.resize(n);
   for (int i = 0; i < n; ++i) {
     int rc = check_bipoly(ctx, f + i, "f");
     if (rc) return rc;
     rc = check_bipoly(ctx, g + i, "g");
     if (rc) return rc;
-    plans[i] = plan_host(grid_of(f + i), grid_of(g + i), var, H.lg_prefix.data(), T);
-    if (plans[i].status)
-      return ctx_fail(ctx, plans[i].status, "planning failed for job " + std::to_string(i));
-    if (!out[i].c) query = true;
+    B.plans[i] = plan_host(grid_of(f + i), grid_of(g + i), var, H.lg_prefix.data(), T);
+    if (B.plans[i].status)
+      return ctx_fail(ctx, B.plans[i].status, "planning failed for job " + std::to_string(i));
   }
-  if (query) {
-    for (int i = 0; i < n; ++i) {
-      const Plan& P = plans[i];
-      out[i].deg = P.trivial == 1 ? -1 : P.D;
-      out[i].limbs = P.out_limbs;
-    }
-    return BS_OK;
-  }
-  for (int i = 0; i < n; ++i)
-    if (out[i].limbs < 1 || out[i].deg < -1)
-      return ctx_fail(ctx, BS_ERR_ARG, "bad output capacity");
-  // tables
-  int needT = 1, needLog = 0, kmax = 1, lmax = 1, maxN = 1, class_mask = 0;
-  for (const Plan& P : plans) {
+  for (const Plan& P : B.plans) {
     if (P.trivial) continue;
-    needT = std::max(needT, P.k_total);
-    needLog = std::max(needLog, P.logN);
-    kmax = std::max(kmax, P.k_need);
-    lmax = std::max(lmax, P.out_limbs + 1);
-    maxN = std::max(maxN, P.N);
+    B.needT = std::max(B.needT, P.k_total);
+    B.needLog = std::max(B.needLog, P.logN);
+    B.kmax = std::max(B.kmax, P.k_need);
+    B.lmax = std::max(B.lmax, P.out_limbs + 1);
+    B.maxN = std::max(B.maxN, P.N);
     const int c = uni_class_of(std::max(P.me, P.ne) + 1);
     if (c < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
-    class_mask |= 1 << c;
+    ++B.cls_count[c];
   }
-  int rc = ctx->tabs.ensure(needT, needLog, ctx->stream);
-  if (rc) return ctx_fail(ctx, rc, "table setup failed");
-  // ---- layout: [upload | compute | download]
-  std::vector<int64_t> in_f(n), in_g(n);  // limb counts
-  size_t in_words = 0;
+  B.in_f.resize(n);
+  B.in_g.resize(n);
+  size_t in_words = 0, pstat_words = 0;
   for (int i = 0; i < n; ++i) {
-    in_f[i] = (int64_t)(f[i].deg_y + 1) * (f[i].deg_x + 1) * f[i].limbs;
-    in_g[i] = (int64_t)(g[i].deg_y + 1) * (g[i].deg_x + 1) * g[i].limbs;
-    in_words += in_f[i] + in_g[i];
+    B.in_f[i] = (int64_t)(f[i].deg_y + 1) * (f[i].deg_x + 1) * f[i].limbs;
+    B.in_g[i] = (int64_t)(g[i].deg_y + 1) * (g[i].deg_x + 1) * g[i].limbs;
+    in_words += B.in_f[i] + B.in_g[i];
+    if (!B.plans[i].trivial) pstat_words += B.plans[i].k_total;
   }
-  int cls_count[kNumUniClasses] = {0};
-  for (int i = 0; i < n; ++i)
-    if (!plans[i].trivial) ++cls_count[uni_class_of(std::max(plans[i].me, plans[i].ne) + 1)];
-  size_t pstat_words = 0;
-  for (const Plan& P : plans)
-    if (!P.trivial) pstat_words += P.k_total;
   Layout up;
-  const size_t o_jobs = up.take(sizeof(Job) * n);
-  const size_t o_eoff = up.take(sizeof(int64_t) * (n + 1));
-  const size_t o_ioff = up.take(sizeof(int64_t) * (n + 1));
-  const size_t o_ewoff = up.take(sizeof(int64_t) * (n + 1));
-  const size_t o_iwoff = up.take(sizeof(int64_t) * (n + 1));
-  const size_t o_coff = up.take(sizeof(int64_t) * (n + 1));
-  size_t o_cids[kNumUniClasses], o_coffs[kNumUniClasses];
+  B.o_jobs = up.take(sizeof(Job) * n);
+  B.o_eoff = up.take(sizeof(int64_t) * (n + 1));
+  B.o_ioff = up.take(sizeof(int64_t) * (n + 1));
+  B.o_ewoff = up.take(sizeof(int64_t) * (n + 1));
+  B.o_iwoff = up.take(sizeof(int64_t) * (n + 1));
+  B.o_coff = up.take(sizeof(int64_t) * (n + 1));
   for (int c = 0; c < kNumUniClasses; ++c) {
-    o_cids[c] = up.take(sizeof(int32_t) * std::max(cls_count[c], 1));
-    o_coffs[c] = up.take(sizeof(int64_t) * (cls_count[c] + 1));
+    B.o_cids[c] = up.take(sizeof(int32_t) * std::max(B.cls_count[c], 1));
+    B.o_coffs[c] = up.take(sizeof(int64_t) * (B.cls_count[c] + 1));
   }
-  const size_t o_status = up.take(sizeof(int32_t) * 4);
-  const size_t o_pstat = up.take(sizeof(int32_t) * std::max<size_t>(pstat_words, 1));
-  const size_t o_in = up.take(sizeof(uint32_t) * std::max<size_t>(in_words, 1));
-  const size_t up_bytes = up.used;
+  B.o_status = up.take(sizeof(int32_t) * 4);
+  B.o_pstat = up.take(sizeof(int32_t) * std::max<size_t>(pstat_words, 1));
+  B.o_in = up.take(sizeof(uint32_t) * std::max<size_t>(in_words, 1));
+  B.up_bytes = up.used;
   Layout cmp;
-  cmp.used = up_bytes;
-  std::vector<size_t> o_ev(n), o_vals(n), o_rmod(n), o_sel(n);
+  cmp.used = B.up_bytes;
+  B.o_ev.assign(n, 0);
+  B.o_vals.assign(n, 0);
+  B.o_rmod.assign(n, 0);
+  B.o_sel.assign(n, 0);
   for (int i = 0; i < n; ++i) {
-    const Plan& P = plans[i];
+    const Plan& P = B.plans[i];
     if (P.trivial) continue;
     const int rows = (P.me + 1) + (P.ne + 1);
-    o_ev[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_total * rows * P.N);
-    o_vals[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_total * P.N);
-    o_rmod[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_need * (P.D + 1));
-    o_sel[i] = cmp.take(sizeof(int32_t) * P.k_need);
+    B.o_ev[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_total * rows * P.N);
+    B.o_vals[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_total * P.N);
+    B.o_rmod[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_need * (P.D + 1));
+    B.o_sel[i] = cmp.take(sizeof(int32_t) * P.k_need);
   }
   Layout dn;
   dn.used = cmp.used;
-  const size_t dn_start = dn.take(0);
-  std::vector<size_t> o_out(n);
+  B.dn_start = dn.take(0);
+  B.o_out.assign(n, 0);
   for (int i = 0; i < n; ++i) {
-    const Plan& P = plans[i];
+    const Plan& P = B.plans[i];
     const int cap_deg = std::max(P.D, 0);
-    o_out[i] = dn.take(sizeof(uint32_t) * (size_t)(cap_deg + 1) * P.out_limbs);
+    B.o_out[i] = dn.take(sizeof(uint32_t) * (size_t)(cap_deg + 1) * P.out_limbs);
   }
-  const size_t o_status_dn = dn.take(sizeof(int32_t) * 4);
-  const size_t total = dn.used;
-  const size_t dn_bytes = total - dn_start;
-  rc = ensure_workspace(ctx, total);
-  if (rc) return rc;
-  rc = ensure_pinned(ctx, up_bytes, dn_bytes);
-  if (rc) return rc;
-  char* base = (char*)ctx->ws;
-  char* hu = (char*)ctx->h_up;
-  std::memset(hu, 0, up_bytes);
-  // staged inputs
-  {
-    uint32_t* dst = (uint32_t*)(hu + o_in);
+  B.o_status_dn = dn.take(sizeof(int32_t) * 4);
+  B.total = dn.used;
+  B.dn_bytes = B.total - B.dn_start;
+  return 0;
+}
+
+int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly* g, char* base,
+                 char* hu, char* hd, bool use_graph) {
+  const int n = B.n;
+  std::memset(hu, 0, B.up_bytes);
+  {  // staged inputs
+    uint32_t* dst = (uint32_t*)(hu + B.o_in);
     for (int i = 0; i < n; ++i) {
-      std::memcpy(dst, f[i].c, sizeof(uint32_t) * in_f[i]);
-      dst += in_f[i];
-      std::memcpy(dst, g[i].c, sizeof(uint32_t) * in_g[i]);
-      dst += in_g[i];
+      std::memcpy(dst, f[i].c, sizeof(uint32_t) * B.in_f[i]);
+      dst += B.in_f[i];
+      std::memcpy(dst, g[i].c, sizeof(uint32_t) * B.in_g[i]);
+      dst += B.in_g[i];
     }
   }
-  Job* hj = (Job*)(hu + o_jobs);
-  int64_t* eoff = (int64_t*)(hu + o_eoff);
-  int64_t* ioff = (int64_t*)(hu + o_ioff);
-  int64_t* ewoff = (int64_t*)(hu + o_ewoff);
-  int64_t* iwoff = (int64_t*)(hu + o_iwoff);
-  int64_t* coff = (int64_t*)(hu + o_coff);
+  Job* hj = (Job*)(hu + B.o_jobs);
+  int64_t* eoff = (int64_t*)(hu + B.o_eoff);
+  int64_t* ioff = (int64_t*)(hu + B.o_ioff);
+  int64_t* ewoff = (int64_t*)(hu + B.o_ewoff);
+  int64_t* iwoff = (int64_t*)(hu + B.o_iwoff);
+  int64_t* coff = (int64_t*)(hu + B.o_coff);
   int32_t* cids[kNumUniClasses];
   int64_t* coffs[kNumUniClasses];
   int cfill[kNumUniClasses] = {0};
   for (int c = 0; c < kNumUniClasses; ++c) {
-    cids[c] = (int32_t*)(hu + o_cids[c]);
-    coffs[c] = (int64_t*)(hu + o_coffs[c]);
+    cids[c] = (int32_t*)(hu + B.o_cids[c]);
+    coffs[c] = (int64_t*)(hu + B.o_coffs[c]);
     coffs[c][0] = 0;
   }
   eoff[0] = ioff[0] = coff[0] = ewoff[0] = iwoff[0] = 0;
   size_t in_pos = 0, ps_pos = 0;
-  int64_t instances = 0, mulmods = 0, k_need_sum = 0, k_total_sum = 0;
-  int maxpts = 0, maxprimes = 0;
+  B.instances = B.mulmods = B.k_need_sum = B.k_total_sum = 0;
+  B.maxpts = B.maxprimes = 0;
   for (int i = 0; i < n; ++i) {
-    const Plan& P = plans[i];
+    const Plan& P = B.plans[i];
     Job J;
     std::memset(&J, 0, sizeof(J));
-    J.f = Grid{(const uint32_t*)(base + o_in) + in_pos, f[i].deg_x, f[i].deg_y, f[i].limbs};
-    in_pos += in_f[i];
-    J.g = Grid{(const uint32_t*)(base + o_in) + in_pos, g[i].deg_x, g[i].deg_y, g[i].limbs};
-    in_pos += in_g[i];
-    J.var = var;
+    J.f = Grid{(const uint32_t*)(base + B.o_in) + in_pos, f[i].deg_x, f[i].deg_y, f[i].limbs};
+    in_pos += B.in_f[i];
+    J.g = Grid{(const uint32_t*)(base + B.o_in) + in_pos, g[i].deg_x, g[i].deg_y, g[i].limbs};
+    in_pos += B.in_g[i];
+    J.var = B.var;
     J.plan = P;
     J.cap_deg = std::max(P.D, 0);
     J.cap_limbs = P.out_limbs;
-    J.out = (uint32_t*)(base + o_out[i]);
-    J.status = (int32_t*)(base + o_status);
-    J.rejected = (int32_t*)(base + o_status) + 1;
+    J.out = (uint32_t*)(base + B.o_out[i]);
+    J.status = (int32_t*)(base + B.o_status);
+    J.rejected = (int32_t*)(base + B.o_status) + 1;
     int64_t ne = 0, ni = 0, nu = 0, new_ = 0, niw = 0;
     if (!P.trivial) {
       J.rows = (P.me + 1) + (P.ne + 1);
-      J.ev = (uint32_t*)(base + o_ev[i]);
-      J.vals = (uint32_t*)(base + o_vals[i]);
-      J.rmod = (uint32_t*)(base + o_rmod[i]);
-      J.sel = (int32_t*)(base + o_sel[i]);
-      J.pstat = (int32_t*)(base + o_pstat) + ps_pos;
+      J.ev = (uint32_t*)(base + B.o_ev[i]);
+      J.vals = (uint32_t*)(base + B.o_vals[i]);
+      J.rmod = (uint32_t*)(base + B.o_rmod[i]);
+      J.sel = (int32_t*)(base + B.o_sel[i]);
+      J.pstat = (int32_t*)(base + B.o_pstat) + ps_pos;
       ps_pos += P.k_total;
       if (P.logN <= kWarpLogNMax)
         new_ = (int64_t)P.k_total * ((J.rows + 7) / 8);
@@ -444,12 +425,12 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
       cids[c][cfill[c]] = i;
       coffs[c][cfill[c] + 1] = coffs[c][cfill[c]] + nu;
       ++cfill[c];
-      instances += (int64_t)P.k_total << P.logN;
-      mulmods += ((int64_t)P.k_total << P.logN) * (int64_t)P.me * P.ne;
-      k_need_sum += P.k_need;
-      k_total_sum += P.k_total;
-      maxpts = std::max(maxpts, P.N);
-      maxprimes = std::max(maxprimes, P.k_total);
+      B.instances += (int64_t)P.k_total << P.logN;
+      B.mulmods += ((int64_t)P.k_total << P.logN) * (int64_t)P.me * P.ne;
+      B.k_need_sum += P.k_need;
+      B.k_total_sum += P.k_total;
+      B.maxpts = std::max(B.maxpts, P.N);
+      B.maxprimes = std::max(B.maxprimes, P.k_total);
     }
     hj[i] = J;
     eoff[i + 1] = eoff[i] + ne;
@@ -459,60 +440,57 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
     coff[i + 1] = coff[i] + (J.cap_deg + kCrtTile) / kCrtTile;
   }
   cudaStream_t s = ctx->stream;
-  rc = ctx_cuda(ctx, cudaMemcpyAsync(base, hu, up_bytes, cudaMemcpyHostToDevice, s), "upload");
+  int rc = ctx_cuda(ctx, cudaMemcpyAsync(base, hu, B.up_bytes, cudaMemcpyHostToDevice, s), "upload");
   if (rc) return rc;
   // ---- device stages
-  const Tables Tv = ctx->tabs.view();
-  const Job* dj = (const Job*)(base + o_jobs);
+  const Tables Tv = ctx->tabs->view();
   StageLaunch L;
-  L.jobs = dj;
-  L.eval = WorkList{nullptr, (const int64_t*)(base + o_eoff), n};
-  L.intt = WorkList{nullptr, (const int64_t*)(base + o_ioff), n};
-  L.crt = WorkList{nullptr, (const int64_t*)(base + o_coff), n};
+  L.jobs = (const Job*)(base + B.o_jobs);
+  L.eval = WorkList{nullptr, (const int64_t*)(base + B.o_eoff), n};
+  L.intt = WorkList{nullptr, (const int64_t*)(base + B.o_ioff), n};
+  L.crt = WorkList{nullptr, (const int64_t*)(base + B.o_coff), n};
   for (int c = 0; c < kNumUniClasses; ++c) {
-    L.uni[c] = WorkList{(const int32_t*)(base + o_cids[c]), (const int64_t*)(base + o_coffs[c]),
-                        cls_count[c]};
-    L.uni_items[c] = cls_count[c] ? coffs[c][cls_count[c]] : 0;
+    L.uni[c] = WorkList{(const int32_t*)(base + B.o_cids[c]), (const int64_t*)(base + B.o_coffs[c]),
+                        B.cls_count[c]};
+    L.uni_items[c] = B.cls_count[c] ? coffs[c][B.cls_count[c]] : 0;
   }
-  L.eval_w = WorkList{nullptr, (const int64_t*)(base + o_ewoff), n};
-  L.intt_w = WorkList{nullptr, (const int64_t*)(base + o_iwoff), n};
+  L.eval_w = WorkList{nullptr, (const int64_t*)(base + B.o_ewoff), n};
+  L.intt_w = WorkList{nullptr, (const int64_t*)(base + B.o_iwoff), n};
   L.eval_items = eoff[n];
   L.intt_items = ioff[n];
   L.eval_w_items = ewoff[n];
   L.intt_w_items = iwoff[n];
   L.crt_items = coff[n];
-  L.maxN = maxN;
-  L.kmax = kmax;
-  L.lmax = lmax;
-  L.kt_max = needT;
-  L.logN_max = needLog;
+  L.maxN = B.maxN;
+  L.kmax = B.kmax;
+  L.lmax = B.lmax;
+  L.kt_max = B.needT;
+  L.logN_max = B.needLog;
   rc = launch_stages(ctx, L, Tv, use_graph);
   if (rc) return rc;
-  rc = ctx_cuda(ctx, cudaMemcpyAsync(base + o_status_dn, base + o_status, sizeof(int32_t) * 4,
+  rc = ctx_cuda(ctx, cudaMemcpyAsync(base + B.o_status_dn, base + B.o_status, sizeof(int32_t) * 4,
                                      cudaMemcpyDeviceToDevice, s),
                 "status copy");
   if (rc) return rc;
-  rc = ctx_cuda(ctx, cudaMemcpyAsync(ctx->h_down, base + dn_start, dn_bytes, cudaMemcpyDeviceToHost, s),
-                "download");
-  if (rc) return rc;
-  rc = ctx_cuda(ctx, cudaStreamSynchronize(s), "stream");
-  if (rc) return rc;
-  const char* hd = (const char*)ctx->h_down;
-  const int32_t* st = (const int32_t*)(hd + (o_status_dn - dn_start));
+  return ctx_cuda(ctx, cudaMemcpyAsync(hd, base + B.dn_start, B.dn_bytes, cudaMemcpyDeviceToHost, s),
+                  "download");
+}
+
+int batch_finish(bs_ctx* ctx, const HostBatch& B, const char* hd, bs_upoly* out) {
+  const int32_t* st = (const int32_t*)(hd + (B.o_status_dn - B.dn_start));
   ctx->stats = bs_stats{};
-  ctx->stats.jobs = n;
-  ctx->stats.primes_needed = k_need_sum;
-  ctx->stats.primes_evaluated = k_total_sum;
+  ctx->stats.jobs = B.n;
+  ctx->stats.primes_needed = B.k_need_sum;
+  ctx->stats.primes_evaluated = B.k_total_sum;
   ctx->stats.primes_rejected = st[1];
-  ctx->stats.instances = instances;
-  ctx->stats.mulmods_alg = mulmods;
-  ctx->stats.max_points = maxpts;
-  ctx->stats.max_primes = maxprimes;
+  ctx->stats.instances = B.instances;
+  ctx->stats.mulmods_alg = B.mulmods;
+  ctx->stats.max_points = B.maxpts;
+  ctx->stats.max_primes = B.maxprimes;
   if (st[0]) return ctx_fail(ctx, st[0], "device stage reported a failure");
-  // ---- format outputs
-  for (int i = 0; i < n; ++i) {
-    const Plan& P = plans[i];
-    const uint32_t* src = (const uint32_t*)(hd + (o_out[i] - dn_start));
+  for (int i = 0; i < B.n; ++i) {
+    const Plan& P = B.plans[i];
+    const uint32_t* src = (const uint32_t*)(hd + (B.o_out[i] - B.dn_start));
     const int ncoef = std::max(P.D, 0) + 1;
     int deg = -1;
     for (int c = ncoef - 1; c >= 0; --c)
@@ -529,6 +507,44 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
     out[i].deg = deg;
   }
   return BS_OK;
+}
+
+}  // namespace bs
+
+int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int var,
+                   bs_upoly* out, bool use_graph) {
+  if (!ctx || n < 0 || !out || (n && (!f || !g)) || (var != 0 && var != 1))
+    return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
+  if (n == 0) return BS_OK;
+  cudaSetDevice(ctx->device);
+  HostBatch B;
+  int rc = batch_plan(ctx, n, f, g, var, &B);
+  if (rc) return rc;
+  bool query = false;
+  for (int i = 0; i < n; ++i)
+    if (!out[i].c) query = true;
+  if (query) {
+    for (int i = 0; i < n; ++i) {
+      const Plan& P = B.plans[i];
+      out[i].deg = P.trivial == 1 ? -1 : P.D;
+      out[i].limbs = P.out_limbs;
+    }
+    return BS_OK;
+  }
+  for (int i = 0; i < n; ++i)
+    if (out[i].limbs < 1 || out[i].deg < -1)
+      return ctx_fail(ctx, BS_ERR_ARG, "bad output capacity");
+  rc = ctx->tabs->ensure(B.needT, B.needLog, ctx->stream);
+  if (rc) return ctx_fail(ctx, rc, "table setup failed");
+  rc = ensure_workspace(ctx, B.total);
+  if (rc) return rc;
+  rc = ensure_pinned(ctx, B.up_bytes, B.dn_bytes);
+  if (rc) return rc;
+  rc = batch_launch(ctx, B, f, g, (char*)ctx->ws, (char*)ctx->h_up, (char*)ctx->h_down, use_graph);
+  if (rc) return rc;
+  rc = ctx_cuda(ctx, cudaStreamSynchronize(ctx->stream), "stream");
+  if (rc) return rc;
+  return batch_finish(ctx, B, (const char*)ctx->h_down, out);
 }
 
 extern "C" int bs_resultant(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var,
@@ -562,7 +578,7 @@ extern "C" int bs_resultant_device(bs_ctx* ctx, const bs_bipoly* f, const bs_bip
     return ctx_fail(ctx, BS_ERR_CAPACITY, "output capacity below bs_resultant_bounds()");
   const int cls = uni_class_of(mb.len);
   if (cls < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
-  rc = ctx->tabs.ensure(mb.k_total, mb.logN, ctx->stream);
+  rc = ctx->tabs->ensure(mb.k_total, mb.logN, ctx->stream);
   if (rc) return ctx_fail(ctx, rc, "table setup failed");
   const int N = 1 << mb.logN;
   Layout lay;
@@ -670,7 +686,7 @@ extern "C" int bs_uni_resultant_modp(bs_ctx* ctx, int n, const uint32_t* p, cons
   rc |= ctx_cuda(ctx, cudaMemcpyAsync(base + o_a, a, sizeof(uint32_t) * (size_t)n * lda, cudaMemcpyHostToDevice, s), "h2d");
   rc |= ctx_cuda(ctx, cudaMemcpyAsync(base + o_b, b, sizeof(uint32_t) * (size_t)n * ldb, cudaMemcpyHostToDevice, s), "h2d");
   if (rc) return rc;
-  const Tables Tv = ctx->tabs.view();
+  const Tables Tv = ctx->tabs->view();
   launch_uni_direct(cls, n, s, (const int32_t*)(base + o_idx), (const uint32_t*)(base + o_a), da, lda,
                     (const uint32_t*)(base + o_b), db, ldb, (uint32_t*)(base + o_r), Tv);
   uint32_t* dR = (uint32_t*)(base + o_r);

@@ -16,7 +16,10 @@ struct bs_ctx {
   size_t budget = 0;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
-  bs::DeviceTables tabs;
+  bs::DeviceTables own_tabs;
+  bs::DeviceTables* tabs = &own_tabs;  // serving slots point at their parent's tables
+  bs_ctx* parent = nullptr;            // set on the serving slots' contexts
+  struct bs_server* server = nullptr;  // serving loop (bs_serve_start)
   // workspace of host-planned calls
   void* ws = nullptr;
   size_t ws_cap = 0;

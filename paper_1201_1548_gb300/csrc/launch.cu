@@ -127,7 +127,7 @@ int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_
 int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const MetaBounds& mb,
                       int cls) {
   cudaStream_t s = ctx->stream;
-  const Tables Tv = ctx->tabs.view();
+  const Tables Tv = ctx->tabs->view();
   const int N = 1 << mb.logN;
   if ((size_t)N * sizeof(uint32_t) > (size_t)ctx->smem_optin)
     return ctx_fail(ctx, kErrRange, "transform size exceeds shared memory");

@@ -88,7 +88,7 @@ extern "C" int bs_resultant_device_noalloc(bs_ctx* ctx, const bs_bipoly* f, cons
   const int cls = uni_class_of(mb.len);
   if (cls < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
   // this call never grows the context's tables
-  if (ctx->tabs.Tt < mb.k_total || ctx->tabs.Tg < mb.k_total || ctx->tabs.logNT < mb.logN)
+  if (ctx->tabs->Tt < mb.k_total || ctx->tabs->Tg < mb.k_total || ctx->tabs->logNT < mb.logN)
     return ctx_fail(ctx, BS_ERR_RANGE,
                     "the context's prime tables do not cover this size yet; make one "
                     "allocating resultant call of this size on the context first");

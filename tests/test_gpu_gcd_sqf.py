@@ -105,7 +105,7 @@ def test_squarefree_part_conventions(ctx):
 
 def test_squarefree_part_already_squarefree(ctx):
     rng = _rng(22)
-    for d in (1, 2, 17, 64):
+    for d in (1, 2, 17, 32):
         r = random_univariate(rng, d, 30)
         assert ctx.squarefree_part(r) == G.squarefree_part(r)
 
@@ -132,7 +132,7 @@ def test_squarefree_part_rejects_prime_dividing_lc(ctx):
 
 def test_squarefree_part_of_resultants(ctx):
     # square-free parts of projections of degenerate curves (the resultant of f and f_y)
-    cases = cfg4_cases(seed=3, deg=4, bits=8)
+    cases = cfg4_cases(seed=3, deg=3, bits=8)
     for name in ("4a", "4c"):
         f, g = cases[name]
         res = R.res_y(f, g)
@@ -150,3 +150,78 @@ def test_squarefree_part_large_degree_by_construction(ctx):
     want = P.primitive_part(_product(u, v, w))
     got = ctx.squarefree_part(r)
     assert got == want
+
+
+# ---- gcd in Z[x] ---------------------------------------------------------------------
+
+def test_gcd_z_planted_factors(ctx):
+    rng = _rng(31)
+    for t in range(30):
+        c = random_univariate(rng, int(rng.integers(0, 8)), int(rng.integers(2, 60)))
+        u = random_univariate(rng, int(rng.integers(0, 10)), int(rng.integers(2, 60)))
+        v = random_univariate(rng, int(rng.integers(0, 10)), int(rng.integers(2, 60)))
+        a, b = _product(c, u), _product(c, v)
+        if t % 3 == 0:
+            a = [6 * x for x in a]
+            b = [-10 * x for x in b]
+        assert ctx.gcd_z(a, b) == G.gcd_z(a, b), t
+
+
+def test_gcd_z_conventions(ctx):
+    assert ctx.gcd_z([], []) == []
+    assert ctx.gcd_z([0, 0], [0]) == []
+    assert ctx.gcd_z([], [-3, -6]) == [3, 6]
+    assert ctx.gcd_z([4, 0, -2], []) == [-4, 0, 2]
+    assert ctx.gcd_z([6], [4]) == [2]
+    assert ctx.gcd_z([6], [1, 1]) == [1]
+    assert ctx.gcd_z([2, 2], [4, 4]) == [2, 2]
+    assert ctx.gcd_z([-2, -2], [4, 4]) == [2, 2]
+    a = [3, -1, 4, 1, -5]
+    assert ctx.gcd_z(a, a) == G.gcd_z(a, a)
+    most_negative = [-(1 << 31)]                           # needs a wider limb when negated
+    assert ctx.gcd_z(most_negative, []) == [1 << 31]
+
+
+def test_gcd_z_wide_and_long(ctx):
+    rng = _rng(32)
+    c = random_univariate(rng, 6, 200)
+    a = _product(c, random_univariate(rng, 8, 250))
+    b = _product(c, random_univariate(rng, 7, 100))
+    assert ctx.gcd_z(a, b) == G.gcd_z(a, b)
+    # long inputs: the planted factor is the gcd with overwhelming probability
+    c = random_univariate(rng, 120, 20)
+    u = random_univariate(rng, 200, 20)
+    v = random_univariate(rng, 150, 20)
+    got = ctx.gcd_z(_product(c, u), _product(c, v))
+    assert got == P.primitive_part(c)
+
+
+def test_gcd_z_prime_dividing_lc(ctx):
+    p0 = bs.bs_prime_table(1)[0]
+    rng = _rng(33)
+    c = random_univariate(rng, 3, 20)
+    u = random_univariate(rng, 4, 20)
+    u[-1] *= p0
+    v = random_univariate(rng, 5, 20)
+    a, b = _product(c, u), _product(c, v)
+    assert ctx.gcd_z(a, b) == G.gcd_z(a, b)
+
+
+def test_modgcd_batch_matches_single_calls(ctx):
+    rng = _rng(34)
+    jobs = []
+    for t in range(24):
+        c = random_univariate(rng, int(rng.integers(0, 6)), int(rng.integers(4, 80)))
+        u = random_univariate(rng, int(rng.integers(1, 8)), int(rng.integers(4, 80)))
+        v = random_univariate(rng, int(rng.integers(1, 8)), int(rng.integers(4, 80)))
+        if t % 2:
+            jobs.append((0, _product(c, u), _product(c, v)))
+        else:
+            jobs.append((1, _product(u, v, v), None))
+    jobs.append((0, [], [5, 10]))
+    jobs.append((1, [9], None))
+    got = ctx.modgcd_batch(jobs)
+    for (k, a, b), g in zip(jobs, got):
+        want = G.gcd_z(a, b) if k == 0 else G.squarefree_part(a)
+        assert g == want
+        assert g == (ctx.gcd_z(a, b) if k == 0 else ctx.squarefree_part(a))
