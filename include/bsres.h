@@ -57,6 +57,7 @@ extern "C" {
 #define BS_ERR_RANGE     7  /* problem exceeds the prime table or the transform size    */
 #define BS_ERR_INTERNAL  8  /* a device-side consistency check failed                   */
 #define BS_ERR_CAPACITY  9  /* caller-provided output capacity is too small             */
+#define BS_PENDING      10  /* bs_poll: the job has not finished yet (not an error)      */
 
 typedef struct bs_ctx bs_ctx;
 
@@ -248,6 +249,78 @@ int bs_gcd_z(bs_ctx *ctx, const bs_upoly *a, const bs_upoly *b, bs_upoly *out);
  * bounds and nothing runs.  Returns the first failing job's status. */
 int bs_modgcd_batch(bs_ctx *ctx, int n, const int *kind, const bs_upoly *a, const bs_upoly *b,
                     bs_upoly *out);
+
+/* ---------------------------------------------------------------------------------
+ * Serving: continuous batching of resultant and gcd jobs
+ *
+ * bs_serve_start() starts `slots` worker threads on the context, each with its own CUDA
+ * stream, and one device arena of `arena_bytes` (0: half the free device memory, capped
+ * by the context's budget).  bs_submit() copies a job's operands and queues it.  A free
+ * worker forms a batch from the queued jobs of the head job's type (resultants in y,
+ * resultants in x, or gcd / square-free jobs), first come first served and at most
+ * `max_batch` jobs, and admits it once the arena can hold it; it then runs the batch
+ * (one graph launch for resultants, one pass of launches for gcds), posts the results
+ * and frees the arena space.  Workers run concurrently, so batches admitted while
+ * others are on the GPU overlap with them.  Every intermediate (residues, images,
+ * reconstructions) stays in the arena; only operands and results cross PCIe.
+ *
+ * While a serving loop runs, the context accepts only bs_submit, bs_poll, bs_wait,
+ * bs_serve_stats and bs_serve_stop; its other compute entry points return BS_ERR_ARG.
+ * These five may be called from any host thread.
+ * ------------------------------------------------------------------------------ */
+
+#define BS_JOB_RESULTANT 0  /* res(f, g; var) */
+#define BS_JOB_GCD       1  /* gcd(a, b) in Z[x], as bs_gcd_z */
+#define BS_JOB_SQFREE    2  /* square-free part of a, as bs_squarefree_part */
+
+typedef struct {
+  int32_t kind;      /* BS_JOB_* */
+  int32_t var;       /* resultants: 0 eliminates x, 1 eliminates y */
+  bs_bipoly f, g;    /* resultant operands (copied by bs_submit) */
+  bs_upoly a, b;     /* gcd operands; b unused for BS_JOB_SQFREE (copied by bs_submit) */
+} bs_job;
+
+typedef struct {
+  int32_t status;    /* the job's status (BS_OK or an error code) */
+  int32_t deg;       /* degree of the result (-1: zero polynomial) */
+  int32_t limbs;     /* limbs per coefficient of the result */
+  uint32_t *c;       /* caller buffer for the coefficients, or NULL (shape only) */
+  int64_t cap_words; /* capacity of c in uint32 words */
+  double queue_ms;   /* submit -> admitted into a batch */
+  double latency_ms; /* submit -> result ready */
+} bs_result;
+
+typedef struct {
+  int64_t submitted, completed, batches, jobs_in_batches, queued;
+  int32_t inflight, max_inflight;   /* batches on the GPU now / at most at once */
+  int64_t arena_bytes, arena_used, arena_peak;
+} bs_serve_info;
+
+/* Start the serving loop (1 <= slots <= 16, max_batch >= 1).  BS_ERR_NOMEM if the arena
+ * cannot be allocated or exceeds the context's budget. */
+int bs_serve_start(bs_ctx *ctx, int slots, int max_batch, size_t arena_bytes);
+
+/* Finish every queued and running job, then stop the workers and free the arena.
+ * Tickets not yet collected are dropped. */
+int bs_serve_stop(bs_ctx *ctx);
+
+/* Queue a job; *ticket identifies it.  The operands are validated and planned here:
+ * BS_ERR_ARG / BS_ERR_RANGE for a bad job, BS_ERR_NOMEM when the job alone needs more
+ * device memory than the arena holds. */
+int bs_submit(bs_ctx *ctx, const bs_job *job, uint64_t *ticket);
+
+/* BS_PENDING while the job runs or waits.  Once it has finished: fills r (status, deg,
+ * limbs, timings) and returns BS_OK; if r->c is not NULL and holds (deg + 1) * limbs
+ * words, the coefficients are copied there and the ticket is released (a later poll of
+ * it returns BS_ERR_ARG).  BS_ERR_CAPACITY if r->c is too small. */
+int bs_poll(bs_ctx *ctx, uint64_t ticket, bs_result *r);
+
+/* Block until the job has finished or timeout_ms elapsed (negative: no limit);
+ * BS_OK or BS_ERR_TIMEOUT. */
+int bs_wait(bs_ctx *ctx, uint64_t ticket, int timeout_ms);
+
+/* Counters of the serving loop. */
+int bs_serve_stats(bs_ctx *ctx, bs_serve_info *out);
 
 /* ---------------------------------------------------------------------------------
  * Measurement

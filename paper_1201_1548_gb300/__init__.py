@@ -6,7 +6,9 @@ kernels.  There is no CPU fallback: if the shared library has not been built, or
 is present, the calls raise.
 
 Names follow the C ABI: ``bs_resultant``, ``bs_resultant_batch``, ``bs_resultant_device``,
-``bs_uni_resultant_modp``, ``bs_gcd_modp``, ``bs_squarefree_part``, ``bs_prime_table``.
+``bs_uni_resultant_modp``, ``bs_gcd_modp``, ``bs_squarefree_part``, ``bs_prime_table``;
+``Context.gcd_z`` / ``Context.modgcd_batch`` wrap ``bs_gcd_z`` / ``bs_modgcd_batch`` and
+``Context.serve_start`` / ``submit`` / ``poll`` / ``wait`` / ``serve_stats`` the serving loop.
 """
 
 from ._abi import (  # noqa: F401
@@ -28,4 +30,8 @@ from ._abi import (  # noqa: F401
     bs_gcd_modp,
     bs_squarefree_part,
     EXPORTED_SYMBOLS,
+    BS_PENDING,
+    JOB_RESULTANT,
+    JOB_GCD,
+    JOB_SQFREE,
 )

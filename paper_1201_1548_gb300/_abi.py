@@ -18,6 +18,7 @@ EXPORTED_SYMBOLS = [
     "bs_device_status", "bs_resultant_batch", "bs_uni_resultant_modp", "bs_prime_table",
     "bs_gcd_modp", "bs_squarefree_part", "bs_plan", "bs_alu_probe", "bs_profile",
     "bs_stage_times", "bs_resultant_device_noalloc", "bs_gcd_z", "bs_modgcd_batch",
+    "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
 ]
 
 
@@ -47,6 +48,28 @@ class _Stats(C.Structure):
                 ("primes_evaluated", C.c_int64), ("primes_rejected", C.c_int64),
                 ("instances", C.c_int64), ("mulmods_alg", C.c_int64),
                 ("max_points", C.c_int32), ("max_primes", C.c_int32)]
+
+
+class _Job(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("var", C.c_int32), ("f", _Bipoly), ("g", _Bipoly),
+                ("a", _Upoly), ("b", _Upoly)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("deg", C.c_int32), ("limbs", C.c_int32),
+                ("c", C.c_void_p), ("cap_words", C.c_int64), ("queue_ms", C.c_double),
+                ("latency_ms", C.c_double)]
+
+
+class _ServeInfo(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("batches", C.c_int64),
+                ("jobs_in_batches", C.c_int64), ("queued", C.c_int64),
+                ("inflight", C.c_int32), ("max_inflight", C.c_int32),
+                ("arena_bytes", C.c_int64), ("arena_used", C.c_int64), ("arena_peak", C.c_int64)]
+
+
+BS_PENDING = 10
+JOB_RESULTANT, JOB_GCD, JOB_SQFREE = 0, 1, 2
 
 
 def library_path():
@@ -91,6 +114,14 @@ def load_library():
     lib.bs_profile.argtypes = [P, I]
     lib.bs_stage_times.argtypes = [P, P, I]
     lib.bs_plan.argtypes = [C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, C.POINTER(_PlanInfo)]
+    lib.bs_gcd_z.argtypes = [P, C.POINTER(_Upoly), C.POINTER(_Upoly), C.POINTER(_Upoly)]
+    lib.bs_modgcd_batch.argtypes = [P, I, P, P, P, P]
+    lib.bs_serve_start.argtypes = [P, I, I, C.c_size_t]
+    lib.bs_serve_stop.argtypes = [P]
+    lib.bs_submit.argtypes = [P, C.POINTER(_Job), C.POINTER(C.c_uint64)]
+    lib.bs_poll.argtypes = [P, C.c_uint64, C.POINTER(_Result)]
+    lib.bs_wait.argtypes = [P, C.c_uint64, I]
+    lib.bs_serve_stats.argtypes = [P, C.POINTER(_ServeInfo)]
     for name in EXPORTED_SYMBOLS:
         getattr(lib, name)
     _LIB = lib
@@ -307,15 +338,77 @@ class Context:
         out = (_Upoly * n)()
         for j in range(n):
             out[j] = _Upoly(0, 0, None)
-        self._check(self.lib.bs_modgcd_batch(self.h, n, kinds, A, Bv, out))
+        self._check(self.lib.bs_modgcd_batch(self.h, n, C.cast(kinds, C.c_void_p),
+                                             C.cast(A, C.c_void_p), C.cast(Bv, C.c_void_p),
+                                             C.cast(out, C.c_void_p)))
         bufs = []
         for j in range(n):
             buf = np.zeros((max(out[j].deg, 0) + 1) * max(out[j].limbs, 1), dtype=np.uint32)
             bufs.append(buf)
             out[j] = _Upoly(out[j].deg, max(out[j].limbs, 1), buf.ctypes.data)
-        self._check(self.lib.bs_modgcd_batch(self.h, n, kinds, A, Bv, out))
+        self._check(self.lib.bs_modgcd_batch(self.h, n, C.cast(kinds, C.c_void_p),
+                                             C.cast(A, C.c_void_p), C.cast(Bv, C.c_void_p),
+                                             C.cast(out, C.c_void_p)))
         return [limbs_to_ints(bufs[j], out[j].deg + 1, out[j].limbs) if out[j].deg >= 0 else []
                 for j in range(n)]
+
+    # ---- serving loop -----------------------------------------------------------------
+    def serve_start(self, slots=3, max_batch=64, arena_bytes=0):
+        self._check(self.lib.bs_serve_start(self.h, int(slots), int(max_batch), int(arena_bytes)))
+        self._serve_keep = {}
+
+    def serve_stop(self):
+        self._check(self.lib.bs_serve_stop(self.h))
+        self._serve_keep = {}
+
+    def submit(self, kind, *operands, var=1):
+        """Queue a job: submit(JOB_RESULTANT, f, g, var=1), submit(JOB_GCD, a, b) or
+        submit(JOB_SQFREE, a).  Returns the ticket."""
+        job = _Job()
+        job.kind = int(kind)
+        job.var = int(var)
+        keep = []
+        if kind == JOB_RESULTANT:
+            for name, poly in zip(("f", "g"), operands):
+                arr, dx, dy, L = bipoly_to_limbs(poly)
+                keep.append(arr)
+                setattr(job, name, _bip(arr, dx, dy, L))
+        else:
+            polys = list(operands) + [[]] * (2 - len(operands))
+            for name, poly in zip(("a", "b"), polys):
+                arr, L = ints_to_limbs(poly)
+                keep.append(arr)
+                setattr(job, name, _Upoly(len(poly) - 1, L, arr.ctypes.data))
+        t = C.c_uint64()
+        self._check(self.lib.bs_submit(self.h, C.byref(job), C.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket):
+        """None while the job runs; otherwise (status, coefficients, queue_ms, latency_ms)."""
+        r = _Result()
+        rc = self.lib.bs_poll(self.h, C.c_uint64(ticket), C.byref(r))
+        if rc == BS_PENDING:
+            return None
+        self._check(rc)
+        words = (r.deg + 1) * r.limbs
+        buf = np.zeros(max(words, 1), dtype=np.uint32)
+        r.c = buf.ctypes.data
+        r.cap_words = buf.size
+        self._check(self.lib.bs_poll(self.h, C.c_uint64(ticket), C.byref(r)))
+        coeffs = limbs_to_ints(buf, r.deg + 1, r.limbs) if r.deg >= 0 else []
+        return int(r.status), coeffs, float(r.queue_ms), float(r.latency_ms)
+
+    def wait(self, ticket, timeout_ms=-1):
+        rc = self.lib.bs_wait(self.h, C.c_uint64(ticket), int(timeout_ms))
+        if rc == 4:
+            return False
+        self._check(rc)
+        return True
+
+    def serve_stats(self):
+        info = _ServeInfo()
+        self._check(self.lib.bs_serve_stats(self.h, C.byref(info)))
+        return {name: getattr(info, name) for name, _ in _ServeInfo._fields_}
 
     def squarefree_part(self, r):
         arr, L = ints_to_limbs(r)

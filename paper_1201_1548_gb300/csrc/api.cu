@@ -121,10 +121,11 @@ extern "C" int bs_init(int device, size_t mem_budget, bs_ctx** out) {
 
 extern "C" void bs_free(bs_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->server) bs_serve_stop(ctx);
   cudaSetDevice(ctx->device);
   if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
   if (ctx->stream && ctx->stream != ctx->own_stream) cudaStreamSynchronize(ctx->stream);
-  ctx->tabs->release();
+  ctx->own_tabs.release();  // serving slots borrow their parent's tables
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->dev_ws) cudaFree(ctx->dev_ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -516,6 +517,7 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
   if (!ctx || n < 0 || !out || (n && (!f || !g)) || (var != 0 && var != 1))
     return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
   if (n == 0) return BS_OK;
+  if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
   cudaSetDevice(ctx->device);
   HostBatch B;
   int rc = batch_plan(ctx, n, f, g, var, &B);
@@ -566,6 +568,7 @@ extern "C" int bs_resultant_device(bs_ctx* ctx, const bs_bipoly* f, const bs_bip
                                    bs_upoly* out) {
   if (!ctx) return BS_ERR_ARG;
   if (!out || !out->c || (var != 0 && var != 1)) return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
+  if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
   int rc = check_bipoly(ctx, f, "f");
   if (rc) return rc;
   rc = check_bipoly(ctx, g, "g");

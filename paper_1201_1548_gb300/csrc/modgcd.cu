@@ -649,6 +649,7 @@ void mg_result_shape(const MgBatch& B, int j, int* deg, int* limbs) {
 }
 
 int run_mg(bs_ctx* ctx, int n, const int* kind, const bs_upoly* a, const bs_upoly* b, bs_upoly* out) {
+  if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
   cudaSetDevice(ctx->device);
   MgBatch B;
   int rc = mg_plan(ctx, n, kind, a, b, &B);

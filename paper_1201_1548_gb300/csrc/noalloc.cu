@@ -53,6 +53,7 @@ extern "C" int bs_resultant_device_noalloc(bs_ctx* ctx, const bs_bipoly* f, cons
   for (const bs_bipoly* p : {f, g})
     if (p->deg_x < 0 || p->deg_y < 0 || p->limbs < 1 || p->limbs > kMaxLimbs || !p->c)
       return ctx_fail(ctx, BS_ERR_ARG, "bad extents, limbs or pointer");
+  if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx_fail(ctx, BS_ERR_CUDA, "set device");
   // size bounds from the extents, exactly as the allocating device entry point
   int32_t dcap = 0, lcap = 0;
