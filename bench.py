@@ -41,6 +41,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (4096 pairs) and served-stream measurements")
     return ap.parse_args()
 
 
@@ -184,6 +186,149 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _marshal_pairs(bs, pairs):
+    """Pre-marshalled C arrays of a batch (kept alive by the returned tuple)."""
+    import ctypes as C
+    import numpy as np
+    from paper_1201_1548_gb300._abi import _Bipoly, _Upoly
+    n = len(pairs)
+    keep = []
+    F = (_Bipoly * n)()
+    G = (_Bipoly * n)()
+    for i, (f, g) in enumerate(pairs):
+        af, dxf, dyf, Lf = bs.bipoly_to_limbs(f)
+        ag, dxg, dyg, Lg = bs.bipoly_to_limbs(g)
+        keep += [af, ag]
+        F[i] = _Bipoly(dxf, dyf, Lf, af.ctypes.data)
+        G[i] = _Bipoly(dxg, dyg, Lg, ag.ctypes.data)
+    O = (_Upoly * n)()
+    for i in range(n):
+        O[i] = _Upoly(0, 0, None)
+    lib = bs.load_library()
+    return F, G, O, keep, lib, C
+
+
+def _bench_batched(bs, ctx, reps=3):
+    """cfg3: 4096 pairs in one graph launch against one call per resultant, both through
+    the C ABI with host buffers (plan, copies and formatting included)."""
+    import numpy as np
+    from workloads import cfg3_batch
+    pairs = cfg3_batch(seed=1, count=4096)
+    n = len(pairs)
+    F, G, O, keep, lib, C = _marshal_pairs(bs, pairs)
+    rc = lib.bs_resultant_batch(ctx.h, n, F, G, 1, O)          # size query
+    if rc:
+        raise SystemExit(f"size query failed: {rc}")
+    caps = [(O[i].deg, O[i].limbs) for i in range(n)]
+    bufs = [np.zeros((max(d, 0) + 1) * L, dtype=np.uint32) for d, L in caps]
+    for i in range(n):
+        O[i].c = bufs[i].ctypes.data
+
+    def reset():
+        for i in range(n):
+            O[i].deg, O[i].limbs = caps[i]
+
+    def batch_call():
+        reset()
+        t0 = time.perf_counter()
+        rc = lib.bs_resultant_batch(ctx.h, n, F, G, 1, O)
+        t1 = time.perf_counter()
+        if rc:
+            raise SystemExit(f"bs_resultant_batch failed: {rc}")
+        return t1 - t0
+
+    batch_call()                                                # warm-up (tables, graph)
+    st = bs._abi._Stats()
+    lib.bs_last_stats(ctx.h, C.byref(st))
+    tb = min(batch_call() for _ in range(reps))
+    ref = [bs.limbs_to_ints(bufs[i], O[i].deg + 1, O[i].limbs) if O[i].deg >= 0 else []
+           for i in range(n)]
+    # one blocking call (one launch sequence, no graph) per resultant
+    one = (bs._abi._Upoly * n)()
+    bufs1 = [np.zeros_like(b) for b in bufs]
+    for i in range(n):
+        one[i] = bs._abi._Upoly(caps[i][0], caps[i][1], bufs1[i].ctypes.data)
+    for i in range(64):
+        lib.bs_resultant(ctx.h, C.byref(F[i]), C.byref(G[i]), 1, C.byref(one[i]))
+    for i in range(n):
+        one[i].deg, one[i].limbs = caps[i]
+    t0 = time.perf_counter()
+    for i in range(n):
+        rc = lib.bs_resultant(ctx.h, C.byref(F[i]), C.byref(G[i]), 1, C.byref(one[i]))
+        if rc:
+            raise SystemExit(f"bs_resultant failed: {rc}")
+    t1 = (time.perf_counter() - t0)
+    for i in range(0, n, 97):                                   # same results either way
+        got = bs.limbs_to_ints(bufs1[i], one[i].deg + 1, one[i].limbs) if one[i].deg >= 0 else []
+        if got != ref[i]:
+            raise SystemExit(f"batched and single results differ at pair {i}")
+    return {"workload": "4096 pairs, total degrees 4-24, 8-64-bit coefficients, 20% zeros, "
+                        "seed 1 (host buffers, planning and copies included)",
+            "pairs": n, "ms_batch": tb * 1e3, "ms_one_call_per_resultant": t1 * 1e3,
+            "resultants_per_s_batch": n / tb, "resultants_per_s_one_by_one": n / t1,
+            "speedup": t1 / tb, "instances": st.instances, "mulmods_alg": st.mulmods_alg,
+            "modp_univariate_resultants_per_s": st.instances / tb}
+
+
+def _bench_served(bs, jobs=96, seed=1):
+    """cfg5: Poisson arrivals of resultant and gcd jobs (total degree 6-64, 16-256-bit
+    coefficients) into the serving loop.  First a closed-loop pass (everything submitted
+    at once) gives the saturated throughput; then an open-loop pass at 70% of it gives
+    the latency percentiles."""
+    from workloads import cfg5_stream
+    srv = bs.Context(0)
+    srv.serve_start(slots=3, max_batch=16)
+    stream = cfg5_stream(seed=seed, jobs=jobs)
+
+    def submit(job):
+        if job["kind"] == "gcd":
+            return srv.submit(bs.JOB_GCD, job["a"], job["b"])
+        return srv.submit(bs.JOB_RESULTANT, job["f"], job["g"])
+
+    warm = [submit(j) for j in stream[:8]]
+    for t in warm:
+        srv.wait(t)
+        srv.poll(t)
+    t0 = time.perf_counter()
+    tickets = [submit(j) for j in stream]
+    for t in tickets:
+        srv.wait(t)
+    sat_s = time.perf_counter() - t0
+    for t in tickets:
+        srv.poll(t)
+    sat_rate = jobs / sat_s
+    rate = 0.7 * sat_rate
+    stream2 = cfg5_stream(seed=seed + 1, jobs=jobs, rate_hz=rate)
+    t0 = time.perf_counter()
+    tickets = []
+    for j in stream2:
+        dt = j["t"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(submit(j))
+    lat = []
+    for t in tickets:
+        srv.wait(t)
+        status, _, _, ms = srv.poll(t)
+        if status:
+            raise SystemExit(f"served job failed: {status}")
+        lat.append(ms)
+    open_s = time.perf_counter() - t0
+    info = srv.serve_stats()
+    srv.serve_stop()
+    srv.close()
+    lat.sort()
+    pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    return {"workload": "Poisson stream, 50% resultants (dense, total degree 6-64) / 50% gcds "
+                        f"(planted factor), 16-256-bit coefficients, seed {seed}",
+            "jobs": jobs, "slots": 3, "max_batch": 16,
+            "saturated_jobs_per_s": sat_rate, "offered_rate_hz": rate,
+            "open_loop_jobs_per_s": jobs / open_s,
+            "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "max": lat[-1]},
+            "batches": info["batches"], "max_inflight_batches": info["max_inflight"],
+            "arena_peak_bytes": info["arena_peak"]}
+
+
 def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -325,6 +470,11 @@ def run_ours(args):
     h2d = (af.nbytes + ag.nbytes)
     d2h = (deg + 1) * plan["out_limbs"] * 4
 
+    batched = served = None
+    if rank == 0 and not args.no_extras:
+        batched = _bench_batched(bs, ctx)
+        served = _bench_served(bs)
+
     cpu = None
     if want_cpu:
         cpu = _cpu_baseline(f, g, pool, cores, npts=max(32, 2 * cores))
@@ -346,7 +496,8 @@ def run_ours(args):
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": 6 * args.steps,
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu,
+                "batched": batched, "served": served}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

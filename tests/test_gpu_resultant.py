@@ -162,3 +162,65 @@ def test_large_transforms_sampled(ctx, tdeg, bits):
         assert P.evaluate(r, x0) == R.res_at_point(f, g, x0)
     p = nt.prime_table(1)[0]
     assert P.evaluate(r, 12345) % p == R.res_at_point_modp(f, g, 12345, p)
+
+
+def test_cfg3_full_batch_sampled(ctx):
+    """4096 pairs of uneven degree (4-24) and coefficient size (8-64 bits) in one graph
+    launch: exact oracle results for the small pairs, exact values at integer points and
+    values mod a prime outside the working set for a seeded sample of the rest."""
+    pairs = cfg3_batch(seed=1, count=4096)
+    got = ctx.resultant_batch(pairs)
+    assert len(got) == len(pairs)
+    rng = random.Random(5)
+    p = 2147483647  # a prime outside the library's table (2^31 - 1 is not 1 mod 2^14)
+    assert nt.is_prime(p)
+    for i in rng.sample(range(len(pairs)), 48):
+        f, g = pairs[i]
+        r = got[i]
+        assert P.deg(r) <= R.degree_bound(f, g)
+        a = rng.randrange(p)
+        assert P.evaluate(r, a) % p == R.res_at_point_modp(f, g, a, p), i
+    for i in rng.sample(range(len(pairs)), 8):
+        f, g = pairs[i]
+        assert P.evaluate(got[i], 1) == R.res_at_point(f, g, 1), i
+        assert got[i] == ctx.resultant(f, g), i
+    small = [i for i in range(len(pairs)) if len(pairs[i][0]) + len(pairs[i][1]) <= 12][:12]
+    for i in small:
+        assert got[i] == R.res_y(*pairs[i]), i
+
+
+@pytest.mark.parametrize("tdeg,bits", [(8, 600), (16, 256)])
+def test_many_primes_block_reconstruction(ctx, tdeg, bits):
+    """k above the warp reconstruction's limit (the block Garner path): exact values at
+    integer points and values mod a prime outside the table."""
+    import paper_1201_1548_gb300 as bs
+    rng = _rng(200 + tdeg)
+    f = dense_curve(rng, tdeg, bits)
+    g = dense_curve(rng, tdeg, bits)
+    info = bs.bs_plan(f, g)
+    assert info["k_need"] > 160
+    r = ctx.resultant(f, g)
+    assert P.deg(r) <= R.degree_bound(f, g)
+    b2 = R.bound_sq(f, g)
+    assert all(c * c <= b2 for c in r)
+    for x0 in (0, 1, -1):
+        assert P.evaluate(r, x0) == R.res_at_point(f, g, x0)
+    p = 2147483647
+    for a in (12345, 987654321):
+        assert P.evaluate(r, a) % p == R.res_at_point_modp(f, g, a, p)
+
+
+def test_largest_served_size(ctx):
+    """The largest job of the served stream (total degree 64, 256-bit coefficients:
+    about 1150 primes and 8192 points per prime): values mod a prime outside the table."""
+    import paper_1201_1548_gb300 as bs
+    rng = _rng(300)
+    f = dense_curve(rng, 64, 256)
+    g = dense_curve(rng, 64, 256)
+    info = bs.bs_plan(f, g)
+    assert info["N"] == 8192 and info["k_need"] > 1000
+    r = ctx.resultant(f, g)
+    assert P.deg(r) <= R.degree_bound(f, g)
+    p = 2147483647
+    for a in (3, 1234567):
+        assert P.evaluate(r, a) % p == R.res_at_point_modp(f, g, a, p)
