@@ -9,6 +9,7 @@
 
 #include "../../include/bsres.h"
 #include "batch.cuh"
+#include "host_parallel.h"
 #include "common.cuh"
 #include "ctx.cuh"
 #include "resultant_kernels.cuh"
@@ -292,10 +293,14 @@ int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int v
     if (rc) return rc;
     rc = check_bipoly(ctx, g + i, "g");
     if (rc) return rc;
+  }
+  // plans are independent: large batches plan on several host threads
+  parallel_for(n, 256, [&](int i) {
     B.plans[i] = plan_host(grid_of(f + i), grid_of(g + i), var, H.lg_prefix.data(), T);
+  });
+  for (int i = 0; i < n; ++i)
     if (B.plans[i].status)
       return ctx_fail(ctx, B.plans[i].status, "planning failed for job " + std::to_string(i));
-  }
   for (const Plan& P : B.plans) {
     if (P.trivial) continue;
     B.needT = std::max(B.needT, P.k_total);
@@ -306,6 +311,7 @@ int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int v
     const int c = uni_class_of(std::max(P.me, P.ne) + 1);
     if (c < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
     ++B.cls_count[c];
+    if (P.logN <= kWarpLogNMax) ++B.ecls_count[eval_class_of(P.logN)];
   }
   B.in_f.resize(n);
   B.in_g.resize(n);
@@ -320,12 +326,14 @@ int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int v
   B.o_jobs = up.take(sizeof(Job) * n);
   B.o_eoff = up.take(sizeof(int64_t) * (n + 1));
   B.o_ioff = up.take(sizeof(int64_t) * (n + 1));
-  B.o_ewoff = up.take(sizeof(int64_t) * (n + 1));
-  B.o_iwoff = up.take(sizeof(int64_t) * (n + 1));
   B.o_coff = up.take(sizeof(int64_t) * (n + 1));
   for (int c = 0; c < kNumUniClasses; ++c) {
     B.o_cids[c] = up.take(sizeof(int32_t) * std::max(B.cls_count[c], 1));
     B.o_coffs[c] = up.take(sizeof(int64_t) * (B.cls_count[c] + 1));
+  }
+  for (int c = 0; c < kNumEvalClasses; ++c) {
+    B.o_eids[c] = up.take(sizeof(int32_t) * std::max(B.ecls_count[c], 1));
+    B.o_eoffs[c] = up.take(sizeof(int64_t) * (B.ecls_count[c] + 1));
   }
   B.o_status = up.take(sizeof(int32_t) * 4);
   B.o_pstat = up.take(sizeof(int32_t) * std::max<size_t>(pstat_words, 1));
@@ -377,8 +385,6 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   Job* hj = (Job*)(hu + B.o_jobs);
   int64_t* eoff = (int64_t*)(hu + B.o_eoff);
   int64_t* ioff = (int64_t*)(hu + B.o_ioff);
-  int64_t* ewoff = (int64_t*)(hu + B.o_ewoff);
-  int64_t* iwoff = (int64_t*)(hu + B.o_iwoff);
   int64_t* coff = (int64_t*)(hu + B.o_coff);
   int32_t* cids[kNumUniClasses];
   int64_t* coffs[kNumUniClasses];
@@ -388,7 +394,15 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
     coffs[c] = (int64_t*)(hu + B.o_coffs[c]);
     coffs[c][0] = 0;
   }
-  eoff[0] = ioff[0] = coff[0] = ewoff[0] = iwoff[0] = 0;
+  int32_t* eids[kNumEvalClasses];
+  int64_t* eoffs[kNumEvalClasses];
+  int efill[kNumEvalClasses] = {0};
+  for (int c = 0; c < kNumEvalClasses; ++c) {
+    eids[c] = (int32_t*)(hu + B.o_eids[c]);
+    eoffs[c] = (int64_t*)(hu + B.o_eoffs[c]);
+    eoffs[c][0] = 0;
+  }
+  eoff[0] = ioff[0] = coff[0] = 0;
   size_t in_pos = 0, ps_pos = 0;
   B.instances = B.mulmods = B.k_need_sum = B.k_total_sum = 0;
   B.maxpts = B.maxprimes = 0;
@@ -407,7 +421,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
     J.out = (uint32_t*)(base + B.o_out[i]);
     J.status = (int32_t*)(base + B.o_status);
     J.rejected = (int32_t*)(base + B.o_status) + 1;
-    int64_t ne = 0, ni = 0, nu = 0, new_ = 0, niw = 0;
+    int64_t ne = 0, ni = 0, nu = 0;
     if (!P.trivial) {
       J.rows = (P.me + 1) + (P.ne + 1);
       J.ev = (uint32_t*)(base + B.o_ev[i]);
@@ -416,10 +430,14 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
       J.sel = (int32_t*)(base + B.o_sel[i]);
       J.pstat = (int32_t*)(base + B.o_pstat) + ps_pos;
       ps_pos += P.k_total;
-      if (P.logN <= kWarpLogNMax)
-        new_ = (int64_t)P.k_total * ((J.rows + 7) / 8);
-      else
+      if (P.logN <= kWarpLogNMax) {
+        const int ec = eval_class_of(P.logN);
+        eids[ec][efill[ec]] = i;
+        eoffs[ec][efill[ec] + 1] = eoffs[ec][efill[ec]] + (int64_t)P.k_total * ((J.rows + 7) / 8);
+        ++efill[ec];
+      } else {
         ne = (int64_t)P.k_total * J.rows;
+      }
       ni = P.k_total;  // interpolation: one block per prime
       nu = (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile;
       const int c = uni_class_of(std::max(P.me, P.ne) + 1);
@@ -436,8 +454,6 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
     hj[i] = J;
     eoff[i + 1] = eoff[i] + ne;
     ioff[i + 1] = ioff[i] + ni;
-    ewoff[i + 1] = ewoff[i] + new_;
-    iwoff[i + 1] = iwoff[i] + niw;
     coff[i + 1] = coff[i] + (J.cap_deg + kCrtTile) / kCrtTile;
   }
   cudaStream_t s = ctx->stream;
@@ -455,12 +471,14 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
                         B.cls_count[c]};
     L.uni_items[c] = B.cls_count[c] ? coffs[c][B.cls_count[c]] : 0;
   }
-  L.eval_w = WorkList{nullptr, (const int64_t*)(base + B.o_ewoff), n};
-  L.intt_w = WorkList{nullptr, (const int64_t*)(base + B.o_iwoff), n};
+  for (int c = 0; c < kNumEvalClasses; ++c) {
+    L.evw[c] = WorkList{(const int32_t*)(base + B.o_eids[c]), (const int64_t*)(base + B.o_eoffs[c]),
+                        B.ecls_count[c]};
+    L.evw_items[c] = B.ecls_count[c] ? eoffs[c][B.ecls_count[c]] : 0;
+  }
+  L.evw_any_items = 0;
   L.eval_items = eoff[n];
   L.intt_items = ioff[n];
-  L.eval_w_items = ewoff[n];
-  L.intt_w_items = iwoff[n];
   L.crt_items = coff[n];
   L.maxN = B.maxN;
   L.kmax = B.kmax;
@@ -489,7 +507,9 @@ int batch_finish(bs_ctx* ctx, const HostBatch& B, const char* hd, bs_upoly* out)
   ctx->stats.max_points = B.maxpts;
   ctx->stats.max_primes = B.maxprimes;
   if (st[0]) return ctx_fail(ctx, st[0], "device stage reported a failure");
-  for (int i = 0; i < B.n; ++i) {
+  // results are independent: large batches are formatted on several host threads
+  std::vector<int> err(B.n, 0);
+  parallel_for(B.n, 256, [&](int i) {
     const Plan& P = B.plans[i];
     const uint32_t* src = (const uint32_t*)(hd + (B.o_out[i] - B.dn_start));
     const int ncoef = std::max(P.D, 0) + 1;
@@ -499,13 +519,22 @@ int batch_finish(bs_ctx* ctx, const HostBatch& B, const char* hd, bs_upoly* out)
         deg = c;
         break;
       }
-    if (deg > out[i].deg) return ctx_fail(ctx, BS_ERR_CAPACITY, "output degree capacity too small");
+    if (deg > out[i].deg) {
+      err[i] = 1;
+      return;
+    }
     const int cap = out[i].deg;
-    if (deg >= 0 && !copy_coeffs(src, P.out_limbs, deg + 1, out[i].c, out[i].limbs))
-      return ctx_fail(ctx, BS_ERR_CAPACITY, "output limb capacity too small");
+    if (deg >= 0 && !copy_coeffs(src, P.out_limbs, deg + 1, out[i].c, out[i].limbs)) {
+      err[i] = 2;
+      return;
+    }
     for (int c = deg + 1; c <= cap; ++c)
       std::memset(out[i].c + (size_t)c * out[i].limbs, 0, sizeof(uint32_t) * out[i].limbs);
     out[i].deg = deg;
+  });
+  for (int i = 0; i < B.n; ++i) {
+    if (err[i] == 1) return ctx_fail(ctx, BS_ERR_CAPACITY, "output degree capacity too small");
+    if (err[i] == 2) return ctx_fail(ctx, BS_ERR_CAPACITY, "output limb capacity too small");
   }
   return BS_OK;
 }

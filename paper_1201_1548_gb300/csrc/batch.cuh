@@ -17,9 +17,11 @@ struct HostBatch {
   std::vector<int64_t> in_f, in_g;  // input limb words per job
   int needT = 1, needLog = 0, kmax = 1, lmax = 1, maxN = 1;
   int cls_count[kNumUniClasses] = {0, 0, 0, 0, 0, 0};
+  int ecls_count[kNumEvalClasses] = {0, 0, 0, 0, 0, 0};
   // layout: [upload | compute | download], offsets from the region's base
-  size_t o_jobs = 0, o_eoff = 0, o_ioff = 0, o_ewoff = 0, o_iwoff = 0, o_coff = 0;
+  size_t o_jobs = 0, o_eoff = 0, o_ioff = 0, o_coff = 0;
   size_t o_cids[kNumUniClasses] = {}, o_coffs[kNumUniClasses] = {};
+  size_t o_eids[kNumEvalClasses] = {}, o_eoffs[kNumEvalClasses] = {};
   size_t o_status = 0, o_pstat = 0, o_in = 0, up_bytes = 0;
   std::vector<size_t> o_ev, o_vals, o_rmod, o_sel, o_out;
   size_t dn_start = 0, o_status_dn = 0, dn_bytes = 0, total = 0;

@@ -51,8 +51,13 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   const int sms = ctx->sms;
   const size_t tsmem = sizeof(uint32_t) * (size_t)L.maxN;
   mark(ctx, 1, s);
-  int g = grid_for(L.eval_w_items, (int64_t)sms * 8);
-  if (g) launch_eval_w(g, s, L.jobs, L.eval_w, Tv, PfHint{L.kt_max, 1 << L.logN_max, L.kmax});
+  int g;
+  for (int c = 0; c < kNumEvalClasses; ++c) {
+    g = grid_for(L.evw_items[c], (int64_t)sms * 8);
+    if (g) launch_eval_w(c, g, s, L.jobs, L.evw[c], Tv, PfHint{L.kt_max, 1 << L.logN_max, L.kmax});
+  }
+  g = grid_for(L.evw_any_items, (int64_t)sms * 8);
+  if (g) launch_eval_w(-1, g, s, L.jobs, L.evw_any, Tv, PfHint{L.kt_max, 1 << L.logN_max, L.kmax});
   g = grid_for(L.eval_items, (int64_t)sms * 8);
   if (g) launch_eval(g, tsmem, s, L.jobs, L.eval, Tv);
   mark(ctx, 2, s);
@@ -61,8 +66,6 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
     if (g) launch_uni(c, g, s, L.jobs, L.uni[c], Tv);
   }
   mark(ctx, 3, s);
-  g = grid_for(L.intt_w_items, (int64_t)sms * 8);
-  if (g) launch_intt_w(g, s, L.jobs, L.intt_w, Tv);
   g = grid_for(L.intt_items, (int64_t)sms * 8);
   if (g) launch_intt(g, tsmem + tsmem / 2, s, L.jobs, L.intt, Tv);  // values + twiddles
   mark(ctx, 4, s);
@@ -140,19 +143,22 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   StageLaunch L;
   L.jobs = dj;
   const bool wsize = mb.logN <= kWarpLogNMax;  // the actual size is at most the bound
-  L.eval_w = WorkList{nullptr, offs + kOffEvalW, 1};
+  for (int c = 0; c < kNumEvalClasses; ++c) {
+    L.evw[c] = WorkList{nullptr, offs + kOffEvalW, 1};
+    L.evw_items[c] = 0;
+  }
   L.eval = WorkList{nullptr, offs + kOffEvalS, 1};
   for (int c = 0; c < kNumUniClasses; ++c) {
     L.uni[c] = WorkList{nullptr, offs + kOffUni, 1};
     L.uni_items[c] = 0;
   }
   L.uni_items[cls] = (((int64_t)mb.k_total << mb.logN) + kUniTile - 1) / kUniTile;
-  L.intt_w = WorkList{nullptr, offs + kOffInttW, 1};
   L.intt = WorkList{nullptr, offs + kOffInttS, 1};
   L.crt = WorkList{nullptr, offs + kOffCrt, 1};
-  L.eval_w_items = (int64_t)mb.k_total * ((mb.rows + 7) / 8);
+  // the transform size is known on the device only: one kernel dispatches per job
+  L.evw_any = WorkList{nullptr, offs + kOffEvalW, 1};
+  L.evw_any_items = (int64_t)mb.k_total * ((mb.rows + 7) / 8);
   L.eval_items = wsize ? 0 : (int64_t)mb.k_total * mb.rows;
-  L.intt_w_items = 0;
   L.intt_items = mb.k_total;
   L.crt_items = ((int64_t)J.cap_deg + kCrtTile) / kCrtTile;
   L.maxN = N;

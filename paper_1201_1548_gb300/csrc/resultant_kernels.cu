@@ -251,14 +251,13 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
     J.rows = (P.trivial || P.status) ? 0 : (P.me + 1) + (P.ne + 1);
     const bool run = (P.status == 0 && P.trivial == 0);
     *dst = J;
-    // offsets of the stages (one job each): warp eval, smem eval, unires tiles,
-    // warp intt, smem intt, crt tiles
+    // offsets of the stages (one job each): warp eval, smem eval, unires tiles, intt,
+    // crt tiles
     const bool wsize = P.logN <= kWarpLogNMax;
     for (int s = 0; s < kNumOffs; s += 2) offs[s] = 0;
     offs[kOffEvalW + 1] = (run && wsize) ? (int64_t)P.k_total * ((J.rows + 7) / 8) : 0;
     offs[kOffEvalS + 1] = (run && !wsize) ? (int64_t)P.k_total * J.rows : 0;
     offs[kOffUni + 1] = run ? (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile : 0;
-    offs[kOffInttW + 1] = 0;
     offs[kOffInttS + 1] = run ? P.k_total : 0;
     offs[kOffCrt + 1] = ((int64_t)J.cap_deg + kCrtTile) / kCrtTile;
   }
@@ -357,26 +356,27 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(const Job* jobs, WorkList
 }
 
 // ------------------------------------------------------------------------------------
-// (a) + (b) and (d) for N <= kWarpNMax: one warp per row / prime, no block barriers
+// (a) + (b) for N <= 2^kWarpLogNMax: one warp per (prime, row), one kernel per size class
 // ------------------------------------------------------------------------------------
+// Residues of row e of f (or g) times g^o, folded modulo N, in layout A: register r of
+// lane l holds element 32 r + l.  Only the first NZ registers can be nonzero when the
+// row has at most 32 NZ coefficients (and N > that count).
 template <int R>
-__device__ __forceinline__ void eval_row_warp(const Job* J, int q, int row, const Tables& T,
-                                              uint32_t* sw, const uint32_t* s_tw,
-                                              const uint32_t* s_cp) {
+__device__ __forceinline__ void eval_load_row(uint32_t (&v)[R], const Job* J, int q, int row,
+                                              const Tables& T, uint32_t* sw, const uint32_t* s_cp,
+                                              const PrimeConst& pc, const Mod& M, int N) {
   const int lane = threadIdx.x & 31;
   const int me = J->plan.me;
-  const int N = J->plan.N;
   const bool isf = row <= me;
   const int e = isf ? row : row - me - 1;
   const Grid G = isf ? J->f : J->g;
   const int var = J->var;
-  const PrimeConst pc = T.pc[q];
-  const Mod M{pc.p, pc.pinv};
   const uint32_t* pw = T.pw + (int64_t)q * (kMaxLimbs + 1);
   const uint32_t* mpw = T.mpw + (int64_t)q * (kMaxLimbs + 1);
   const int eo = ext_o(G, var);
   // residues times g^o, folded modulo N, staged in this warp's shared slice (rolled loop)
-  for (int t = lane; t < N; t += 32) {
+  const int top = min(eo + 1, N);
+  for (int t = lane; t < top; t += 32) {
     uint32_t acc = 0;
     for (int o = t; o <= eo; o += N) {
       const uint32_t x = residue_m(coef_ptr(G, var, e, o), G.L, pw, mpw, M.p, M.pinv);
@@ -386,43 +386,78 @@ __device__ __forceinline__ void eval_row_warp(const Job* J, int q, int row, cons
     sw[t] = acc;
   }
   __syncwarp();
-  uint32_t v[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = (32 * r + lane < N) ? sw[32 * r + lane] : 0u;
-  __syncwarp();  // the transposes below reuse sw
-  // twiddles of the transform of size N: s_tw[i] = omega_N^i, so stage len reads index
-  // j << (logN - lg - 1)
-  const uint32_t* tw = s_tw;
-  const int logN = J->plan.logN;
-  if (R == 1 && N < 32) {
-    // short transform inside one register: only the stages below N
-    for (int lg = 4; lg >= 0; --lg) {
-      const int len = 1 << lg;
-      if (len >= N) continue;
-      const bool upper = (lane & len) != 0;
-      const int sh = logN - (lg + 1);
-      const uint32_t w = upper ? tw[(lane & (len - 1)) << sh] : pc.one_m;
-      const uint32_t x = v[0];
-      const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
-      v[0] = mmul(upper ? msub(y, x, M.p) : madd(x, y, M.p), w, M);
-    }
-  } else if constexpr (R == 32) {
-    warp_dif_1024(v, sw, tw, logN, M);
-  } else {
-    warp_dif<R>(v, tw, logN, M, pc.one_m);
-  }
+  for (int r = 0; r < R; ++r) v[r] = (32 * r + lane < top) ? sw[32 * r + lane] : 0u;
+  __syncwarp();  // the transposes reuse sw
+}
+
+template <int R, int NZ>
+__device__ __forceinline__ void eval_row_nz(const Job* J, int q, int row, const Tables& T, uint32_t* sw,
+                                            const uint32_t* s_tw, const uint32_t* s_cp,
+                                            const PrimeConst& pc, const Mod& M) {
+  constexpr int N = 32 * R;
+  constexpr uint32_t MASK = (NZ >= 32) ? 0xffffffffu : ((1u << NZ) - 1u);
+  const int lane = threadIdx.x & 31;
+  uint32_t v[R];
+  eval_load_row<R>(v, J, q, row, T, sw, s_cp, pc, M, N);
+  if constexpr (R == 32)
+    warp_dif_1024_pk<MASK>(v, sw, s_tw, M);
+  else
+    warp_dif_pk<R, MASK>(v, s_tw, M, pc.one_m);
   uint32_t* dst = J->ev + ((int64_t)q * J->rows + row) * N;
 #pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (32 * r + lane < N) dst[32 * r + lane] = v[r];
+  for (int r = 0; r < R; ++r) dst[32 * r + lane] = v[r];
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kEvalThreads) k_eval_w(const Job* jobs, WorkList wl, Tables T,
-                                                          PfHint pf) {
-  __shared__ uint32_t s_stage[kEvalThreads / 32][33 * 32];
-  __shared__ uint32_t s_tw[1 << (kWarpLogNMax - 1)];  // omega_N^i, i < N/2, of this block's prime
-  __shared__ uint32_t s_cp[(1 << kWarpLogNMax)];      // g^o, o < N
+// R = 1 covers every N <= 32
+__device__ __forceinline__ void eval_row_small(const Job* J, int q, int row, const Tables& T,
+                                               uint32_t* sw, const uint32_t* s_tw,
+                                               const uint32_t* s_cp, const PrimeConst& pc,
+                                               const Mod& M, int N) {
+  const int lane = threadIdx.x & 31;
+  uint32_t v[1];
+  eval_load_row<1>(v, J, q, row, T, sw, s_cp, pc, M, N);
+  if (N < 32)
+    warp_dif_short(v[0], N, s_tw, M, pc.one_m);
+  else
+    warp_dif_pk<1, 1u>(v, s_tw, M, pc.one_m);
+  if (lane < N) J->ev[((int64_t)q * J->rows + row) * N + lane] = v[0];
+  __syncwarp();
+}
+
+// one row of a transform of size N = 32 R (R = 1: any N <= 32), pruned by the row's
+// coefficient count
+template <int R>
+__device__ __forceinline__ void eval_row_class(const Job* J, int q, int row, const Tables& T,
+                                               uint32_t* sw, const uint32_t* s_tw,
+                                               const uint32_t* s_cp, const PrimeConst& pc,
+                                               const Mod& M) {
+  if constexpr (R == 1) {
+    eval_row_small(J, q, row, T, sw, s_tw, s_cp, pc, M, J->plan.N);
+  } else {
+    // how many registers of layout A the row's coefficients reach
+    const bool isf = row <= J->plan.me;
+    const int eo = ext_o(isf ? J->f : J->g, J->var);
+    if (R >= 4 && eo < 32)
+      eval_row_nz<R, 1>(J, q, row, T, sw, s_tw, s_cp, pc, M);
+    else if (R >= 4 && eo < 64)
+      eval_row_nz<R, 2>(J, q, row, T, sw, s_tw, s_cp, pc, M);
+    else
+      eval_row_nz<R, 32>(J, q, row, T, sw, s_tw, s_cp, pc, M);
+  }
+}
+
+// R > 0: every job of the list has N = 32 R (R = 1: N <= 32).  R = 0: any N up to
+// 2^kWarpLogNMax, dispatched per job (device-planned jobs, whose size the host does not
+// know).  Three blocks per SM: the largest class fits that register budget without spills.
+template <int R>
+__global__ void __launch_bounds__(kEvalThreads, 3) k_eval_w(const Job* jobs, WorkList wl,
+                                                                          Tables T, PfHint pf) {
+  constexpr int NS = R == 0 ? (1 << kWarpLogNMax) : 32 * R;  // largest transform size
+  __shared__ uint32_t s_stage[kEvalThreads / 32][(R == 32 || R == 0) ? 33 * 32 : NS];
+  __shared__ uint32_t s_tw[NS];  // packed twiddles of this block's prime
+  __shared__ uint32_t s_cp[NS];  // g^o, o < N
   const int warp = threadIdx.x >> 5;
   uint32_t* sw = s_stage[warp];
   const int nw = blockDim.x >> 5;
@@ -438,8 +473,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_w(const Job* jobs, WorkLi
     }
     prefetch_late_tables(T, kt, N, kn, blockIdx.x, min((int)gridDim.x, kPfIssuers));
   }
-  int cur_q = -1, cur_logN = -1;
-  const Job* cur_J = nullptr;
+  int cur_q = -1, cur_N = -1;
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
     const int ji = find_item(wl.off, wl.n, item);
     const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
@@ -448,118 +482,39 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_w(const Job* jobs, WorkLi
     const int groups = (rows + nw - 1) / nw;
     const int q = (int)(local / groups);
     const int row = (int)(local - (int64_t)q * groups) * nw + warp;
-    // stage this prime's twiddles (stride NT/N) and coset powers once per prime
-    const int logN = J->plan.logN;
-    if (q != cur_q || logN != cur_logN || J != cur_J) {
+    const int N = J->plan.N;
+    // stage this prime's packed twiddles and coset powers once per prime:
+    // s_tw[len + j] = omega_{2 len}^j = omega_NT^(j NT / (2 len))
+    if (q != cur_q || N != cur_N) {
       __syncthreads();
-      const int N = 1 << logN;
-      const int st = T.logNT - logN;
       const uint32_t* twq = T.tw + (int64_t)q * (T.NT >> 1);
       const uint32_t* cpq = T.cp + (int64_t)q * T.NT;
-      for (int t = threadIdx.x; t < (N >> 1); t += blockDim.x) s_tw[t] = __ldg(twq + ((int64_t)t << st));
-      for (int t = threadIdx.x; t < N; t += blockDim.x) s_cp[t] = __ldg(cpq + t);
+      for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        if (t > 0) {
+          const int lg = 31 - __clz(t);
+          s_tw[t] = __ldg(twq + ((int64_t)(t - (1 << lg)) << (T.logNT - lg - 1)));
+        }
+        s_cp[t] = __ldg(cpq + t);
+      }
       __syncthreads();
       cur_q = q;
-      cur_logN = logN;
-      cur_J = J;
+      cur_N = N;
     }
     if (row >= rows) continue;
-    switch (J->plan.logN) {
-      case 0: case 1: case 2: case 3: case 4: case 5: eval_row_warp<1>(J, q, row, T, sw, s_tw, s_cp); break;
-      case 6: eval_row_warp<2>(J, q, row, T, sw, s_tw, s_cp); break;
-      case 7: eval_row_warp<4>(J, q, row, T, sw, s_tw, s_cp); break;
-      case 8: eval_row_warp<8>(J, q, row, T, sw, s_tw, s_cp); break;
-      case 9: eval_row_warp<16>(J, q, row, T, sw, s_tw, s_cp); break;
-      default: eval_row_warp<32>(J, q, row, T, sw, s_tw, s_cp); break;
-    }
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void intt_prime_warp(const Job* J, int q, int r, const Tables& T,
-                                                uint32_t* sw) {
-  const int lane = threadIdx.x & 31;
-  const int N = J->plan.N, logN = J->plan.logN, D = J->plan.D;
-  const PrimeConst pc = T.pc[q];
-  const Mod M{pc.p, pc.pinv};
-  const uint32_t* src = J->vals + ((int64_t)q << logN);
-  uint32_t v[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) v[i] = (32 * i + lane < N) ? src[32 * i + lane] : 0u;
-  const uint32_t* itw = T.itw + (int64_t)q * (T.NT >> 1);
-  if (R == 1 && N < 32) {
-    for (int lg = 0; lg <= 4; ++lg) {
-      const int len = 1 << lg;
-      if (len >= N) break;
-      const bool upper = (lane & len) != 0;
-      const int sh = T.logNT - (lg + 1);
-      const uint32_t w = __ldg(itw + ((lane & (len - 1)) << sh));
-      const uint32_t x = v[0];
-      const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
-      const uint32_t t = mmul(upper ? x : y, w, M);
-      v[0] = upper ? msub(y, t, M.p) : madd(x, t, M.p);
-    }
-  } else if constexpr (R == 32) {
-    warp_dit_1024(v, sw, itw, T.logNT, M);
-  } else {
-    warp_dit<R>(v, itw, T.logNT, M, pc.one_m);
-  }
-#pragma unroll
-  for (int i = 0; i < R; ++i)
-    if (32 * i + lane < N) sw[32 * i + lane] = v[i];
-  __syncwarp();
-  // unscale (N^-1 g^-c) in a rolled loop; coefficients above D must vanish
-  const uint32_t* icp = T.icp + (int64_t)q * T.NT;
-  const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
-  uint32_t* dst = J->rmod + (int64_t)r * (D + 1);
-  bool bad = false;
-  for (int c = lane; c < N; c += 32) {
-    const uint32_t val = mmul(mmul(sw[c], __ldg(icp + c), M), ni, M);
-    if (c <= D)
-      dst[c] = val;
-    else if (val != 0)
-      bad = true;
-  }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(J->status, kErrInternal);
-  if (lane == 0) J->sel[r] = q;
-  __syncwarp();
-}
-
-__global__ void __launch_bounds__(kEvalThreads) k_intt_w(const Job* jobs, WorkList wl, Tables T) {
-  __shared__ uint32_t s_stage[kEvalThreads / 32][33 * 32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t* sw = s_stage[warp];
-  const int nw = blockDim.x >> 5;
-  const int64_t total = wl.off[wl.n];
-  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
-    const int ji = find_item(wl.off, wl.n, item);
-    const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
-    const int q = (int)(item - wl.off[ji]) * nw + warp;
-    const int k_need = J->plan.k_need, k_total = J->plan.k_total;
-    if (q >= k_total) continue;
-    // rank of prime q among the good primes
-    int cnt = 0;
-    for (int j = lane; j < q; j += 32) cnt += (J->pstat[j] == 0);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (q == 0) {
-      int g = 0;
-      for (int j = lane; j < k_total; j += 32) g += (J->pstat[j] == 0);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-      if (lane == 0) {
-        if (g < k_need) set_status(J->status, kErrUnlucky);
-        if (J->rejected) atomicAdd(J->rejected, k_total - g);
+    const PrimeConst pc = T.pc[q];
+    const Mod M{pc.p, pc.pinv};
+    if constexpr (R > 0) {
+      eval_row_class<R>(J, q, row, T, sw, s_tw, s_cp, pc, M);
+    } else {
+      switch (J->plan.logN) {
+        case 0: case 1: case 2: case 3: case 4: case 5:
+          eval_row_class<1>(J, q, row, T, sw, s_tw, s_cp, pc, M); break;
+        case 6: eval_row_class<2>(J, q, row, T, sw, s_tw, s_cp, pc, M); break;
+        case 7: eval_row_class<4>(J, q, row, T, sw, s_tw, s_cp, pc, M); break;
+        case 8: eval_row_class<8>(J, q, row, T, sw, s_tw, s_cp, pc, M); break;
+        case 9: eval_row_class<16>(J, q, row, T, sw, s_tw, s_cp, pc, M); break;
+        default: eval_row_class<32>(J, q, row, T, sw, s_tw, s_cp, pc, M); break;
       }
-    }
-    if (J->pstat[q] != 0 || cnt >= k_need) continue;
-    switch (J->plan.logN) {
-      case 0: case 1: case 2: case 3: case 4: case 5: intt_prime_warp<1>(J, q, cnt, T, sw); break;
-      case 6: intt_prime_warp<2>(J, q, cnt, T, sw); break;
-      case 7: intt_prime_warp<4>(J, q, cnt, T, sw); break;
-      case 8: intt_prime_warp<8>(J, q, cnt, T, sw); break;
-      case 9: intt_prime_warp<16>(J, q, cnt, T, sw); break;
-      default: intt_prime_warp<32>(J, q, cnt, T, sw); break;
     }
   }
 }
@@ -1316,11 +1271,17 @@ void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const
 void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   k_eval<<<grid, kEvalThreads, smem, s>>>(jobs, wl, T);
 }
-void launch_eval_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T, PfHint pf) {
-  k_eval_w<<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf);
-}
-void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
-  k_intt_w<<<grid, kEvalThreads, 0, s>>>(jobs, wl, T);
+void launch_eval_w(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
+                   PfHint pf) {
+  switch (cls) {
+    case -1: k_eval_w<0><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
+    case 0: k_eval_w<1><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
+    case 1: k_eval_w<2><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
+    case 2: k_eval_w<4><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
+    case 3: k_eval_w<8><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
+    case 4: k_eval_w<16><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
+    default: k_eval_w<32><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
+  }
 }
 void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   k_intt<<<grid, kEvalThreads, smem, s>>>(jobs, wl, T);

@@ -13,8 +13,11 @@ constexpr int kCrtWarpMaxK = 160; // prime counts handled by the warp-per-coeffi
 constexpr int kPlanThreads = 512; // threads of the device plan block (two halves)
 constexpr int kWarpLogNMax = 10;  // transforms up to 2^10 points run one per warp
 // device-plan offset slots (pairs [start, end) of each stage's work list)
-constexpr int kOffEvalW = 0, kOffEvalS = 2, kOffUni = 4, kOffInttW = 6, kOffInttS = 8,
-              kOffCrt = 10, kNumOffs = 12;
+constexpr int kOffEvalW = 0, kOffEvalS = 2, kOffUni = 4, kOffInttS = 6, kOffCrt = 8,
+              kNumOffs = 10;
+// size classes of the warp evaluation kernels: N <= 32, 64, 128, 256, 512, 1024
+constexpr int kNumEvalClasses = 6;
+inline int eval_class_of(int logN) { return logN <= 5 ? 0 : logN - 5; }
 
 // launchers (defined next to the kernels)
 int uni_occupancy(int cls);
@@ -30,8 +33,9 @@ struct PfHint {
   int kt, N, kn;
 };
 constexpr int kPfIssuers = 128;   // blocks that issue one prefetch chunk each
-void launch_eval_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T, PfHint pf);
-void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+// cls = eval_class_of(logN) for lists of one size class, -1 for any size (device plans)
+void launch_eval_w(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
+                   PfHint pf);
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
                 Tables T, int kmax, int lmax, int staged);
 void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T);

@@ -1,45 +1,91 @@
-// Transforms of length N = 32 R held by one warp: lane l, register r holds element
-// i = 32 r + l.  Butterflies whose partners are 32 or more apart stay in registers;
-// the last five stages of the forward transform (first five of the inverse) pair lanes
-// l and l ^ len through shuffles.
+// Forward transforms of length N = 32 R held by one warp (step (b) of the modular
+// algorithm, Sec. 5.1: evaluation at the N points of a coset of the order-N subgroup).
 //
-// Forward: decimation in frequency with omega of order N; position i ends up holding the
-// value at omega^{bitreverse(i)} (times the coset scaling applied to the input).
-// Inverse: decimation in time from that bit-reversed order; natural order out, times N.
+// Layout A: lane l, register r holds element i = 32 r + l.  Butterflies whose partners
+// are 32 or more apart stay in registers; the stages with partners closer than 32 pair
+// lanes through shuffles (R < 32) or run in registers after a transpose through shared
+// memory (R = 32, layout B: lane l, register r holds element 32 l + r).
+//
+// Decimation in frequency with omega of order N: position i ends up holding the value at
+// omega^{bitreverse(i)} (times the coset scaling applied to the input).
+//
+// Twiddles come from a packed table P with P[len + j] = omega_{2 len}^j for the stage
+// whose butterfly partners are len apart (len = 1, 2, ..., N/2; P[0] unused), so every
+// stage reads consecutive entries: lanes never collide on a shared-memory bank.  The
+// table does not depend on N, only on the prime.
+//
+// MASK marks the registers that may be nonzero on input (bit r for register r).  The
+// butterflies of the register stages are specialised at compile time: a pair with both
+// inputs zero is skipped, a pair with one zero input costs one multiplication.  Rows
+// with few coefficients (a polynomial of degree < 32 k evaluated at N points) thus skip
+// most of the first stages.
 #pragma once
 #include "modarith.cuh"
 
 namespace bs {
 
-template <int R>
-__device__ __forceinline__ void warp_dif(uint32_t (&v)[R], const uint32_t* tw, int logNT,
-                                         const Mod M, uint32_t one_m) {
-  constexpr int logR = (R >= 64) ? 6 : (R >= 32) ? 5 : (R >= 16) ? 4 : (R >= 8) ? 3 : (R >= 4) ? 2 : (R >= 2) ? 1 : 0;
-  const int lane = threadIdx.x & 31;
-  // in-register stages: len = 32 h, h = R/2 .. 1
-#pragma unroll
-  for (int lh = logR - 1; lh >= 0; --lh) {
-    const int h = 1 << lh;
-    const int lg = lh + 5;                      // len = 2^lg
-    const int sh = logNT - (lg + 1);            // twiddle stride shift
+// mask after a register stage with partner distance h: each pair with a nonzero input
+// has two nonzero outputs
+__host__ __device__ constexpr uint32_t stage_mask(uint32_t mask, int h) {
+  uint32_t out = mask;
+  for (int r = 0; r < 32; ++r)
+    if (!(r & h) && (((mask >> r) & 1u) || ((mask >> (r + h)) & 1u))) out |= (1u << r) | (1u << (r + h));
+  return out;
+}
+
+// register stages with partner distance h = 2^LH, 2^(LH-1), ..., 1 (in register
+// indices), twiddles P[LEN0 h + LEN0 (r mod h) + LANEMUL lane]: layout A uses LEN0 = 32,
+// LANEMUL = 1 (element distance 32 h); layout B uses LEN0 = 1, LANEMUL = 0.
+template <int R, int LH, uint32_t MASK, int LEN0, int LANEMUL>
+struct RegStages {
+  static __device__ __forceinline__ void run(uint32_t (&v)[R], const uint32_t* P, int lane,
+                                             const Mod& M) {
+    constexpr int h = 1 << LH;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & h) continue;
-      const int m = r & (h - 1);                // j = 32 m + lane
-      const uint32_t w = tw[(32 * m + lane) << sh];
-      const uint32_t a = v[r], b = v[r + h];
-      v[r] = madd(a, b, M.p);
-      v[r + h] = mmul(msub(a, b, M.p), w, M);
+      const bool az = !((MASK >> r) & 1u);
+      const bool bz = !((MASK >> (r + h)) & 1u);
+      if (az && bz) continue;
+      const uint32_t w = P[LEN0 * h + LEN0 * (r & (h - 1)) + LANEMUL * lane];
+      if (bz) {  // (a, 0) -> (a, a w)
+        v[r + h] = mmul(v[r], w, M);
+      } else if (az) {  // (0, b) -> (b, -b w)
+        const uint32_t b = v[r + h];
+        v[r] = b;
+        v[r + h] = mmul(mneg(b, M.p), w, M);
+      } else {
+        const uint32_t a = v[r], b = v[r + h];
+        v[r] = madd(a, b, M.p);
+        v[r + h] = mmul(msub(a, b, M.p), w, M);
+      }
     }
+    RegStages<R, LH - 1, stage_mask(MASK, h), LEN0, LANEMUL>::run(v, P, lane, M);
   }
-  // shuffle stages: len = 16 .. 1 (kept rolled: one copy of the body keeps the code
-  // small enough for the instruction cache)
+};
+
+template <int R, uint32_t MASK, int LEN0, int LANEMUL>
+struct RegStages<R, -1, MASK, LEN0, LANEMUL> {
+  static __device__ __forceinline__ void run(uint32_t (&)[R], const uint32_t*, int, const Mod&) {}
+};
+
+template <int R>
+struct Log2R {
+  static constexpr int v = (R >= 32) ? 5 : (R >= 16) ? 4 : (R >= 8) ? 3 : (R >= 4) ? 2 : (R >= 2) ? 1 : 0;
+};
+
+// N = 32 R, 2 <= R <= 16 (R = 1 with N = 32 as well): register stages, then five
+// shuffle stages (len = 16 .. 1)
+template <int R, uint32_t MASK>
+__device__ __forceinline__ void warp_dif_pk(uint32_t (&v)[R], const uint32_t* P, const Mod M,
+                                            uint32_t one_m) {
+  const int lane = threadIdx.x & 31;
+  RegStages<R, Log2R<R>::v - 1, MASK, 32, 1>::run(v, P, lane, M);
 #pragma unroll 1
   for (int lg = 4; lg >= 0; --lg) {
     const int len = 1 << lg;
     const bool upper = (lane & len) != 0;
-    const int sh = logNT - (lg + 1);
-    const uint32_t w = upper ? tw[(lane & (len - 1)) << sh] : one_m;
+    const uint32_t w = upper ? P[len + (lane & (len - 1))] : one_m;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t x = v[r];
@@ -50,55 +96,21 @@ __device__ __forceinline__ void warp_dif(uint32_t (&v)[R], const uint32_t* tw, i
   }
 }
 
-template <int R>
-__device__ __forceinline__ void warp_dit(uint32_t (&v)[R], const uint32_t* itw, int logNT,
-                                         const Mod M, uint32_t one_m) {
-  constexpr int logR = (R >= 64) ? 6 : (R >= 32) ? 5 : (R >= 16) ? 4 : (R >= 8) ? 3 : (R >= 4) ? 2 : (R >= 2) ? 1 : 0;
+// N < 32: one register per lane, lanes >= N hold zeros; stages len = N/2 .. 1
+__device__ __forceinline__ void warp_dif_short(uint32_t& v, int N, const uint32_t* P, const Mod M,
+                                               uint32_t one_m) {
   const int lane = threadIdx.x & 31;
-#pragma unroll 1
-  for (int lg = 0; lg <= 4; ++lg) {
-    const int len = 1 << lg;
+  for (int len = N >> 1; len >= 1; len >>= 1) {
     const bool upper = (lane & len) != 0;
-    const int sh = logNT - (lg + 1);
-    const uint32_t w = itw[(lane & (len - 1)) << sh];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint32_t x = v[r];
-      const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
-      // lower lane: x + y w ; upper lane: y - x w
-      const uint32_t t = mmul(upper ? x : y, w, M);
-      v[r] = upper ? msub(y, t, M.p) : madd(x, t, M.p);
-    }
+    const uint32_t w = upper ? P[len + (lane & (len - 1))] : one_m;
+    const uint32_t x = v;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
+    v = mmul(upper ? msub(y, x, M.p) : madd(x, y, M.p), w, M);
   }
-#pragma unroll
-  for (int lh = 0; lh < logR; ++lh) {
-    const int h = 1 << lh;
-    const int lg = lh + 5;
-    const int sh = logNT - (lg + 1);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (r & h) continue;
-      const int m = r & (h - 1);
-      const uint32_t w = itw[(32 * m + lane) << sh];
-      const uint32_t a = v[r];
-      const uint32_t b = mmul(v[r + h], w, M);
-      v[r] = madd(a, b, M.p);
-      v[r + h] = msub(a, b, M.p);
-    }
-  }
-  (void)one_m;
 }
 
-}  // namespace bs
-
-namespace bs {
-
-// 1024-point transforms held by one warp with every stage in registers: the stages
-// whose butterfly partners are >= 32 apart run on layout A (lane l, register r holds
-// element 32 r + l); a transpose through shared memory (row stride 33, so both the
-// row-wise writes and the column-wise reads are free of bank conflicts) switches to
-// layout B (lane l, register r holds element 32 l + r) for the stages with partners < 32
-// apart.  sw must hold 33 * 32 words private to the warp.
+// layout A <-> B through shared memory (row stride 33: row writes and column reads are
+// free of bank conflicts); sw holds 33 * 32 words private to the warp
 __device__ __forceinline__ void warp_transpose_ab(uint32_t (&v)[32], uint32_t* sw) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -119,74 +131,16 @@ __device__ __forceinline__ void warp_transpose_ba(uint32_t (&v)[32], uint32_t* s
   __syncwarp();
 }
 
-// forward (decimation in frequency), input and output in layout A
-__device__ __forceinline__ void warp_dif_1024(uint32_t (&v)[32], uint32_t* sw, const uint32_t* tw,
-                                              int logNT, const Mod M) {
+// N = 1024: five register stages in layout A (len = 512 .. 32), transpose, five register
+// stages in layout B (len = 16 .. 1), transpose back
+template <uint32_t MASK>
+__device__ __forceinline__ void warp_dif_1024_pk(uint32_t (&v)[32], uint32_t* sw, const uint32_t* P,
+                                                 const Mod M) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int lh = 4; lh >= 0; --lh) {  // len = 512 .. 32 (layout A, partner r + h)
-    const int h = 1 << lh;
-    const int sh = logNT - (lh + 6);
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      if (r & h) continue;
-      const uint32_t w = tw[(32 * (r & (h - 1)) + lane) << sh];
-      const uint32_t a = v[r], b = v[r + h];
-      v[r] = madd(a, b, M.p);
-      v[r + h] = mmul(msub(a, b, M.p), w, M);
-    }
-  }
+  RegStages<32, 4, MASK, 32, 1>::run(v, P, lane, M);
   warp_transpose_ab(v, sw);
-#pragma unroll
-  for (int lg = 4; lg >= 0; --lg) {  // len = 16 .. 1 (layout B, partner r + len)
-    const int len = 1 << lg;
-    const int sh = logNT - (lg + 1);
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      if (r & len) continue;
-      const uint32_t w = tw[(r & (len - 1)) << sh];
-      const uint32_t a = v[r], b = v[r + len];
-      v[r] = madd(a, b, M.p);
-      v[r + len] = mmul(msub(a, b, M.p), w, M);
-    }
-  }
+  RegStages<32, 4, 0xffffffffu, 1, 0>::run(v, P, lane, M);
   warp_transpose_ba(v, sw);
-}
-
-// inverse (decimation in time), input and output in layout A
-__device__ __forceinline__ void warp_dit_1024(uint32_t (&v)[32], uint32_t* sw, const uint32_t* itw,
-                                              int logNT, const Mod M) {
-  const int lane = threadIdx.x & 31;
-  warp_transpose_ab(v, sw);
-#pragma unroll
-  for (int lg = 0; lg <= 4; ++lg) {  // len = 1 .. 16 (layout B)
-    const int len = 1 << lg;
-    const int sh = logNT - (lg + 1);
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      if (r & len) continue;
-      const uint32_t w = itw[(r & (len - 1)) << sh];
-      const uint32_t a = v[r];
-      const uint32_t b = mmul(v[r + len], w, M);
-      v[r] = madd(a, b, M.p);
-      v[r + len] = msub(a, b, M.p);
-    }
-  }
-  warp_transpose_ba(v, sw);
-#pragma unroll
-  for (int lh = 0; lh <= 4; ++lh) {  // len = 32 .. 512 (layout A)
-    const int h = 1 << lh;
-    const int sh = logNT - (lh + 6);
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      if (r & h) continue;
-      const uint32_t w = itw[(32 * (r & (h - 1)) + lane) << sh];
-      const uint32_t a = v[r];
-      const uint32_t b = mmul(v[r + h], w, M);
-      v[r] = madd(a, b, M.p);
-      v[r + h] = msub(a, b, M.p);
-    }
-  }
 }
 
 }  // namespace bs
