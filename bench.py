@@ -32,6 +32,9 @@ METRIC = "exact res_y(f,g) in Z[x] per second"
 UNIT = "resultants/s"
 WORKLOAD = "res_y(f, df/dy), f dense total degree 32, signed 32-bit coefficients, seed 1"
 SEED = 1
+# DRAM bytes (read + write) of one k_unires<33> launch of this workload, from one ncu capture
+# (caches flushed between passes, as ncu does); profiles/k_unires_cfg2.md
+K3_DRAM_BYTES = 22150912
 
 
 def _args():
@@ -425,19 +428,33 @@ def run_ours(args):
     # dominant kernel: the univariate-resultant stage (ALU bound)
     alg_mulmods = instances * m_e * n_e
     achieved = alg_mulmods / (k3 * 1e-3) / 1e9
+    clk_probe = ClockSampler(local)
+    clk_probe.start()
     probe = {k: ctx.alu_probe(i) / 1e12 for i, k in
              enumerate(("mad_lo_Tops", "mad_hi_Tops", "mad_wide_Tops", "mulmod_Tops"))}
+    probe["clock_mhz"] = clk_probe.stop().get("sm_mhz") or 2070.0
     import torch.cuda as tc
     props = tc.get_device_properties(local)
     sms = props.multi_processor_count
     max_mhz = clk.get("sm_max_mhz") or 2070.0
-    # peak: SMs x max clock x 64 32-bit integer multiply lanes per SM per clock, divided by
-    # the 4 multiply-pipe issues of one Montgomery multiplication (two wide products
-    # counted twice, one low product, one high product)
-    peak = sms * max_mhz * 1e6 * 64 / 4 / 1e9
+    # peaks of the integer multiply pipe for one Montgomery multiplication (one mad.wide,
+    # one mad.lo, one mad.hi), from the per-SM-per-clock rates of those instructions that
+    # the probe measures, times SMs and the maximum clock
+    probe_mhz = probe.pop("clock_mhz")
+    per_clk = {k: probe[k] * 1e12 / (sms * probe_mhz * 1e6)
+               for k in ("mad_lo_Tops", "mad_hi_Tops", "mad_wide_Tops")}
+    mix = 1.0 / (1.0 / per_clk["mad_wide_Tops"] + 1.0 / per_clk["mad_lo_Tops"]
+                 + 1.0 / per_clk["mad_hi_Tops"])
+    peak = sms * max_mhz * 1e6 * mix / 1e9
+    # four multiplications at the full low-product rate (64 per SM per clock)
+    peak_lo = sms * max_mhz * 1e6 * 64 / 4 / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gmulmod/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": K3_DRAM_BYTES,
             "kernel": "k_unires<33>", "alg_per_launch": alg_mulmods,
+            "peak_basis": "measured mad.wide + mad.lo + mad.hi rates per SM and clock "
+                          f"({mix:.2f} Montgomery multiplications per SM per clock) x "
+                          f"{sms} SMs x {max_mhz:.0f} MHz",
+            "peak_lo_rate": peak_lo, "frac_vs_lo_rate": achieved / peak_lo,
             "note": "algorithmic m_e*n_e mulmods per (prime, point) instance"}
 
     # e2e through the C ABI with pinned host buffers

@@ -326,6 +326,7 @@ int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int v
   B.o_jobs = up.take(sizeof(Job) * n);
   B.o_eoff = up.take(sizeof(int64_t) * (n + 1));
   B.o_ioff = up.take(sizeof(int64_t) * (n + 1));
+  B.o_iwoff = up.take(sizeof(int64_t) * (n + 1));
   B.o_coff = up.take(sizeof(int64_t) * (n + 1));
   for (int c = 0; c < kNumUniClasses; ++c) {
     B.o_cids[c] = up.take(sizeof(int32_t) * std::max(B.cls_count[c], 1));
@@ -385,6 +386,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   Job* hj = (Job*)(hu + B.o_jobs);
   int64_t* eoff = (int64_t*)(hu + B.o_eoff);
   int64_t* ioff = (int64_t*)(hu + B.o_ioff);
+  int64_t* iwoff = (int64_t*)(hu + B.o_iwoff);
   int64_t* coff = (int64_t*)(hu + B.o_coff);
   int32_t* cids[kNumUniClasses];
   int64_t* coffs[kNumUniClasses];
@@ -402,7 +404,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
     eoffs[c] = (int64_t*)(hu + B.o_eoffs[c]);
     eoffs[c][0] = 0;
   }
-  eoff[0] = ioff[0] = coff[0] = 0;
+  eoff[0] = ioff[0] = iwoff[0] = coff[0] = 0;
   size_t in_pos = 0, ps_pos = 0;
   B.instances = B.mulmods = B.k_need_sum = B.k_total_sum = 0;
   B.maxpts = B.maxprimes = 0;
@@ -421,7 +423,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
     J.out = (uint32_t*)(base + B.o_out[i]);
     J.status = (int32_t*)(base + B.o_status);
     J.rejected = (int32_t*)(base + B.o_status) + 1;
-    int64_t ne = 0, ni = 0, nu = 0;
+    int64_t ne = 0, ni = 0, niw = 0, nu = 0;
     if (!P.trivial) {
       J.rows = (P.me + 1) + (P.ne + 1);
       J.ev = (uint32_t*)(base + B.o_ev[i]);
@@ -438,7 +440,11 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
       } else {
         ne = (int64_t)P.k_total * J.rows;
       }
-      ni = P.k_total;  // interpolation: one block per prime
+      // interpolation: one warp per prime up to 2^kWarpLogNMax points, else one block
+      if (P.logN <= kWarpInttLogNMax)
+        niw = P.k_total;
+      else
+        ni = P.k_total;
       nu = (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile;
       const int c = uni_class_of(std::max(P.me, P.ne) + 1);
       cids[c][cfill[c]] = i;
@@ -454,6 +460,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
     hj[i] = J;
     eoff[i + 1] = eoff[i] + ne;
     ioff[i + 1] = ioff[i] + ni;
+    iwoff[i + 1] = iwoff[i] + niw;
     coff[i + 1] = coff[i] + (J.cap_deg + kCrtTile) / kCrtTile;
   }
   cudaStream_t s = ctx->stream;
@@ -465,6 +472,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   L.jobs = (const Job*)(base + B.o_jobs);
   L.eval = WorkList{nullptr, (const int64_t*)(base + B.o_eoff), n};
   L.intt = WorkList{nullptr, (const int64_t*)(base + B.o_ioff), n};
+  L.intt_w = WorkList{nullptr, (const int64_t*)(base + B.o_iwoff), n};
   L.crt = WorkList{nullptr, (const int64_t*)(base + B.o_coff), n};
   for (int c = 0; c < kNumUniClasses; ++c) {
     L.uni[c] = WorkList{(const int32_t*)(base + B.o_cids[c]), (const int64_t*)(base + B.o_coffs[c]),
@@ -479,6 +487,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   L.evw_any_items = 0;
   L.eval_items = eoff[n];
   L.intt_items = ioff[n];
+  L.intt_w_items = iwoff[n];
   L.crt_items = coff[n];
   L.maxN = B.maxN;
   L.kmax = B.kmax;

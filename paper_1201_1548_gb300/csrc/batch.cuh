@@ -19,7 +19,7 @@ struct HostBatch {
   int cls_count[kNumUniClasses] = {0, 0, 0, 0, 0, 0};
   int ecls_count[kNumEvalClasses] = {0, 0, 0, 0, 0, 0};
   // layout: [upload | compute | download], offsets from the region's base
-  size_t o_jobs = 0, o_eoff = 0, o_ioff = 0, o_coff = 0;
+  size_t o_jobs = 0, o_eoff = 0, o_ioff = 0, o_iwoff = 0, o_coff = 0;
   size_t o_cids[kNumUniClasses] = {}, o_coffs[kNumUniClasses] = {};
   size_t o_eids[kNumEvalClasses] = {}, o_eoffs[kNumEvalClasses] = {};
   size_t o_status = 0, o_pstat = 0, o_in = 0, up_bytes = 0;

@@ -45,6 +45,10 @@ struct Tables {
   const uint32_t* cp;    // [Tt][NT] g^i (Montgomery)
   const uint32_t* icp;   // [Tt][NT] g^-i (standard form)
   const uint32_t* ninv;  // [Tt][kLogNMax + 1] 2^-s (Montgomery form)
+  // packed twiddles [Tt][NT]: twp[len + j] = omega_{2 len}^j, itwp[len + j] = omega_{2 len}^-j
+  // (len = 1, 2, ..., NT/2; j < len; entry 0 is 1), Montgomery form
+  const uint32_t* twp;
+  const uint32_t* itwp;
   // Garner table for the first Tg primes: ginv[a * Tg + b] = p_a^-1 mod p_b (Montgomery)
   const uint32_t* ginv;
   // prefix products of the table primes: pp[j * LPP + l] = limb l of p_0 ... p_{j-1}

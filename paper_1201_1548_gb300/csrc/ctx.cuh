@@ -67,11 +67,11 @@ struct MetaBounds {
 
 struct StageLaunch {
   const Job* jobs;
-  WorkList eval, intt, crt;
+  WorkList eval, intt, intt_w, crt;
   WorkList evw[kNumEvalClasses];  // warp evaluation, one list per transform-size class
   WorkList evw_any;               // warp evaluation of any size class (device plans)
   WorkList uni[kNumUniClasses];
-  int64_t eval_items, intt_items, crt_items;
+  int64_t eval_items, intt_items, intt_w_items, crt_items;
   int64_t evw_items[kNumEvalClasses], evw_any_items;
   int64_t uni_items[kNumUniClasses];
   int maxN, kmax, lmax;

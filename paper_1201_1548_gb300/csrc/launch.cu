@@ -66,8 +66,10 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
     if (g) launch_uni(c, g, s, L.jobs, L.uni[c], Tv);
   }
   mark(ctx, 3, s);
+  g = grid_for((L.intt_w_items + kInttWarps - 1) / kInttWarps, (int64_t)sms * 8);
+  if (g) launch_intt_w(g, s, L.jobs, L.intt_w, Tv);
   g = grid_for(L.intt_items, (int64_t)sms * 8);
-  if (g) launch_intt(g, tsmem + tsmem / 2, s, L.jobs, L.intt, Tv);  // values + twiddles
+  if (g) launch_intt(g, 2 * tsmem, s, L.jobs, L.intt, Tv);  // values + packed twiddles
   mark(ctx, 4, s);
   g = grid_for(L.crt_items, (int64_t)sms * 4);
   const size_t wsm = crt_warp_smem(L.kmax, L.lmax);
@@ -80,7 +82,7 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
 
 int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_graph) {
   cudaStream_t s = ctx->stream;
-  if ((size_t)L.maxN * sizeof(uint32_t) > (size_t)ctx->smem_optin)
+  if (2 * (size_t)L.maxN * sizeof(uint32_t) > (size_t)ctx->smem_optin)  // interpolation block
     return ctx_fail(ctx, kErrRange, "transform size exceeds shared memory");
   size_t crt_smem = 0;
   int crt_staged = 0;
@@ -132,7 +134,7 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   cudaStream_t s = ctx->stream;
   const Tables Tv = ctx->tabs->view();
   const int N = 1 << mb.logN;
-  if ((size_t)N * sizeof(uint32_t) > (size_t)ctx->smem_optin)
+  if (2 * (size_t)N * sizeof(uint32_t) > (size_t)ctx->smem_optin)  // interpolation block
     return ctx_fail(ctx, kErrRange, "transform size exceeds shared memory");
   if (ctx->profile)
     for (int i = 0; i < kProfEvents; ++i) ctx->prof_rec[i] = false;
@@ -154,11 +156,14 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   }
   L.uni_items[cls] = (((int64_t)mb.k_total << mb.logN) + kUniTile - 1) / kUniTile;
   L.intt = WorkList{nullptr, offs + kOffInttS, 1};
+  L.intt_w = WorkList{nullptr, offs + kOffInttW, 1};
   L.crt = WorkList{nullptr, offs + kOffCrt, 1};
   // the transform size is known on the device only: one kernel dispatches per job
   L.evw_any = WorkList{nullptr, offs + kOffEvalW, 1};
   L.evw_any_items = (int64_t)mb.k_total * ((mb.rows + 7) / 8);
   L.eval_items = wsize ? 0 : (int64_t)mb.k_total * mb.rows;
+  // a single job has few primes: one block per prime (no second, possibly empty launch)
+  L.intt_w_items = 0;
   L.intt_items = mb.k_total;
   L.crt_items = ((int64_t)J.cap_deg + kCrtTile) / kCrtTile;
   L.maxN = N;

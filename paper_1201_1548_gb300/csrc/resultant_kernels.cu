@@ -54,7 +54,7 @@ __device__ void prefetch_late_tables(const Tables& T, int kt, int N, int kn, int
   int64_t mwords = 0;  // the M_k block of k = K
   if (K >= 1) mwords = (int64_t)K * ws_len(K);
   const PfRange R[6] = {
-      {T.itw, sizeof(uint32_t) * (size_t)kt * (T.NT >> 1)},
+      {T.itwp, sizeof(uint32_t) * (size_t)kt * T.NT},
       {T.icp, sizeof(uint32_t) * (size_t)kt * T.NT},
       {T.ginv, sizeof(uint32_t) * (size_t)kt * T.Tg},
       {T.pp, sizeof(uint32_t) * (size_t)(kn + 1) * T.LPP},
@@ -251,13 +251,14 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
     J.rows = (P.trivial || P.status) ? 0 : (P.me + 1) + (P.ne + 1);
     const bool run = (P.status == 0 && P.trivial == 0);
     *dst = J;
-    // offsets of the stages (one job each): warp eval, smem eval, unires tiles, intt,
-    // crt tiles
+    // offsets of the stages (one job each): warp eval, smem eval, unires tiles, warp
+    // intt, smem intt, crt tiles
     const bool wsize = P.logN <= kWarpLogNMax;
     for (int s = 0; s < kNumOffs; s += 2) offs[s] = 0;
     offs[kOffEvalW + 1] = (run && wsize) ? (int64_t)P.k_total * ((J.rows + 7) / 8) : 0;
     offs[kOffEvalS + 1] = (run && !wsize) ? (int64_t)P.k_total * J.rows : 0;
     offs[kOffUni + 1] = run ? (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile : 0;
+    offs[kOffInttW + 1] = 0;  // a single job interpolates one block per prime
     offs[kOffInttS + 1] = run ? P.k_total : 0;
     offs[kOffCrt + 1] = ((int64_t)J.cap_deg + kCrtTile) / kCrtTile;
   }
@@ -296,18 +297,18 @@ __device__ __forceinline__ void dif_ntt(uint32_t* sm, int logN, const uint32_t* 
 
 // in-place inverse transform (decimation in time) of bit-reversed input; output natural
 // order, scaled by N
-__device__ __forceinline__ void dit_intt(uint32_t* sm, int logN, const uint32_t* itw, int logNT,
-                                         const Mod M) {
+// inverse transform in shared memory; Pi holds the packed inverse twiddles
+// (Pi[len + j] = omega_{2 len}^-j), so the threads of a stage read consecutive words
+__device__ __forceinline__ void dit_intt(uint32_t* sm, int logN, const uint32_t* Pi, const Mod M) {
   const int N = 1 << logN;
   for (int lg = 0; lg < logN; ++lg) {
     const int len = 1 << lg;
-    const int stride_sh = logNT - (lg + 1);
     for (int bf = threadIdx.x; bf < (N >> 1); bf += blockDim.x) {
       const int j = bf & (len - 1);
       const int i0 = ((bf >> lg) << (lg + 1)) + j;
       const int i1 = i0 + len;
       const uint32_t u = sm[i0];
-      const uint32_t v = mmul(sm[i1], itw[j << stride_sh], M);
+      const uint32_t v = mmul(sm[i1], Pi[len + j], M);
       sm[i0] = madd(u, v, M.p);
       sm[i1] = msub(u, v, M.p);
     }
@@ -483,17 +484,14 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_w(const Job* jobs, Wor
     const int q = (int)(local / groups);
     const int row = (int)(local - (int64_t)q * groups) * nw + warp;
     const int N = J->plan.N;
-    // stage this prime's packed twiddles and coset powers once per prime:
-    // s_tw[len + j] = omega_{2 len}^j = omega_NT^(j NT / (2 len))
+    // stage this prime's packed twiddles (s_tw[len + j] = omega_{2 len}^j) and coset
+    // powers once per prime
     if (q != cur_q || N != cur_N) {
       __syncthreads();
-      const uint32_t* twq = T.tw + (int64_t)q * (T.NT >> 1);
+      const uint32_t* twq = T.twp + (int64_t)q * T.NT;
       const uint32_t* cpq = T.cp + (int64_t)q * T.NT;
       for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        if (t > 0) {
-          const int lg = 31 - __clz(t);
-          s_tw[t] = __ldg(twq + ((int64_t)(t - (1 << lg)) << (T.logNT - lg - 1)));
-        }
+        s_tw[t] = __ldg(twq + t);
         s_cp[t] = __ldg(cpq + t);
       }
       __syncthreads();
@@ -598,15 +596,14 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
     const uint32_t* src = J->vals + ((int64_t)q << logN);
     for (int t = threadIdx.x; t < N; t += blockDim.x) sm[t] = src[t];
     __syncthreads();
-    // this prime's inverse twiddles at stride NT / N, staged after the values
+    // this prime's packed inverse twiddles, staged after the values
     uint32_t* sit = sm + N;
     {
-      const int st = T.logNT - logN;
-      const uint32_t* itq = T.itw + (int64_t)q * (T.NT >> 1);
-      for (int t = threadIdx.x; t < (N >> 1); t += blockDim.x) sit[t] = __ldg(itq + ((int64_t)t << st));
+      const uint32_t* itq = T.itwp + (int64_t)q * T.NT;
+      for (int t = threadIdx.x; t < N; t += blockDim.x) sit[t] = __ldg(itq + t);
     }
     __syncthreads();
-    dit_intt(sm, logN, sit, logN, M);
+    dit_intt(sm, logN, sit, M);
     const uint32_t* icp = T.icp + (int64_t)q * T.NT;
     const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
     uint32_t* dst = J->rmod + (int64_t)r * (D + 1);
@@ -621,6 +618,96 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
     if (bad) set_status(J->status, kErrInternal);
     if (threadIdx.x == 0) J->sel[r] = q;
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// prime selection + (d) for N <= 2^kWarpInttLogNMax: one warp per (job, prime), the
+// inverse transform in registers (larger transforms have too few primes to fill the GPU
+// one warp each; they run one block per prime)
+// ------------------------------------------------------------------------------------
+template <int R>
+__device__ __forceinline__ void intt_prime_warp(const Job* J, int q, int r, const Tables& T,
+                                                uint32_t* sw, uint32_t* Pi) {
+  const int lane = threadIdx.x & 31;
+  const int logN = J->plan.logN;
+  const int N = 1 << logN;
+  const int D = J->plan.D;
+  const PrimeConst pc = T.pc[q];
+  const Mod M{pc.p, pc.pinv};
+  const uint32_t* src = J->vals + ((int64_t)q << logN);
+  // the prime's packed inverse twiddles, staged in this warp's shared slice (all loads in
+  // flight at once instead of one L2 round trip per butterfly)
+  const uint32_t* Pg = T.itwp + (int64_t)q * T.NT;
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+    if (32 * k + lane < N) Pi[32 * k + lane] = __ldg(Pg + 32 * k + lane);
+  uint32_t v[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = (32 * k + lane < N) ? src[32 * k + lane] : 0u;
+  __syncwarp();
+  if constexpr (R == 32)
+    warp_dit_1024_pk(v, sw, Pi, M);
+  else
+    warp_dit_pk<R>(v, N, Pi, M);
+  const uint32_t* icp = T.icp + (int64_t)q * T.NT;
+  const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
+  uint32_t* dst = J->rmod + (int64_t)r * (D + 1);
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int i = 32 * k + lane;
+    if (i >= N) continue;
+    const uint32_t x = mmul(mmul(v[k], icp[i], M), ni, M);
+    if (i <= D)
+      dst[i] = x;
+    else if (x != 0)
+      bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(J->status, kErrInternal);
+  if (lane == 0) J->sel[r] = q;
+  __syncwarp();  // Pi and sw are reused by the warp's next prime
+}
+
+__global__ void __launch_bounds__(kInttWarps * 32) k_intt_w(const Job* jobs, WorkList wl, Tables T) {
+  __shared__ uint32_t s_stage[kInttWarps][32];
+  __shared__ uint32_t s_tw[kInttWarps][1 << kWarpInttLogNMax];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* sw = s_stage[warp];
+  uint32_t* Pi = s_tw[warp];
+  const int64_t total = wl.off[wl.n];
+  for (int64_t item = (int64_t)blockIdx.x * kInttWarps + warp; item < total;
+       item += (int64_t)gridDim.x * kInttWarps) {
+    const int ji = find_item(wl.off, wl.n, item);
+    const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
+    const int q = (int)(item - wl.off[ji]);
+    const int k_need = J->plan.k_need, k_total = J->plan.k_total;
+    // rank of prime q among the good primes (ballots over the prime flags); the warp of
+    // prime 0 also checks that enough good primes exist
+    int r = 0;
+    for (int j0 = 0; j0 < q; j0 += 32) {
+      const int j = j0 + lane;
+      r += __popc(__ballot_sync(0xffffffffu, j < q && J->pstat[j] == 0));
+    }
+    if (q == 0) {
+      int good = 0;
+      for (int j0 = 0; j0 < k_total; j0 += 32) {
+        const int j = j0 + lane;
+        good += __popc(__ballot_sync(0xffffffffu, j < k_total && J->pstat[j] == 0));
+      }
+      if (lane == 0) {
+        if (good < k_need) set_status(J->status, kErrUnlucky);
+        if (J->rejected) atomicAdd(J->rejected, k_total - good);
+      }
+    }
+    if (J->pstat[q] != 0 || r >= k_need) continue;  // uniform across the warp
+    switch (J->plan.logN) {
+      case 0: case 1: case 2: case 3: case 4: case 5: intt_prime_warp<1>(J, q, r, T, sw, Pi); break;
+      case 6: intt_prime_warp<2>(J, q, r, T, sw, Pi); break;
+      case 7: intt_prime_warp<4>(J, q, r, T, sw, Pi); break;
+      case 8: intt_prime_warp<8>(J, q, r, T, sw, Pi); break;
+      default: intt_prime_warp<16>(J, q, r, T, sw, Pi); break;
+    }
   }
 }
 
@@ -1282,6 +1369,9 @@ void launch_eval_w(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList 
     case 4: k_eval_w<16><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
     default: k_eval_w<32><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
   }
+}
+void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
+  k_intt_w<<<grid, kInttWarps * 32, 0, s>>>(jobs, wl, T);
 }
 void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   k_intt<<<grid, kEvalThreads, smem, s>>>(jobs, wl, T);

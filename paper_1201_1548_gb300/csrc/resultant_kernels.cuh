@@ -13,8 +13,10 @@ constexpr int kCrtWarpMaxK = 160; // prime counts handled by the warp-per-coeffi
 constexpr int kPlanThreads = 512; // threads of the device plan block (two halves)
 constexpr int kWarpLogNMax = 10;  // transforms up to 2^10 points run one per warp
 // device-plan offset slots (pairs [start, end) of each stage's work list)
-constexpr int kOffEvalW = 0, kOffEvalS = 2, kOffUni = 4, kOffInttS = 6, kOffCrt = 8,
-              kNumOffs = 10;
+constexpr int kOffEvalW = 0, kOffEvalS = 2, kOffUni = 4, kOffInttW = 6, kOffInttS = 8,
+              kOffCrt = 10, kNumOffs = 12;
+constexpr int kInttWarps = 4;     // warps (primes) of a warp-interpolation block
+constexpr int kWarpInttLogNMax = 9;  // interpolations up to 2^9 points run one per warp
 // size classes of the warp evaluation kernels: N <= 32, 64, 128, 256, 512, 1024
 constexpr int kNumEvalClasses = 6;
 inline int eval_class_of(int logN) { return logN <= 5 ? 0 : logN - 5; }
@@ -26,6 +28,8 @@ void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const
                        int lda, const uint32_t* b, int db, int ldb, uint32_t* res, Tables T);
 void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+// one warp per (job, prime) for N <= 2^kWarpInttLogNMax
+void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_crt_w(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
                   int kmax, int lmax);
 // sizes for the L2 prefetch the evaluation kernel issues (kt < 0: read the first job's plan)

@@ -142,6 +142,27 @@ __global__ void k_init_transform(const PrimeConst* pc, const uint32_t* omega_m,
   }
 }
 
+// packed twiddles: P[len + j] = omega_{2 len}^{+-j} = tw[j NT / (2 len)] for len = 1 .. NT/2,
+// j < len (entry 0 holds 1); every transform stage then reads consecutive entries
+__global__ void k_init_packed(const PrimeConst* pc, int Tt, int NT, int logNT, const uint32_t* tw,
+                              const uint32_t* itw, uint32_t* twp, uint32_t* itwp) {
+  const int64_t total = (int64_t)Tt * NT;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / NT);
+    const int t = (int)(idx - (int64_t)q * NT);
+    if (t == 0) {
+      twp[idx] = pc[q].one_m;
+      itwp[idx] = pc[q].one_m;
+      continue;
+    }
+    const int lg = 31 - __clz(t);
+    const int64_t src = (int64_t)q * (NT / 2) + ((int64_t)(t - (1 << lg)) << (logNT - lg - 1));
+    twp[idx] = tw[src];
+    itwp[idx] = itw[src];
+  }
+}
+
 __global__ void k_init_garner(const PrimeConst* pc, int Tg, uint32_t* ginv) {
   const int64_t total = (int64_t)Tg * Tg;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -248,8 +269,9 @@ int DeviceTables::init(cudaStream_t s) {
 void DeviceTables::release() {
   for (void* p : {(void*)pc, (void*)pw, (void*)mpw, (void*)lgp, (void*)tw, (void*)itw,
                   (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp, (void*)ws_m,
-                  (void*)ws_y, (void*)ws_moff, (void*)ws_yoff, (void*)q62})
+                  (void*)ws_y, (void*)ws_moff, (void*)ws_yoff, (void*)q62, (void*)twp, (void*)itwp})
     if (p) cudaFree(p);
+  twp = itwp = nullptr;
   ws_m = ws_y = q62 = nullptr;
   ws_moff = nullptr;
   ws_yoff = nullptr;
@@ -277,10 +299,12 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   // finish any work that may still read the old tables
   if (cudaStreamSynchronize(s) != cudaSuccess) return kErrCuda;
   uint32_t *ntw = nullptr, *nitw = nullptr, *ncp = nullptr, *nicp = nullptr, *nninv = nullptr,
-           *nginv = nullptr, *omega = nullptr, *gi = nullptr;
+           *nginv = nullptr, *omega = nullptr, *gi = nullptr, *ntwp = nullptr, *nitwp = nullptr;
   int rc = 0;
   rc |= cu_fail(cudaMalloc(&ntw, sizeof(uint32_t) * (size_t)newT * (newNT / 2)));
   rc |= cu_fail(cudaMalloc(&nitw, sizeof(uint32_t) * (size_t)newT * (newNT / 2)));
+  rc |= cu_fail(cudaMalloc(&ntwp, sizeof(uint32_t) * (size_t)newT * newNT));
+  rc |= cu_fail(cudaMalloc(&nitwp, sizeof(uint32_t) * (size_t)newT * newNT));
   rc |= cu_fail(cudaMalloc(&ncp, sizeof(uint32_t) * (size_t)newT * newNT));
   rc |= cu_fail(cudaMalloc(&nicp, sizeof(uint32_t) * (size_t)newT * newNT));
   rc |= cu_fail(cudaMalloc(&nninv, sizeof(uint32_t) * (size_t)newT * (kLogNMax + 1)));
@@ -292,7 +316,7 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   rc |= cu_fail(cudaMalloc(&gi, sizeof(uint32_t) * newT));
   if (rc) {
     for (void* p : {(void*)ntw, (void*)nitw, (void*)ncp, (void*)nicp, (void*)nninv, (void*)nginv,
-                    (void*)omega, (void*)gi})
+                    (void*)omega, (void*)gi, (void*)ntwp, (void*)nitwp})
       if (p) cudaFree(p);
     return kErrNoMem;
   }
@@ -306,6 +330,8 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   rc |= cu_fail(cudaMemcpyAsync(omega, om.data(), sizeof(uint32_t) * newT, cudaMemcpyHostToDevice, s));
   rc |= cu_fail(cudaMemcpyAsync(gi, gim.data(), sizeof(uint32_t) * newT, cudaMemcpyHostToDevice, s));
   k_init_transform<<<1024, 256, 0, s>>>(pc, omega, gi, newT, newNT, newLog, ntw, nitw, ncp, nicp, nninv);
+  rc |= cu_fail(cudaGetLastError());
+  k_init_packed<<<1024, 256, 0, s>>>(pc, newT, newNT, newLog, ntw, nitw, ntwp, nitwp);
   rc |= cu_fail(cudaGetLastError());
   k_init_garner<<<1024, 256, 0, s>>>(pc, newT, nginv);
   rc |= cu_fail(cudaGetLastError());
@@ -341,8 +367,11 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   cudaFree(omega);
   cudaFree(gi);
   for (void* p : {(void*)tw, (void*)itw, (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp,
-                  (void*)ws_m, (void*)ws_y, (void*)ws_moff, (void*)ws_yoff, (void*)q62})
+                  (void*)ws_m, (void*)ws_y, (void*)ws_moff, (void*)ws_yoff, (void*)q62, (void*)twp,
+                  (void*)itwp})
     if (p) cudaFree(p);
+  twp = ntwp;
+  itwp = nitwp;
   ws_m = nwsm;
   ws_y = nwsy;
   ws_moff = nmoff;
@@ -373,6 +402,8 @@ Tables DeviceTables::view() const {
   t.lg_prefix = lgp;
   t.tw = tw;
   t.itw = itw;
+  t.twp = twp;
+  t.itwp = itwp;
   t.cp = cp;
   t.icp = icp;
   t.ninv = ninv;

@@ -144,3 +144,61 @@ __device__ __forceinline__ void warp_dif_1024_pk(uint32_t (&v)[32], uint32_t* sw
 }
 
 }  // namespace bs
+
+namespace bs {
+
+// ---- inverse transforms (decimation in time), bit-reversed order in, natural order out
+// (times N); Pi[len + j] = omega_{2 len}^-j.  A butterfly maps (a, b) to (a + b w, a - b w).
+
+// register stages with partner distance h = 1, 2, ..., 2^LH (in register indices)
+template <int R, int LH, int LEN0, int LANEMUL>
+__device__ __forceinline__ void reg_stages_dit(uint32_t (&v)[R], const uint32_t* Pi, int lane,
+                                               const Mod& M) {
+#pragma unroll
+  for (int lh = 0; lh <= LH; ++lh) {
+    const int h = 1 << lh;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & h) continue;
+      const uint32_t w = Pi[LEN0 * h + LEN0 * (r & (h - 1)) + LANEMUL * lane];
+      const uint32_t a = v[r];
+      const uint32_t b = mmul(v[r + h], w, M);
+      v[r] = madd(a, b, M.p);
+      v[r + h] = msub(a, b, M.p);
+    }
+  }
+}
+
+// N = 32 R, R <= 16 (R = 1 also covers N < 32): shuffle stages len = 1 .. min(16, N/2)
+// within each register (elements 32 r .. 32 r + 31), then the register stages
+template <int R>
+__device__ __forceinline__ void warp_dit_pk(uint32_t (&v)[R], int N, const uint32_t* Pi, const Mod M) {
+  const int lane = threadIdx.x & 31;
+  const int nmax = (N < 32 ? N : 32) >> 1;
+#pragma unroll 1
+  for (int len = 1; len <= nmax; len <<= 1) {
+    const bool upper = (lane & len) != 0;
+    const uint32_t w = Pi[len + (lane & (len - 1))];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t x = v[r];
+      const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
+      const uint32_t t = mmul(upper ? x : y, w, M);
+      v[r] = upper ? msub(y, t, M.p) : madd(x, t, M.p);
+    }
+  }
+  reg_stages_dit<R, Log2R<R>::v - 1, 32, 1>(v, Pi, lane, M);
+}
+
+// N = 1024: layout A in, transpose to B, stages len = 1 .. 16 in registers, transpose
+// back, stages len = 32 .. 512 in registers
+__device__ __forceinline__ void warp_dit_1024_pk(uint32_t (&v)[32], uint32_t* sw, const uint32_t* Pi,
+                                                 const Mod M) {
+  const int lane = threadIdx.x & 31;
+  warp_transpose_ab(v, sw);
+  reg_stages_dit<32, 4, 1, 0>(v, Pi, lane, M);
+  warp_transpose_ba(v, sw);
+  reg_stages_dit<32, 4, 32, 1>(v, Pi, lane, M);
+}
+
+}  // namespace bs
