@@ -243,6 +243,17 @@ def _bench_batched(bs, ctx, reps=3):
     batch_call()                                                # warm-up (tables, graph)
     st = bs._abi._Stats()
     lib.bs_last_stats(ctx.h, C.byref(st))
+    tb_default = min(batch_call() for _ in range(reps))
+    # launch shapes autotuned on this batch (stage times by CUDA events), then timed again
+    info = bs._abi._TuneInfo()
+    rc = lib.bs_autotune_batch(ctx.h, n, F, G, 1, C.byref(info))
+    if rc:
+        raise SystemExit(f"bs_autotune_batch failed: {rc}")
+    tune = {"eval_warps": info.eval_warps, "eval_blocks_per_sm": info.eval_blocks_per_sm,
+            "uni_threads": list(info.uni_threads), "crt_tile": info.crt_tile,
+            "crt_blocks_per_sm": info.crt_blocks_per_sm, "trials": info.trials,
+            "stage_ms_default": info.ms_default, "stage_ms_tuned": info.ms_tuned}
+    batch_call()
     tb = min(batch_call() for _ in range(reps))
     ref = [bs.limbs_to_ints(bufs[i], O[i].deg + 1, O[i].limbs) if O[i].deg >= 0 else []
            for i in range(n)]
@@ -267,7 +278,8 @@ def _bench_batched(bs, ctx, reps=3):
             raise SystemExit(f"batched and single results differ at pair {i}")
     return {"workload": "4096 pairs, total degrees 4-24, 8-64-bit coefficients, 20% zeros, "
                         "seed 1 (host buffers, planning and copies included)",
-            "pairs": n, "ms_batch": tb * 1e3, "ms_one_call_per_resultant": t1 * 1e3,
+            "pairs": n, "ms_batch": tb * 1e3, "ms_batch_default_shapes": tb_default * 1e3,
+            "autotuned": tune, "ms_one_call_per_resultant": t1 * 1e3,
             "resultants_per_s_batch": n / tb, "resultants_per_s_one_by_one": n / t1,
             "speedup": t1 / tb, "instances": st.instances, "mulmods_alg": st.mulmods_alg,
             "modp_univariate_resultants_per_s": st.instances / tb}

@@ -250,6 +250,36 @@ int bs_gcd_z(bs_ctx *ctx, const bs_upoly *a, const bs_upoly *b, bs_upoly *out);
 int bs_modgcd_batch(bs_ctx *ctx, int n, const int *kind, const bs_upoly *a, const bs_upoly *b,
                     bs_upoly *out);
 
+/* Launch shapes of the batched stages (bs_autotune_batch). */
+typedef struct {
+  int32_t eval_warps;          /* rows (one warp each) per evaluation block, 1..8 */
+  int32_t eval_blocks_per_sm;  /* cap of the persistent evaluation grid */
+  int32_t uni_threads[6];      /* threads per univariate-resultant block by degree class
+                                  (eliminated-variable length <= 8, 16, 24, 33, 48, 65): 64, 128 or 256 */
+  int32_t crt_tile;            /* coefficients (one warp each) per reconstruction block: 1, 2, 4, 8 */
+  int32_t crt_blocks_per_sm;   /* cap of the persistent reconstruction grid */
+  float ms_default;            /* device time of the batch's stages with the default shapes */
+  float ms_tuned;              /* ... with the chosen shapes (CUDA events, best of two runs) */
+  int32_t trials;              /* shape combinations measured */
+} bs_tune_info;
+
+/* Autotune the launch shapes for batches like this one: plans and uploads the batch, then
+ * runs its stages on the context's stream once per candidate shape (coordinate descent:
+ * evaluation warps per block and grid, univariate threads per block for each degree
+ * class present, reconstruction tile and grid), keeping for each stage the shape with the
+ * least device time.  The chosen shapes stay on the context and apply to its later
+ * bs_resultant_batch and bs_resultant calls (not to the device-planned entry points);
+ * *info (may be NULL) receives them.  Results are not returned; the call waits for the
+ * device.  Errors as bs_resultant_batch. */
+int bs_autotune_batch(bs_ctx *ctx, int n, const bs_bipoly *f, const bs_bipoly *g, int var,
+                      bs_tune_info *info);
+
+/* Set the batched launch shapes explicitly (t == NULL restores the defaults: 8 warps and
+ * 8 blocks per SM for evaluation, 128 threads per univariate block, 8 coefficients and 4
+ * blocks per SM for reconstruction).  The timing fields of *t are ignored.  BS_ERR_ARG for
+ * a shape outside the ranges of bs_tune_info. */
+int bs_set_tune(bs_ctx *ctx, const bs_tune_info *t);
+
 /* ---------------------------------------------------------------------------------
  * Serving: continuous batching of resultant and gcd jobs
  *

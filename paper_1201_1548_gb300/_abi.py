@@ -18,8 +18,15 @@ EXPORTED_SYMBOLS = [
     "bs_device_status", "bs_resultant_batch", "bs_uni_resultant_modp", "bs_prime_table",
     "bs_gcd_modp", "bs_squarefree_part", "bs_plan", "bs_alu_probe", "bs_profile",
     "bs_stage_times", "bs_resultant_device_noalloc", "bs_gcd_z", "bs_modgcd_batch",
-    "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
+    "bs_autotune_batch", "bs_set_tune", "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
 ]
+
+
+class _TuneInfo(C.Structure):
+    _fields_ = [("eval_warps", C.c_int32), ("eval_blocks_per_sm", C.c_int32),
+                ("uni_threads", C.c_int32 * 6), ("crt_tile", C.c_int32),
+                ("crt_blocks_per_sm", C.c_int32), ("ms_default", C.c_float),
+                ("ms_tuned", C.c_float), ("trials", C.c_int32)]
 
 
 class BsError(RuntimeError):
@@ -115,6 +122,9 @@ def load_library():
     lib.bs_stage_times.argtypes = [P, P, I]
     lib.bs_plan.argtypes = [C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, C.POINTER(_PlanInfo)]
     lib.bs_gcd_z.argtypes = [P, C.POINTER(_Upoly), C.POINTER(_Upoly), C.POINTER(_Upoly)]
+    lib.bs_autotune_batch.argtypes = [P, I, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I,
+                                      C.POINTER(_TuneInfo)]
+    lib.bs_set_tune.argtypes = [P, C.POINTER(_TuneInfo)]
     lib.bs_modgcd_batch.argtypes = [P, I, P, P, P, P]
     lib.bs_serve_start.argtypes = [P, I, I, C.c_size_t]
     lib.bs_serve_stop.argtypes = [P]
@@ -409,6 +419,31 @@ class Context:
         info = _ServeInfo()
         self._check(self.lib.bs_serve_stats(self.h, C.byref(info)))
         return {name: getattr(info, name) for name, _ in _ServeInfo._fields_}
+
+    def autotune_batch(self, pairs, var=1):
+        """Tune the batched launch shapes on these pairs; returns the chosen shapes."""
+        n = len(pairs)
+        F, G, keep = (_Bipoly * n)(), (_Bipoly * n)(), []
+        for i, (f, g) in enumerate(pairs):
+            af, dxf, dyf, Lf = bipoly_to_limbs(f)
+            ag, dxg, dyg, Lg = bipoly_to_limbs(g)
+            keep += [af, ag]
+            F[i] = _bip(af, dxf, dyf, Lf)
+            G[i] = _bip(ag, dxg, dyg, Lg)
+        info = _TuneInfo()
+        self._check(self.lib.bs_autotune_batch(self.h, n, F, G, int(var), C.byref(info)))
+        out = {name: getattr(info, name) for name, _ in _TuneInfo._fields_}
+        out["uni_threads"] = list(info.uni_threads)
+        return out
+
+    def set_tune(self, eval_warps=8, eval_blocks_per_sm=8, uni_threads=(128,) * 6, crt_tile=8,
+                 crt_blocks_per_sm=4):
+        t = _TuneInfo()
+        t.eval_warps, t.eval_blocks_per_sm = eval_warps, eval_blocks_per_sm
+        for c in range(6):
+            t.uni_threads[c] = uni_threads[c]
+        t.crt_tile, t.crt_blocks_per_sm = crt_tile, crt_blocks_per_sm
+        self._check(self.lib.bs_set_tune(self.h, C.byref(t)))
 
     def squarefree_part(self, r):
         arr, L = ints_to_limbs(r)

@@ -106,7 +106,8 @@ extern "C" int bs_init(int device, size_t mem_budget, bs_ctx** out) {
     return BS_ERR_CUDA;
   }
   cudaMemset(ctx->d_status, 0, sizeof(int32_t) * 4);
-  for (int c = 0; c < kNumUniClasses; ++c) ctx->occ[c] = uni_occupancy(c);
+  for (int c = 0; c < kNumUniClasses; ++c)
+    for (int t = 0; t < 3; ++t) ctx->occ[c][t] = uni_occupancy(c, kUniThreadChoices[t]);
   if (set_stage_smem_limits(ctx->smem_optin) != 0) {
     cudaGetLastError();
     bs_free(ctx);
@@ -406,6 +407,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   }
   eoff[0] = ioff[0] = iwoff[0] = coff[0] = 0;
   size_t in_pos = 0, ps_pos = 0;
+  const int crt_tile = crt_warp_kernel(ctx, B.kmax, B.lmax) ? ctx->tune.crt_tile : kCrtTile;
   B.instances = B.mulmods = B.k_need_sum = B.k_total_sum = 0;
   B.maxpts = B.maxprimes = 0;
   for (int i = 0; i < n; ++i) {
@@ -435,7 +437,8 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
       if (P.logN <= kWarpLogNMax) {
         const int ec = eval_class_of(P.logN);
         eids[ec][efill[ec]] = i;
-        eoffs[ec][efill[ec] + 1] = eoffs[ec][efill[ec]] + (int64_t)P.k_total * ((J.rows + 7) / 8);
+        const int ew = ctx->tune.eval_warps;
+        eoffs[ec][efill[ec] + 1] = eoffs[ec][efill[ec]] + (int64_t)P.k_total * ((J.rows + ew - 1) / ew);
         ++efill[ec];
       } else {
         ne = (int64_t)P.k_total * J.rows;
@@ -445,7 +448,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
         niw = P.k_total;
       else
         ni = P.k_total;
-      nu = (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile;
+      nu = (int64_t)P.k_total << P.logN;  // instances
       const int c = uni_class_of(std::max(P.me, P.ne) + 1);
       cids[c][cfill[c]] = i;
       coffs[c][cfill[c] + 1] = coffs[c][cfill[c]] + nu;
@@ -461,7 +464,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
     eoff[i + 1] = eoff[i] + ne;
     ioff[i + 1] = ioff[i] + ni;
     iwoff[i + 1] = iwoff[i] + niw;
-    coff[i + 1] = coff[i] + (J.cap_deg + kCrtTile) / kCrtTile;
+    coff[i + 1] = coff[i] + (J.cap_deg + crt_tile) / crt_tile;
   }
   cudaStream_t s = ctx->stream;
   int rc = ctx_cuda(ctx, cudaMemcpyAsync(base, hu, B.up_bytes, cudaMemcpyHostToDevice, s), "upload");
@@ -494,6 +497,11 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   L.lmax = B.lmax;
   L.kt_max = B.needT;
   L.logN_max = B.needLog;
+  L.eval_warps = ctx->tune.eval_warps;
+  L.eval_blocks_per_sm = ctx->tune.eval_blocks_per_sm;
+  L.crt_tile = crt_tile;
+  L.crt_blocks_per_sm = ctx->tune.crt_blocks_per_sm;
+  for (int c = 0; c < kNumUniClasses; ++c) L.uni_threads[c] = ctx->tune.uni_threads[c];
   rc = launch_stages(ctx, L, Tv, use_graph);
   if (rc) return rc;
   rc = ctx_cuda(ctx, cudaMemcpyAsync(base + B.o_status_dn, base + B.o_status, sizeof(int32_t) * 4,
@@ -585,6 +593,160 @@ int run_host_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, i
   rc = ctx_cuda(ctx, cudaStreamSynchronize(ctx->stream), "stream");
   if (rc) return rc;
   return batch_finish(ctx, B, (const char*)ctx->h_down, out);
+}
+
+// ------------------------------------------------------------------------------------
+// autotuning of the batched launch shapes
+// ------------------------------------------------------------------------------------
+extern "C" int bs_autotune_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g,
+                                 int var, bs_tune_info* info) {
+  if (!ctx || n < 1 || !f || !g || (var != 0 && var != 1)) return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
+  if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
+  cudaSetDevice(ctx->device);
+  HostBatch B;
+  int rc = batch_plan(ctx, n, f, g, var, &B);
+  if (rc) return rc;
+  rc = ctx->tabs->ensure(B.needT, B.needLog, ctx->stream);
+  if (rc) return ctx_fail(ctx, rc, "table setup failed");
+  rc = ensure_workspace(ctx, B.total);
+  if (rc) return rc;
+  rc = ensure_pinned(ctx, B.up_bytes, B.dn_bytes);
+  if (rc) return rc;
+  const bool was_profiling = ctx->profile;
+  if (!ctx->prof_ev[0])
+    for (int i = 0; i < kProfEvents; ++i) cudaEventCreate(&ctx->prof_ev[i]);
+  ctx->profile = true;
+  int trials = 0;
+  // stage times (ms) of one run with the context's current shapes: [eval, unires, intt, crt]
+  auto run = [&](float* st) -> int {
+    float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+    for (int rep = 0; rep < 2; ++rep) {
+      int r = batch_launch(ctx, B, f, g, (char*)ctx->ws, (char*)ctx->h_up, (char*)ctx->h_down, false);
+      if (r) return r;
+      r = ctx_cuda(ctx, cudaStreamSynchronize(ctx->stream), "stream");
+      if (r) return r;
+      for (int k = 0; k < 4; ++k) {
+        float ms = 0.f;
+        if (ctx->prof_rec[k + 1] && ctx->prof_rec[k + 2])
+          cudaEventElapsedTime(&ms, ctx->prof_ev[k + 1], ctx->prof_ev[k + 2]);
+        best[k] = std::min(best[k], ms);
+      }
+    }
+    ++trials;
+    for (int k = 0; k < 4; ++k) st[k] = best[k];
+    return 0;
+  };
+  const Tune dflt;
+  ctx->tune = dflt;
+  float st[4];
+  rc = run(st);
+  if (rc) {
+    ctx->profile = was_profiling;
+    return rc;
+  }
+  const float ms_default = st[0] + st[1] + st[2] + st[3];
+  Tune best = dflt;
+  // evaluation: rows per block and grid cap
+  {
+    float bt = st[0];
+    for (int w : {2, 4, 8})
+      for (int b : {4, 8, 16}) {
+        if (w == dflt.eval_warps && b == dflt.eval_blocks_per_sm) continue;
+        ctx->tune = best;
+        ctx->tune.eval_warps = w;
+        ctx->tune.eval_blocks_per_sm = b;
+        if ((rc = run(st))) break;
+        if (st[0] < bt) {
+          bt = st[0];
+          best.eval_warps = w;
+          best.eval_blocks_per_sm = b;
+        }
+      }
+  }
+  // univariate resultants: threads per block, one degree class at a time
+  for (int c = 0; c < kNumUniClasses && !rc; ++c) {
+    if (!B.cls_count[c]) continue;
+    ctx->tune = best;
+    if ((rc = run(st))) break;
+    float bt = st[1];
+    const int cur = best.uni_threads[c];
+    for (int th : kUniThreadChoices) {
+      if (th == cur) continue;
+      ctx->tune = best;
+      ctx->tune.uni_threads[c] = th;
+      if ((rc = run(st))) break;
+      if (st[1] < bt) {
+        bt = st[1];
+        best.uni_threads[c] = th;
+      }
+    }
+  }
+  // reconstruction: coefficients per block and grid cap (warp kernel only)
+  if (!rc && crt_warp_kernel(ctx, B.kmax, B.lmax)) {
+    ctx->tune = best;
+    rc = run(st);
+    float bt = st[3];
+    for (int t : {2, 4, 8})
+      for (int b : {2, 4, 8}) {
+        if (rc || (t == best.crt_tile && b == best.crt_blocks_per_sm)) continue;
+        ctx->tune = best;
+        ctx->tune.crt_tile = t;
+        ctx->tune.crt_blocks_per_sm = b;
+        if ((rc = run(st))) break;
+        if (st[3] < bt) {
+          bt = st[3];
+          best.crt_tile = t;
+          best.crt_blocks_per_sm = b;
+        }
+      }
+  }
+  ctx->tune = best;
+  float ms_tuned = 0.f;
+  if (!rc) {
+    rc = run(st);
+    ms_tuned = st[0] + st[1] + st[2] + st[3];
+  }
+  ctx->profile = was_profiling;
+  if (rc) {
+    ctx->tune = dflt;
+    return rc;
+  }
+  if (info) {
+    info->eval_warps = best.eval_warps;
+    info->eval_blocks_per_sm = best.eval_blocks_per_sm;
+    for (int c = 0; c < kNumUniClasses; ++c) info->uni_threads[c] = best.uni_threads[c];
+    info->crt_tile = best.crt_tile;
+    info->crt_blocks_per_sm = best.crt_blocks_per_sm;
+    info->ms_default = ms_default;
+    info->ms_tuned = ms_tuned;
+    info->trials = trials;
+  }
+  return BS_OK;
+}
+
+extern "C" int bs_set_tune(bs_ctx* ctx, const bs_tune_info* t) {
+  if (!ctx) return BS_ERR_ARG;
+  if (!t) {
+    ctx->tune = Tune{};
+    return BS_OK;
+  }
+  Tune u;
+  if (t->eval_warps < 1 || t->eval_warps > kEvalThreads / 32 || t->eval_blocks_per_sm < 1 ||
+      t->eval_blocks_per_sm > 64 || (t->crt_tile != 1 && t->crt_tile != 2 && t->crt_tile != 4 &&
+                                     t->crt_tile != 8) ||
+      t->crt_blocks_per_sm < 1 || t->crt_blocks_per_sm > 64)
+    return ctx_fail(ctx, BS_ERR_ARG, "launch shape out of range");
+  for (int c = 0; c < kNumUniClasses; ++c) {
+    if (t->uni_threads[c] != 64 && t->uni_threads[c] != 128 && t->uni_threads[c] != 256)
+      return ctx_fail(ctx, BS_ERR_ARG, "univariate block size must be 64, 128 or 256");
+    u.uni_threads[c] = t->uni_threads[c];
+  }
+  u.eval_warps = t->eval_warps;
+  u.eval_blocks_per_sm = t->eval_blocks_per_sm;
+  u.crt_tile = t->crt_tile;
+  u.crt_blocks_per_sm = t->crt_blocks_per_sm;
+  ctx->tune = u;
+  return BS_OK;
 }
 
 extern "C" int bs_resultant(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var,

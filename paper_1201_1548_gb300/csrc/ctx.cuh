@@ -9,6 +9,19 @@
 #include "resultant_kernels.cuh"
 #include "tables.cuh"
 
+namespace bs {
+// launch shapes of the batched stages: defaults, or what bs_autotune_batch measured best
+// for a batch (the device-planned single job always uses the defaults)
+struct Tune {
+  int eval_warps = 8;           // rows (one warp each) per evaluation block, 1..8
+  int eval_blocks_per_sm = 8;   // cap of the persistent evaluation grid
+  int uni_threads[kNumUniClasses] = {128, 128, 128, 128, 128, 128};  // 64, 128 or 256
+  int crt_tile = 8;             // coefficients (one warp each) per reconstruction block, 1..8
+  int crt_blocks_per_sm = 4;    // cap of the persistent reconstruction grid
+};
+constexpr int kUniThreadChoices[3] = {64, 128, 256};
+}  // namespace bs
+
 struct bs_ctx {
   int device = 0;
   int sms = 0;
@@ -33,7 +46,8 @@ struct bs_ctx {
   void* h_down = nullptr;
   size_t h_down_cap = 0;
   int32_t* d_status = nullptr;  // [status, rejected, -, -] of device-planned calls
-  int occ[bs::kNumUniClasses] = {1, 1, 1, 1, 1, 1};
+  int occ[bs::kNumUniClasses][3] = {};  // resident univariate blocks per SM (64/128/256 threads)
+  bs::Tune tune;
   // cached executable graph of the batched stages
   cudaGraphExec_t graph_exec = nullptr;
   // square-free / gcd scratch
@@ -73,12 +87,17 @@ struct StageLaunch {
   WorkList uni[kNumUniClasses];
   int64_t eval_items, intt_items, intt_w_items, crt_items;
   int64_t evw_items[kNumEvalClasses], evw_any_items;
+  int eval_warps = 8, eval_blocks_per_sm = 8, crt_tile = kCrtTile, crt_blocks_per_sm = 4;
+  int uni_threads[kNumUniClasses] = {kUniTile, kUniTile, kUniTile, kUniTile, kUniTile, kUniTile};
   int64_t uni_items[kNumUniClasses];
   int maxN, kmax, lmax;
   int kt_max, logN_max;  // largest prime count and transform size (L2 prefetch)
 };
 
 int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_graph);
+// whether the reconstruction of a batch runs in the warp-per-coefficient kernel (whose
+// block size is tunable) or in the block Garner kernel (tiles of kCrtTile coefficients)
+bool crt_warp_kernel(const bs_ctx* ctx, int kmax, int lmax);
 int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const MetaBounds& mb,
                       int cls);
 

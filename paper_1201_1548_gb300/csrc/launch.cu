@@ -35,7 +35,7 @@ static int crt_warps(const bs_ctx* ctx, int kmax, int lmax, size_t* smem, int* s
 }
 
 // shared memory of the warp-per-coefficient reconstruction block
-static size_t crt_warp_smem(int kmax, int lmax) {
+size_t crt_warp_smem(int kmax, int lmax) {
   return ((size_t)kmax * kmax + (size_t)kmax * lmax + (size_t)kmax * kCrtTile + 3 * (size_t)kmax +
           (size_t)kCrtTile * kmax + (size_t)kCrtTile * lmax) * sizeof(uint32_t);
 }
@@ -52,18 +52,21 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   const size_t tsmem = sizeof(uint32_t) * (size_t)L.maxN;
   mark(ctx, 1, s);
   int g;
+  const PfHint pf{L.kt_max, 1 << L.logN_max, L.kmax};
   for (int c = 0; c < kNumEvalClasses; ++c) {
-    g = grid_for(L.evw_items[c], (int64_t)sms * 8);
-    if (g) launch_eval_w(c, g, s, L.jobs, L.evw[c], Tv, PfHint{L.kt_max, 1 << L.logN_max, L.kmax});
+    g = grid_for(L.evw_items[c], (int64_t)sms * L.eval_blocks_per_sm);
+    if (g) launch_eval_w(c, g, L.eval_warps, s, L.jobs, L.evw[c], Tv, pf);
   }
   g = grid_for(L.evw_any_items, (int64_t)sms * 8);
-  if (g) launch_eval_w(-1, g, s, L.jobs, L.evw_any, Tv, PfHint{L.kt_max, 1 << L.logN_max, L.kmax});
+  if (g) launch_eval_w(-1, g, kEvalThreads / 32, s, L.jobs, L.evw_any, Tv, pf);
   g = grid_for(L.eval_items, (int64_t)sms * 8);
   if (g) launch_eval(g, tsmem, s, L.jobs, L.eval, Tv);
   mark(ctx, 2, s);
   for (int c = 0; c < kNumUniClasses; ++c) {
-    g = grid_for(L.uni_items[c], (int64_t)sms * ctx->occ[c]);
-    if (g) launch_uni(c, g, s, L.jobs, L.uni[c], Tv);
+    const int th = L.uni_threads[c];
+    const int ti = th == 64 ? 0 : th == 128 ? 1 : 2;
+    g = grid_for((L.uni_items[c] + th - 1) / th, (int64_t)sms * ctx->occ[c][ti]);
+    if (g) launch_uni(c, g, th, s, L.jobs, L.uni[c], Tv);
   }
   mark(ctx, 3, s);
   g = grid_for((L.intt_w_items + kInttWarps - 1) / kInttWarps, (int64_t)sms * 8);
@@ -71,13 +74,17 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   g = grid_for(L.intt_items, (int64_t)sms * 8);
   if (g) launch_intt(g, 2 * tsmem, s, L.jobs, L.intt, Tv);  // values + packed twiddles
   mark(ctx, 4, s);
-  g = grid_for(L.crt_items, (int64_t)sms * 4);
+  g = grid_for(L.crt_items, (int64_t)sms * L.crt_blocks_per_sm);
   const size_t wsm = crt_warp_smem(L.kmax, L.lmax);
   if (g && L.kmax <= kCrtWarpMaxK && wsm <= (size_t)ctx->smem_optin - 64)
-    launch_crt_w(g, wsm, s, L.jobs, L.crt, Tv, L.kmax, L.lmax);
+    launch_crt_w(g, L.crt_tile, wsm, s, L.jobs, L.crt, Tv, L.kmax, L.lmax);
   else if (g)
     launch_crt(g, crt_w * 32, crt_smem, s, L.jobs, L.crt, Tv, L.kmax, L.lmax, crt_staged);
   mark(ctx, 5, s);
+}
+
+bool crt_warp_kernel(const bs_ctx* ctx, int kmax, int lmax) {
+  return kmax <= kCrtWarpMaxK && crt_warp_smem(kmax, lmax) <= (size_t)ctx->smem_optin - 64;
 }
 
 int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_graph) {
@@ -154,7 +161,7 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
     L.uni[c] = WorkList{nullptr, offs + kOffUni, 1};
     L.uni_items[c] = 0;
   }
-  L.uni_items[cls] = (((int64_t)mb.k_total << mb.logN) + kUniTile - 1) / kUniTile;
+  L.uni_items[cls] = (int64_t)mb.k_total << mb.logN;  // instances
   L.intt = WorkList{nullptr, offs + kOffInttS, 1};
   L.intt_w = WorkList{nullptr, offs + kOffInttW, 1};
   L.crt = WorkList{nullptr, offs + kOffCrt, 1};

@@ -569,7 +569,7 @@ int mg_launch(bs_ctx* ctx, MgBatch& B, const bs_upoly* a, const bs_upoly* b, cha
                      sizeof(uint32_t);
   auto crt = [&](const WorkList& wl) -> int {
     if (B.kmax <= kCrtWarpMaxK && wsm <= (size_t)ctx->smem_optin - 64) {
-      launch_crt_w(crt_grid, wsm, s, dc, wl, Tv, B.kmax, B.lmax);
+      launch_crt_w(crt_grid, kCrtTile, wsm, s, dc, wl, Tv, B.kmax, B.lmax);
       return 0;
     }
     const size_t per = (size_t)3 * B.lmax * sizeof(uint32_t);

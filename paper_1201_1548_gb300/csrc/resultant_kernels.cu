@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
     for (int s = 0; s < kNumOffs; s += 2) offs[s] = 0;
     offs[kOffEvalW + 1] = (run && wsize) ? (int64_t)P.k_total * ((J.rows + 7) / 8) : 0;
     offs[kOffEvalS + 1] = (run && !wsize) ? (int64_t)P.k_total * J.rows : 0;
-    offs[kOffUni + 1] = run ? (((int64_t)P.k_total << P.logN) + kUniTile - 1) / kUniTile : 0;
+    offs[kOffUni + 1] = run ? ((int64_t)P.k_total << P.logN) : 0;  // instances
     offs[kOffInttW + 1] = 0;  // a single job interpolates one block per prime
     offs[kOffInttS + 1] = run ? P.k_total : 0;
     offs[kOffCrt + 1] = ((int64_t)J.cap_deg + kCrtTile) / kCrtTile;
@@ -520,16 +520,18 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_w(const Job* jobs, Wor
 // ------------------------------------------------------------------------------------
 // (c): univariate resultants, one per thread
 // ------------------------------------------------------------------------------------
+// Work list offsets count (prime, point) instances; thread i of the grid-stride sweep
+// takes instance i of the flat index space and finds its job by binary search, so any
+// block size works and no thread idles at the end of a job.
 template <int L>
-__global__ void __launch_bounds__(kUniTile) k_unires(const Job* jobs, WorkList wl, Tables T) {
+__global__ void __launch_bounds__(kUniMaxThreads) k_unires(const Job* jobs, WorkList wl, Tables T) {
   const int64_t total = wl.off[wl.n];
-  for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    const int ji = find_item(wl.off, wl.n, tile);
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int ji = find_item(wl.off, wl.n, g);
     const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
     const int logN = J->plan.logN;
-    const int64_t ninst = (int64_t)J->plan.k_total << logN;
-    const int64_t inst = (tile - wl.off[ji]) * kUniTile + threadIdx.x;
-    if (inst >= ninst) continue;
+    const int64_t inst = g - wl.off[ji];
     const int N = 1 << logN;
     const int q = (int)(inst >> logN);
     const int t = (int)(inst & (N - 1));
@@ -1168,11 +1170,13 @@ __device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, 
 
 // Block: kCrtTile coefficients of one job, one warp each.  Shared memory (words):
 // [inv k*k][pp k*nlmax][X k*kCrtTile][p k][pinv k][sel k][digits kCrtTile*k][limbs kCrtTile*lmax]
-__global__ void __launch_bounds__(kCrtTile * 32) k_crt_w(const Job* jobs, WorkList wl, Tables T,
+template <int TILE>
+__global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList wl, Tables T,
                                                          int kmax, int lmax) {
   extern __shared__ uint32_t smc[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nthr = blockDim.x;
+  constexpr int tile = TILE;  // coefficients per block, one warp each (<= kCrtTile)
   uint32_t* sinv = smc;
   uint32_t* spp = sinv + (size_t)kmax * kmax;
   uint32_t* X = spp + (size_t)kmax * lmax;
@@ -1185,10 +1189,10 @@ __global__ void __launch_bounds__(kCrtTile * 32) k_crt_w(const Job* jobs, WorkLi
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
     const int ji = find_item(wl.off, wl.n, item);
     const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
-    const int i0 = (int)(item - wl.off[ji]) * kCrtTile;
+    const int i0 = (int)(item - wl.off[ji]) * tile;
     const int cap = J->cap_limbs;
     const Plan P = J->plan;
-    const int ncoef = min(kCrtTile, J->cap_deg + 1 - i0);
+    const int ncoef = min(tile, J->cap_deg + 1 - i0);
     if (P.status != 0 || P.trivial != 0 || i0 > P.D) {
       for (int t = threadIdx.x; t < ncoef * cap; t += nthr) {
         const int c = t / cap, l = t - c * cap;
@@ -1208,7 +1212,7 @@ __global__ void __launch_bounds__(kCrtTile * 32) k_crt_w(const Job* jobs, WorkLi
       selq[j] = (uint32_t)s;
     }
 #pragma unroll 4
-    for (int t = threadIdx.x; t < k * kCrtTile; t += nthr) {
+    for (int t = threadIdx.x; t < k * kCrtTile; t += nthr) {  // columns >= tile stay unused
       const int j = t / kCrtTile, c = t - j * kCrtTile;
       X[t] = (c < nvalid) ? J->rmod[(int64_t)j * (D + 1) + i0 + c] : 0u;
     }
@@ -1262,9 +1266,14 @@ __global__ void __launch_bounds__(kCrtTile * 32) k_crt_w(const Job* jobs, WorkLi
   }
 }
 
-void launch_crt_w(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
-                  int kmax, int lmax) {
-  k_crt_w<<<grid, kCrtTile * 32, smem, s>>>(jobs, wl, T, kmax, lmax);
+void launch_crt_w(int grid, int tile, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
+                  Tables T, int kmax, int lmax) {
+  switch (tile) {
+    case 1: k_crt_w<1><<<grid, 32, smem, s>>>(jobs, wl, T, kmax, lmax); break;
+    case 2: k_crt_w<2><<<grid, 64, smem, s>>>(jobs, wl, T, kmax, lmax); break;
+    case 4: k_crt_w<4><<<grid, 128, smem, s>>>(jobs, wl, T, kmax, lmax); break;
+    default: k_crt_w<8><<<grid, 256, smem, s>>>(jobs, wl, T, kmax, lmax); break;
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -1314,31 +1323,31 @@ template __global__ void k_unires<65>(const Job*, WorkList, Tables);
 // launchers (kernels are launched from the translation unit that defines them)
 // ------------------------------------------------------------------------------------
 template <int L>
-static int occ1() {
+static int occ1(int threads) {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_unires<L>, kUniTile, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_unires<L>, threads, 0);
   return b > 0 ? b : 1;
 }
 
-int uni_occupancy(int cls) {
+int uni_occupancy(int cls, int threads) {
   switch (cls) {
-    case 0: return occ1<8>();
-    case 1: return occ1<16>();
-    case 2: return occ1<24>();
-    case 3: return occ1<33>();
-    case 4: return occ1<48>();
-    default: return occ1<65>();
+    case 0: return occ1<8>(threads);
+    case 1: return occ1<16>(threads);
+    case 2: return occ1<24>(threads);
+    case 3: return occ1<33>(threads);
+    case 4: return occ1<48>(threads);
+    default: return occ1<65>(threads);
   }
 }
 
-void launch_uni(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
+void launch_uni(int cls, int grid, int threads, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   switch (cls) {
-    case 0: k_unires<8><<<grid, kUniTile, 0, s>>>(jobs, wl, T); break;
-    case 1: k_unires<16><<<grid, kUniTile, 0, s>>>(jobs, wl, T); break;
-    case 2: k_unires<24><<<grid, kUniTile, 0, s>>>(jobs, wl, T); break;
-    case 3: k_unires<33><<<grid, kUniTile, 0, s>>>(jobs, wl, T); break;
-    case 4: k_unires<48><<<grid, kUniTile, 0, s>>>(jobs, wl, T); break;
-    default: k_unires<65><<<grid, kUniTile, 0, s>>>(jobs, wl, T); break;
+    case 0: k_unires<8><<<grid, threads, 0, s>>>(jobs, wl, T); break;
+    case 1: k_unires<16><<<grid, threads, 0, s>>>(jobs, wl, T); break;
+    case 2: k_unires<24><<<grid, threads, 0, s>>>(jobs, wl, T); break;
+    case 3: k_unires<33><<<grid, threads, 0, s>>>(jobs, wl, T); break;
+    case 4: k_unires<48><<<grid, threads, 0, s>>>(jobs, wl, T); break;
+    default: k_unires<65><<<grid, threads, 0, s>>>(jobs, wl, T); break;
   }
 }
 
@@ -1358,16 +1367,17 @@ void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const
 void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   k_eval<<<grid, kEvalThreads, smem, s>>>(jobs, wl, T);
 }
-void launch_eval_w(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
-                   PfHint pf) {
+void launch_eval_w(int cls, int grid, int warps, cudaStream_t s, const Job* jobs, WorkList wl,
+                   Tables T, PfHint pf) {
+  const int th = warps * 32;
   switch (cls) {
-    case -1: k_eval_w<0><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
-    case 0: k_eval_w<1><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
-    case 1: k_eval_w<2><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
-    case 2: k_eval_w<4><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
-    case 3: k_eval_w<8><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
-    case 4: k_eval_w<16><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
-    default: k_eval_w<32><<<grid, kEvalThreads, 0, s>>>(jobs, wl, T, pf); break;
+    case -1: k_eval_w<0><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
+    case 0: k_eval_w<1><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
+    case 1: k_eval_w<2><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
+    case 2: k_eval_w<4><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
+    case 3: k_eval_w<8><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
+    case 4: k_eval_w<16><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
+    default: k_eval_w<32><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
   }
 }
 void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
@@ -1397,7 +1407,10 @@ int set_stage_smem_limits(int optin) {
   rc |= set_dyn_smem_limit((const void*)k_eval, optin);
   rc |= set_dyn_smem_limit((const void*)k_intt, optin);
   rc |= set_dyn_smem_limit((const void*)k_crt, optin);
-  rc |= set_dyn_smem_limit((const void*)k_crt_w, optin);
+  rc |= set_dyn_smem_limit((const void*)k_crt_w<1>, optin);
+  rc |= set_dyn_smem_limit((const void*)k_crt_w<2>, optin);
+  rc |= set_dyn_smem_limit((const void*)k_crt_w<4>, optin);
+  rc |= set_dyn_smem_limit((const void*)k_crt_w<8>, optin);
   return rc;
 }
 

@@ -4,7 +4,8 @@
 
 namespace bs {
 
-constexpr int kUniTile = 128;     // instances per univariate-resultant tile (one block)
+constexpr int kUniTile = 128;     // default threads of a univariate-resultant block
+constexpr int kUniMaxThreads = 256;  // largest univariate-resultant block
 constexpr int kEvalThreads = 256; // threads of a transform block
 constexpr int kCrtWarps = 8;      // warps of a reconstruction block
 constexpr int kCrtTile = 8;       // coefficients per reconstruction block
@@ -22,24 +23,26 @@ constexpr int kNumEvalClasses = 6;
 inline int eval_class_of(int logN) { return logN <= 5 ? 0 : logN - 5; }
 
 // launchers (defined next to the kernels)
-int uni_occupancy(int cls);
-void launch_uni(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+int uni_occupancy(int cls, int threads);
+void launch_uni(int cls, int grid, int threads, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const uint32_t* a, int da,
                        int lda, const uint32_t* b, int db, int ldb, uint32_t* res, Tables T);
 void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 // one warp per (job, prime) for N <= 2^kWarpInttLogNMax
 void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
-void launch_crt_w(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
-                  int kmax, int lmax);
+// tile: coefficients per block (one warp each), 1 <= tile <= kCrtTile
+void launch_crt_w(int grid, int tile, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
+                  Tables T, int kmax, int lmax);
 // sizes for the L2 prefetch the evaluation kernel issues (kt < 0: read the first job's plan)
 struct PfHint {
   int kt, N, kn;
 };
 constexpr int kPfIssuers = 128;   // blocks that issue one prefetch chunk each
 // cls = eval_class_of(logN) for lists of one size class, -1 for any size (device plans)
-void launch_eval_w(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T,
-                   PfHint pf);
+// warps: rows per block (1 .. kEvalThreads / 32); the work list counts groups of that many rows
+void launch_eval_w(int cls, int grid, int warps, cudaStream_t s, const Job* jobs, WorkList wl,
+                   Tables T, PfHint pf);
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
                 Tables T, int kmax, int lmax, int staged);
 void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T);

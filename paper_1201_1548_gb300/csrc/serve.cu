@@ -147,7 +147,9 @@ static int make_slot(bs_ctx* parent, bs_ctx** out) {
   c->budget = parent->budget;
   c->tabs = parent->tabs;
   c->parent = parent;
-  for (int i = 0; i < kNumUniClasses; ++i) c->occ[i] = parent->occ[i];
+  for (int i = 0; i < kNumUniClasses; ++i)
+    for (int t = 0; t < 3; ++t) c->occ[i][t] = parent->occ[i][t];
+  c->tune = parent->tune;
   if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete c;
     return BS_ERR_CUDA;

@@ -224,3 +224,37 @@ def test_largest_served_size(ctx):
     p = 2147483647
     for a in (3, 1234567):
         assert P.evaluate(r, a) % p == R.res_at_point_modp(f, g, a, p)
+
+
+@pytest.mark.parametrize("shape", [
+    dict(eval_warps=2, eval_blocks_per_sm=4, uni_threads=(64,) * 6, crt_tile=2, crt_blocks_per_sm=2),
+    dict(eval_warps=4, eval_blocks_per_sm=16, uni_threads=(256,) * 6, crt_tile=4, crt_blocks_per_sm=8),
+    dict(eval_warps=1, eval_blocks_per_sm=1, uni_threads=(64, 128, 256, 64, 128, 256), crt_tile=1,
+         crt_blocks_per_sm=1),
+])
+def test_batch_results_do_not_depend_on_launch_shape(ctx, shape):
+    pairs = cfg3_batch(seed=23, count=64, deg_lo=2, deg_hi=12, bits_lo=8, bits_hi=96)
+    ctx.set_tune()
+    ref = ctx.resultant_batch(pairs)
+    ctx.set_tune(**shape)
+    try:
+        assert ctx.resultant_batch(pairs) == ref
+        assert ctx.resultant(*pairs[5]) == ref[5]
+    finally:
+        ctx.set_tune()
+    for i in range(0, 64, 16):
+        assert ref[i] == R.res_y(*pairs[i])
+
+
+def test_autotune_batch(ctx):
+    pairs = cfg3_batch(seed=24, count=256)
+    ref = ctx.resultant_batch(pairs)
+    info = ctx.autotune_batch(pairs)
+    try:
+        assert info["trials"] >= 3
+        assert info["eval_warps"] in (2, 4, 8) and info["crt_tile"] in (2, 4, 8)
+        assert all(t in (64, 128, 256) for t in info["uni_threads"])
+        assert 0 < info["ms_tuned"] <= 1.1 * info["ms_default"]
+        assert ctx.resultant_batch(pairs) == ref
+    finally:
+        ctx.set_tune()
