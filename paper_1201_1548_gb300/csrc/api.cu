@@ -502,6 +502,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   L.crt_tile = crt_tile;
   L.crt_blocks_per_sm = ctx->tune.crt_blocks_per_sm;
   for (int c = 0; c < kNumUniClasses; ++c) L.uni_threads[c] = ctx->tune.uni_threads[c];
+  L.pdl = true;
   rc = launch_stages(ctx, L, Tv, use_graph);
   if (rc) return rc;
   rc = ctx_cuda(ctx, cudaMemcpyAsync(base + B.o_status_dn, base + B.o_status, sizeof(int32_t) * 4,

@@ -88,6 +88,7 @@ struct StageLaunch {
   int64_t eval_items, intt_items, intt_w_items, crt_items;
   int64_t evw_items[kNumEvalClasses], evw_any_items;
   int eval_warps = 8, eval_blocks_per_sm = 8, crt_tile = kCrtTile, crt_blocks_per_sm = 4;
+  bool pdl = false;  // programmatic dependent launch between the stage kernels
   int uni_threads[kNumUniClasses] = {kUniTile, kUniTile, kUniTile, kUniTile, kUniTile, kUniTile};
   int64_t uni_items[kNumUniClasses];
   int maxN, kmax, lmax;

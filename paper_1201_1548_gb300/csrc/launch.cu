@@ -50,6 +50,8 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
                     size_t crt_smem, int crt_staged) {
   const int sms = ctx->sms;
   const size_t tsmem = sizeof(uint32_t) * (size_t)L.maxN;
+  // the profiling events between the stages would separate them: no overlap then
+  set_launch_pdl(L.pdl && !ctx->profile);
   mark(ctx, 1, s);
   int g;
   const PfHint pf{L.kt_max, 1 << L.logN_max, L.kmax};
@@ -80,6 +82,7 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
     launch_crt_w(g, L.crt_tile, wsm, s, L.jobs, L.crt, Tv, L.kmax, L.lmax);
   else if (g)
     launch_crt(g, crt_w * 32, crt_smem, s, L.jobs, L.crt, Tv, L.kmax, L.lmax, crt_staged);
+  set_launch_pdl(false);
   mark(ctx, 5, s);
 }
 
@@ -178,6 +181,7 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   L.logN_max = 0;
   L.kmax = mb.k_need;
   L.lmax = J.cap_limbs;
+  L.pdl = true;
   size_t crt_smem = 0;
   int crt_staged = 0;
   const int crt_w = crt_warps(ctx, L.kmax, L.lmax, &crt_smem, &crt_staged);

@@ -23,6 +23,15 @@
 namespace bs {
 
 // ------------------------------------------------------------------------------------
+// programmatic dependent launch: a stage kernel launched with programmatic stream
+// serialisation may start while its predecessor finishes; it waits for the predecessor's
+// results before touching them, and lets its own successor launch once its blocks are
+// done.  Both instructions are no-ops for an ordinary launch.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ------------------------------------------------------------------------------------
 // L2 prefetch of the table ranges a job will read (the step may start with a cold L2):
 // one bulk prefetch per contiguous range, trimmed inward to 16-byte boundaries so that
 // every prefetched byte lies inside its allocation
@@ -262,6 +271,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
     offs[kOffInttS + 1] = run ? P.k_total : 0;
     offs[kOffCrt + 1] = ((int64_t)J.cap_deg + kCrtTile) / kCrtTile;
   }
+  pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------
@@ -317,6 +327,7 @@ __device__ __forceinline__ void dit_intt(uint32_t* sm, int logN, const uint32_t*
 }
 
 __global__ void __launch_bounds__(kEvalThreads) k_eval(const Job* jobs, WorkList wl, Tables T) {
+  pdl_wait();
   extern __shared__ uint32_t sm[];
   const int64_t total = wl.off[wl.n];
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
@@ -354,6 +365,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(const Job* jobs, WorkList
     for (int t = threadIdx.x; t < N; t += blockDim.x) dst[t] = sm[t];
     __syncthreads();
   }
+  pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------
@@ -455,6 +467,7 @@ __device__ __forceinline__ void eval_row_class(const Job* J, int q, int row, con
 template <int R>
 __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_w(const Job* jobs, WorkList wl,
                                                                           Tables T, PfHint pf) {
+  pdl_wait();
   constexpr int NS = R == 0 ? (1 << kWarpLogNMax) : 32 * R;  // largest transform size
   __shared__ uint32_t s_stage[kEvalThreads / 32][(R == 32 || R == 0) ? 33 * 32 : NS];
   __shared__ uint32_t s_tw[NS];  // packed twiddles of this block's prime
@@ -515,6 +528,7 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_w(const Job* jobs, Wor
       }
     }
   }
+  pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------
@@ -525,6 +539,7 @@ __global__ void __launch_bounds__(kEvalThreads, 3) k_eval_w(const Job* jobs, Wor
 // block size works and no thread idles at the end of a job.
 template <int L>
 __global__ void __launch_bounds__(kUniMaxThreads) k_unires(const Job* jobs, WorkList wl, Tables T) {
+  pdl_wait();
   const int64_t total = wl.off[wl.n];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -552,12 +567,14 @@ __global__ void __launch_bounds__(kUniMaxThreads) k_unires(const Job* jobs, Work
     uint32_t num = unires_numden<L>(A, me + 1, B, ne + 1, M, pc.one_m, &den);
     J->vals[inst] = mmul(num, minv(den, pc.one_m, M), M);
   }
+  pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------
 // prime selection + (d): inverse transform, unscaling, degree check
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList wl, Tables T) {
+  pdl_wait();
   extern __shared__ uint32_t sm[];
   const int64_t total = wl.off[wl.n];
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
@@ -621,6 +638,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
     if (threadIdx.x == 0) J->sel[r] = q;
     __syncthreads();
   }
+  pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------
@@ -672,6 +690,7 @@ __device__ __forceinline__ void intt_prime_warp(const Job* J, int q, int r, cons
 }
 
 __global__ void __launch_bounds__(kInttWarps * 32) k_intt_w(const Job* jobs, WorkList wl, Tables T) {
+  pdl_wait();
   __shared__ uint32_t s_stage[kInttWarps][32];
   __shared__ uint32_t s_tw[kInttWarps][1 << kWarpInttLogNMax];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -711,6 +730,7 @@ __global__ void __launch_bounds__(kInttWarps * 32) k_intt_w(const Job* jobs, Wor
       default: intt_prime_warp<16>(J, q, r, T, sw, Pi); break;
     }
   }
+  pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------
@@ -748,6 +768,7 @@ __device__ __forceinline__ void crt_carry_out(const uint32_t* V, int nlimbs, int
 
 __global__ void __launch_bounds__(kCrtWarps * 32) k_crt(const Job* jobs, WorkList wl, Tables T,
                                                         int kmax, int lmax, int staged) {
+  pdl_wait();
   extern __shared__ uint32_t smc[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nthr = blockDim.x;
@@ -913,6 +934,7 @@ __global__ void __launch_bounds__(kCrtWarps * 32) k_crt(const Job* jobs, WorkLis
     }
     __syncthreads();
   }
+  pdl_trigger();
 }
 
 // ------------------------------------------------------------------------------------
@@ -1173,6 +1195,7 @@ __device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, 
 template <int TILE>
 __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList wl, Tables T,
                                                          int kmax, int lmax) {
+  pdl_wait();
   extern __shared__ uint32_t smc[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nthr = blockDim.x;
@@ -1264,15 +1287,40 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
     }
     __syncthreads();
   }
+  pdl_trigger();
+}
+
+static thread_local bool tl_pdl = false;
+void set_launch_pdl(bool on) { tl_pdl = on; }
+
+// launch with programmatic stream serialisation when enabled for this thread's enqueue
+template <typename... KArgs, typename... Args>
+static void launch_k(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                     Args... args) {
+  if (tl_pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+  } else {
+    kern<<<grid, block, smem, s>>>(args...);
+  }
 }
 
 void launch_crt_w(int grid, int tile, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
                   Tables T, int kmax, int lmax) {
   switch (tile) {
-    case 1: k_crt_w<1><<<grid, 32, smem, s>>>(jobs, wl, T, kmax, lmax); break;
-    case 2: k_crt_w<2><<<grid, 64, smem, s>>>(jobs, wl, T, kmax, lmax); break;
-    case 4: k_crt_w<4><<<grid, 128, smem, s>>>(jobs, wl, T, kmax, lmax); break;
-    default: k_crt_w<8><<<grid, 256, smem, s>>>(jobs, wl, T, kmax, lmax); break;
+    case 1: launch_k(k_crt_w<1>, grid, 32, smem, s, jobs, wl, T, kmax, lmax); break;
+    case 2: launch_k(k_crt_w<2>, grid, 64, smem, s, jobs, wl, T, kmax, lmax); break;
+    case 4: launch_k(k_crt_w<4>, grid, 128, smem, s, jobs, wl, T, kmax, lmax); break;
+    default: launch_k(k_crt_w<8>, grid, 256, smem, s, jobs, wl, T, kmax, lmax); break;
   }
 }
 
@@ -1342,12 +1390,12 @@ int uni_occupancy(int cls, int threads) {
 
 void launch_uni(int cls, int grid, int threads, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   switch (cls) {
-    case 0: k_unires<8><<<grid, threads, 0, s>>>(jobs, wl, T); break;
-    case 1: k_unires<16><<<grid, threads, 0, s>>>(jobs, wl, T); break;
-    case 2: k_unires<24><<<grid, threads, 0, s>>>(jobs, wl, T); break;
-    case 3: k_unires<33><<<grid, threads, 0, s>>>(jobs, wl, T); break;
-    case 4: k_unires<48><<<grid, threads, 0, s>>>(jobs, wl, T); break;
-    default: k_unires<65><<<grid, threads, 0, s>>>(jobs, wl, T); break;
+    case 0: launch_k(k_unires<8>, grid, threads, 0, s, jobs, wl, T); break;
+    case 1: launch_k(k_unires<16>, grid, threads, 0, s, jobs, wl, T); break;
+    case 2: launch_k(k_unires<24>, grid, threads, 0, s, jobs, wl, T); break;
+    case 3: launch_k(k_unires<33>, grid, threads, 0, s, jobs, wl, T); break;
+    case 4: launch_k(k_unires<48>, grid, threads, 0, s, jobs, wl, T); break;
+    default: launch_k(k_unires<65>, grid, threads, 0, s, jobs, wl, T); break;
   }
 }
 
@@ -1365,30 +1413,30 @@ void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const
 }
 
 void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
-  k_eval<<<grid, kEvalThreads, smem, s>>>(jobs, wl, T);
+  launch_k(k_eval, grid, kEvalThreads, smem, s, jobs, wl, T);
 }
 void launch_eval_w(int cls, int grid, int warps, cudaStream_t s, const Job* jobs, WorkList wl,
                    Tables T, PfHint pf) {
   const int th = warps * 32;
   switch (cls) {
-    case -1: k_eval_w<0><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
-    case 0: k_eval_w<1><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
-    case 1: k_eval_w<2><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
-    case 2: k_eval_w<4><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
-    case 3: k_eval_w<8><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
-    case 4: k_eval_w<16><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
-    default: k_eval_w<32><<<grid, th, 0, s>>>(jobs, wl, T, pf); break;
+    case -1: launch_k(k_eval_w<0>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 0: launch_k(k_eval_w<1>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 1: launch_k(k_eval_w<2>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 2: launch_k(k_eval_w<4>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 3: launch_k(k_eval_w<8>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 4: launch_k(k_eval_w<16>, grid, th, 0, s, jobs, wl, T, pf); break;
+    default: launch_k(k_eval_w<32>, grid, th, 0, s, jobs, wl, T, pf); break;
   }
 }
 void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
-  k_intt_w<<<grid, kInttWarps * 32, 0, s>>>(jobs, wl, T);
+  launch_k(k_intt_w, grid, kInttWarps * 32, 0, s, jobs, wl, T);
 }
 void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
-  k_intt<<<grid, kEvalThreads, smem, s>>>(jobs, wl, T);
+  launch_k(k_intt, grid, kEvalThreads, smem, s, jobs, wl, T);
 }
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
                 Tables T, int kmax, int lmax, int staged) {
-  k_crt<<<grid, threads, smem, s>>>(jobs, wl, T, kmax, lmax, staged);
+  launch_k(k_crt, grid, threads, smem, s, jobs, wl, T, kmax, lmax, staged);
 }
 void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T) {
   k_plan_single<<<1, kPlanThreads, 0, s>>>(J, dst, offs, T);

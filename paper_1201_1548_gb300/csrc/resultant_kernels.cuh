@@ -47,6 +47,9 @@ void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* j
                 Tables T, int kmax, int lmax, int staged);
 void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T);
 int set_stage_smem_limits(int optin);
+// launches of the stage kernels from the calling thread use programmatic dependent launch
+// while on (each stage kernel waits for its predecessor before reading its results)
+void set_launch_pdl(bool on);
 // raise a kernel's dynamic shared memory limit to what the opt-in size leaves next to its
 // static shared memory
 int set_dyn_smem_limit(const void* func, int optin);
