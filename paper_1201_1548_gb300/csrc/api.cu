@@ -227,7 +227,8 @@ extern "C" int bs_plan(const bs_bipoly* f, const bs_bipoly* g, int var, bs_plan_
   if (!out || (var != 0 && var != 1)) return BS_ERR_ARG;
   if (check_bipoly(nullptr, f, "f") || check_bipoly(nullptr, g, "g")) return BS_ERR_ARG;
   const HostPrimes& H = host_primes();
-  const Plan P = plan_host(grid_of(f), grid_of(g), var, H.lg_prefix.data(), (int)H.p.size());
+  const Plan P = plan_host(grid_of(f), grid_of(g), var, H.lg_prefix.data(), (int)H.p.size(),
+                          H.p.data());
   out->trivial = P.trivial;
   out->m_e = P.me;
   out->n_e = P.ne;
@@ -297,7 +298,7 @@ int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int v
   }
   // plans are independent: large batches plan on several host threads
   parallel_for(n, 256, [&](int i) {
-    B.plans[i] = plan_host(grid_of(f + i), grid_of(g + i), var, H.lg_prefix.data(), T);
+    B.plans[i] = plan_host(grid_of(f + i), grid_of(g + i), var, H.lg_prefix.data(), T, H.p.data());
   });
   for (int i = 0; i < n; ++i)
     if (B.plans[i].status)

@@ -238,9 +238,11 @@ struct Plan {
 //   tdeg*: total degree; dego*: degree in the other variable; lcbits*: min nonzero
 //   magnitude bits of the leading row.  plan_head() fills everything but the prime
 //   count and returns the Q16 amount of log2(prod p) needed in *need (or a status);
-//   plan_tail() completes it from k_need.
-BS_HD Plan plan_head(UF Sf, int mf, int tdf, int dof, UF Sg, int mg, int tdg, int dog,
-                     int64_t* need) {
+//   plan_tail() completes it from k_need with a conservative spare count (the exact one,
+//   exact_prime_total() below, needs the coefficients).  plan_head_logs() takes the
+//   logarithms lf = log2 Sf, lg = log2 Sg (Q16, rounded up; 0 for 0) already computed.
+BS_HD Plan plan_head_logs(int64_t lf, int mf, int tdf, int dof, int64_t lg, int mg, int tdg, int dog,
+                          int64_t* need) {
   Plan P;
   P.status = 0;
   P.trivial = 0;
@@ -275,8 +277,6 @@ BS_HD Plan plan_head(UF Sf, int mf, int tdf, int dof, UF Sg, int mg, int tdg, in
   while ((1ll << logN) < D + 1) ++logN;
   P.logN = logN;
   P.N = 1 << logN;
-  int64_t lf = Sf.m ? uf_log2_q16_up(Sf) : 0;
-  int64_t lg = Sg.m ? uf_log2_q16_up(Sg) : 0;
   int64_t l2b = ((int64_t)mg * lf + (int64_t)mf * lg + 1) / 2 + 1;  // Q16, rounded up
   if (l2b < 0) l2b = 0;
   P.log2B_q16 = l2b;
@@ -284,12 +284,21 @@ BS_HD Plan plan_head(UF Sf, int mf, int tdf, int dof, UF Sg, int mg, int tdg, in
   return P;
 }
 
-BS_HD void plan_tail(Plan& P, int k_need, int lcbf, int lcbg, int table_size) {
+BS_HD Plan plan_head(UF Sf, int mf, int tdf, int dof, UF Sg, int mg, int tdg, int dog,
+                     int64_t* need) {
+  return plan_head_logs(Sf.m ? uf_log2_q16_up(Sf) : 0, mf, tdf, dof, Sg.m ? uf_log2_q16_up(Sg) : 0,
+                        mg, tdg, dog, need);
+}
+
+BS_HD void plan_tail(Plan& P, int k_need, int lcbf, int lcbg, int table_size,
+                     bool lc_monomials = false) {
   P.k_need = k_need < 1 ? 1 : k_need;
   // a prime p > 2^30 can divide every coefficient of a leading row only if it divides
   // the smallest one: at most (bits - 1) / 30 such primes; two more cover evaluation
-  // sets that happen to contain a root of a leading coefficient
-  int spare = (lcbf > 0 ? (lcbf - 1) / 30 : 0) + (lcbg > 0 ? (lcbg - 1) / 30 : 0) + 2;
+  // sets that happen to contain a root of a leading coefficient (none needed when both
+  // leading rows are monomials: c x^k never vanishes on a coset, which avoids 0)
+  int spare = (lcbf > 0 ? (lcbf - 1) / 30 : 0) + (lcbg > 0 ? (lcbg - 1) / 30 : 0) +
+              (lc_monomials ? 0 : 2);
   P.k_total = P.k_need + spare;
   if (P.k_total > table_size) {
     P.status = 7;
@@ -333,9 +342,39 @@ BS_HD Plan finish_plan(UF Sf, int mf, int tdf, int dof, int lcbf, UF Sg, int mg,
   return P;
 }
 
+// |c| mod p of a two's complement coefficient of L limbs (host)
+inline uint32_t host_residue(const uint32_t* c, int L, uint32_t p) {
+  uint64_t acc = 0;
+  for (int l = L - 1; l >= 0; --l) acc = ((acc << 32) | c[l]) % p;
+  if (c[L - 1] >> 31) {  // value = raw - 2^(32 L)
+    uint64_t t = 1;
+    for (int l = 0; l < L; ++l) t = (t << 32) % p;
+    acc = (acc + p - t) % p;
+  }
+  return (uint32_t)acc;
+}
+
+// Spare primes, exactly: a prime is rejected for a whole job when a leading row vanishes
+// identically mod p, which needs p to divide that row's smallest coefficient (cf, cg);
+// an evaluation point hits a root of a leading coefficient only when the row has more
+// than one nonzero coefficient (a monomial c x^k never vanishes on the coset, which
+// avoids 0), and then two more primes cover such hits.  The smallest K such that
+// [0, K) holds k_need + coset primes dividing neither cf nor cg is returned; is_div(q)
+// tells whether table prime q divides cf or cg.
+template <class IsDiv>
+BS_HD int exact_prime_total(int k_need, bool lc_monomials, int table_size, IsDiv is_div) {
+  const int want = k_need + (lc_monomials ? 0 : 2);
+  int K = want, d = 0, counted = 0;
+  while (true) {
+    for (; counted < K && counted < table_size; ++counted) d += is_div(counted) ? 1 : 0;
+    if (K - d >= want || K >= table_size) return K < table_size ? K : table_size;
+    K = want + d;
+  }
+}
+
 // host version: scan both grids
 inline Plan plan_host(const Grid& f, const Grid& g, int var, const int64_t* lg_prefix,
-                      int table_size) {
+                      int table_size, const uint32_t* primes = nullptr) {
   auto summarise = [&](const Grid& h, UF* S, int* m, int* td, int* dego, int* lcb) {
     *S = UF{0u, 0};
     *m = -1;
@@ -357,7 +396,34 @@ inline Plan plan_host(const Grid& f, const Grid& g, int var, const int64_t* lg_p
   int mf, tf, df, lf, mg, tg, dg, lgb;
   summarise(f, &Sf, &mf, &tf, &df, &lf);
   summarise(g, &Sg, &mg, &tg, &dg, &lgb);
-  return finish_plan(Sf, mf, tf, df, lf, Sg, mg, tg, dg, lgb, lg_prefix, table_size);
+  Plan P = finish_plan(Sf, mf, tf, df, lf, Sg, mg, tg, dg, lgb, lg_prefix, table_size);
+  if (!primes || P.status || P.trivial) return P;
+  // leading rows: smallest nonzero coefficient and number of nonzero coefficients
+  auto lead = [&](const Grid& h, int m, int* nnz) {
+    const uint32_t* best = nullptr;
+    int bb = 0;
+    *nnz = 0;
+    for (int o = 0; o <= ext_o(h, var); ++o) {
+      bool nz;
+      int bits;
+      mag_uf(coef_ptr(h, var, m, o), h.L, &nz, &bits);
+      if (!nz) continue;
+      ++*nnz;
+      if (!best || bits < bb) {
+        best = coef_ptr(h, var, m, o);
+        bb = bits;
+      }
+    }
+    return best;
+  };
+  int nf, ng;
+  const uint32_t* cf = lead(f, mf, &nf);
+  const uint32_t* cg = lead(g, mg, &ng);
+  const int K = exact_prime_total(P.k_need, nf == 1 && ng == 1, table_size, [&](int q) {
+    return host_residue(cf, f.L, primes[q]) == 0 || host_residue(cg, g.L, primes[q]) == 0;
+  });
+  if (K < P.k_total) P.k_total = K;  // never above the conservative count
+  return P;
 }
 
 }  // namespace bs

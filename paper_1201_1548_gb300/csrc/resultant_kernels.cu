@@ -90,12 +90,25 @@ __device__ void prefetch_late_tables(const Tables& T, int kt, int N, int kn, int
   }
 }
 
+// c mod p in Montgomery form for a two's complement coefficient of L limbs
+__device__ __forceinline__ uint32_t residue_m(const uint32_t* c, int L, const uint32_t* pw,
+                                              const uint32_t* mpw, uint32_t p, uint32_t pinv) {
+  uint32_t acc = 0;
+  for (int l = 0; l < L; ++l) acc = madd(acc, redc((uint64_t)c[l] * pw[l], p, pinv), p);
+  if (c[L - 1] >> 31) acc = msub(acc, mpw[L], p);
+  return acc;
+}
+
 // ------------------------------------------------------------------------------------
 // plan of a single device-resident job (one block of kPlanThreads)
 // ------------------------------------------------------------------------------------
+constexpr int kSlotInts = 6;  // per row slot: m, td, dego, lcb, lcnt, lco
+
 struct PolySummary {
   UF S;
   int m, td, dego, lcb;
+  int lcnt, lco;  // leading row: nonzero coefficients, index of the smallest one
+  int64_t l2S;    // log2 S (Q16, rounded up), 0 for S = 0
 };
 
 __device__ __forceinline__ UF shfl_uf(UF a, int src_lane_xor) {
@@ -115,12 +128,23 @@ __device__ void summarise_half(const Grid& h, int var, int tid, PolySummary* out
   constexpr int kHalf = kPlanThreads / 2;
   const int sub = tid & 7;
   const int ee = ext_e(h, var), eo = ext_o(h, var);
+  // issue every line this thread reads before the first use, so the loads of the loop
+  // below overlap instead of waiting one after another
+  for (int e0 = 0; e0 <= ee; e0 += kHalf / 8) {
+    const int e = e0 + tid / 8;
+    if (e > ee) break;
+    for (int o = sub; o <= eo; o += 8) {
+      const uint32_t* c = coef_ptr(h, var, e, o);
+      asm volatile("prefetch.L1 [%0];" ::"l"(c));
+      if (h.L > 1) asm volatile("prefetch.L1 [%0];" ::"l"(c + h.L - 1));
+    }
+  }
   UF S{0u, 0};
-  int m = -1, td = -1, dego = -1, lcb = 0;
+  int m = -1, td = -1, dego = -1, lcb = 0, lcnt = 0, lco = 0;
   for (int e0 = 0; e0 <= ee; e0 += kHalf / 8) {
     const int e = e0 + tid / 8;
     UF l1{0u, 0};
-    int mo = -1, mb = 0;
+    int mo = -1, mb = 0, cnt = 0, mbo = 0;
     if (e <= ee) {
       for (int o = sub; o <= eo; o += 8) {
         bool nz;
@@ -129,7 +153,11 @@ __device__ void summarise_half(const Grid& h, int var, int tid, PolySummary* out
         if (nz) {
           l1 = uf_add(l1, u);
           mo = o;
-          mb = (mb == 0 || bits < mb) ? bits : mb;
+          ++cnt;
+          if (mb == 0 || bits < mb) {
+            mb = bits;
+            mbo = o;
+          }
         }
       }
     }
@@ -137,14 +165,21 @@ __device__ void summarise_half(const Grid& h, int var, int tid, PolySummary* out
     for (int x = 4; x > 0; x >>= 1) {
       l1 = uf_add(l1, shfl_uf(l1, x));
       mo = max(mo, __shfl_xor_sync(0xffffffffu, mo, x));
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, x);
       const int ob = __shfl_xor_sync(0xffffffffu, mb, x);
-      mb = (mb == 0 || (ob != 0 && ob < mb)) ? ob : mb;
+      const int obo = __shfl_xor_sync(0xffffffffu, mbo, x);
+      if (ob != 0 && (mb == 0 || ob < mb || (ob == mb && obo < mbo))) {
+        mb = ob;
+        mbo = obo;
+      }
     }
     if (sub == 0 && mo >= 0) {
       S = uf_add(S, uf_mul(l1, l1));
       if (e > m) {
         m = e;
         lcb = mb;
+        lcnt = cnt;
+        lco = mbo;
       }
       td = max(td, e + mo);
       dego = max(dego, mo);
@@ -155,32 +190,40 @@ __device__ void summarise_half(const Grid& h, int var, int tid, PolySummary* out
   const int slot = tid / 8;
   if (sub == 0) {
     sh_uf[slot] = S;
-    sh_int[5 * slot + 0] = m;
-    sh_int[5 * slot + 1] = td;
-    sh_int[5 * slot + 2] = dego;
-    sh_int[5 * slot + 3] = lcb;
+    sh_int[kSlotInts * slot + 0] = m;
+    sh_int[kSlotInts * slot + 1] = td;
+    sh_int[kSlotInts * slot + 2] = dego;
+    sh_int[kSlotInts * slot + 3] = lcb;
+    sh_int[kSlotInts * slot + 4] = lcnt;
+    sh_int[kSlotInts * slot + 5] = lco;
   }
   __syncthreads();
   if (tid < 32) {
     UF s{0u, 0};
-    int M = -1, TD = -1, DO = -1, LCB = 0;
+    int M = -1, TD = -1, DO = -1, LCB = 0, LCN = 0, LCO = 0;
     for (int w = tid; w < kHalf / 8; w += 32) {
       s = uf_add(s, sh_uf[w]);
-      if (sh_int[5 * w] > M) {
-        M = sh_int[5 * w];
-        LCB = sh_int[5 * w + 3];
+      if (sh_int[kSlotInts * w] > M) {
+        M = sh_int[kSlotInts * w];
+        LCB = sh_int[kSlotInts * w + 3];
+        LCN = sh_int[kSlotInts * w + 4];
+        LCO = sh_int[kSlotInts * w + 5];
       }
-      TD = max(TD, sh_int[5 * w + 1]);
-      DO = max(DO, sh_int[5 * w + 2]);
+      TD = max(TD, sh_int[kSlotInts * w + 1]);
+      DO = max(DO, sh_int[kSlotInts * w + 2]);
     }
 #pragma unroll
     for (int x = 16; x > 0; x >>= 1) {
       s = uf_add(s, shfl_uf(s, x));
       const int oM = __shfl_xor_sync(0xffffffffu, M, x);
       const int oL = __shfl_xor_sync(0xffffffffu, LCB, x);
+      const int oN = __shfl_xor_sync(0xffffffffu, LCN, x);
+      const int oO = __shfl_xor_sync(0xffffffffu, LCO, x);
       if (oM > M) {
         M = oM;
         LCB = oL;
+        LCN = oN;
+        LCO = oO;
       }
       TD = max(TD, __shfl_xor_sync(0xffffffffu, TD, x));
       DO = max(DO, __shfl_xor_sync(0xffffffffu, DO, x));
@@ -191,6 +234,9 @@ __device__ void summarise_half(const Grid& h, int var, int tid, PolySummary* out
       out->td = TD;
       out->dego = DO;
       out->lcb = LCB;
+      out->lcnt = LCN;
+      out->lco = LCO;
+      out->l2S = s.m ? uf_log2_q16_up(s) : 0;
     }
   }
   __syncthreads();
@@ -218,10 +264,11 @@ __device__ int prime_count_warp(const int64_t* lg_prefix, int T, int64_t need) {
 __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, int64_t* offs, Tables T) {
   constexpr int kRows = kPlanThreads / 16;  // row slots per half
   __shared__ UF sh_uf[2][kRows];
-  __shared__ int sh_int[2][5 * kRows];
+  __shared__ int sh_int[2][kSlotInts * kRows];
   __shared__ PolySummary sf, sg;
   __shared__ Plan sP;
   __shared__ int64_t s_need;
+
   // warm L2 with the input grids (read right below)
   if (threadIdx.x == blockDim.x - 1)
     l2_prefetch_range(J.f.c, sizeof(uint32_t) * (size_t)(J.f.dx + 1) * (J.f.dy + 1) * J.f.L);
@@ -235,14 +282,17 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
                  sh_uf[first ? 0 : 1], sh_int[first ? 0 : 1]);
   if (threadIdx.x == 0) {
     int64_t need;
-    sP = plan_head(sf.S, sf.m, sf.td, sf.dego, sg.S, sg.m, sg.td, sg.dego, &need);
+    sP = plan_head_logs(sf.l2S, sf.m, sf.td, sf.dego, sg.l2S, sg.m, sg.td, sg.dego, &need);
     s_need = need;
     if (sP.status == 0 && sP.trivial == 0 && T.lg_prefix[T.T] < need) sP.status = kErrRange;
   }
   __syncthreads();
   if (threadIdx.x < 32 && sP.status == 0 && sP.trivial == 0) {
+    const int lane = threadIdx.x;
     const int k = prime_count_warp(T.lg_prefix, T.T, s_need);
-    if (threadIdx.x == 0) plan_tail(sP, k, sf.lcb, sg.lcb, T.T);
+    // conservative count of primes that can divide a leading row; no coset spares when
+    // both leading rows are monomials (they never vanish on a coset, which avoids 0)
+    if (lane == 0) plan_tail(sP, k, sf.lcb, sg.lcb, T.T, sf.lcnt == 1 && sg.lcnt == 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -277,13 +327,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
 // ------------------------------------------------------------------------------------
 // (a) + (b): reduction, coset scaling, forward transform (decimation in frequency)
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t residue_m(const uint32_t* c, int L, const uint32_t* pw,
-                                              const uint32_t* mpw, uint32_t p, uint32_t pinv) {
-  uint32_t acc = 0;
-  for (int l = 0; l < L; ++l) acc = madd(acc, redc((uint64_t)c[l] * pw[l], p, pinv), p);
-  if (c[L - 1] >> 31) acc = msub(acc, mpw[L], p);
-  return acc;
-}
 
 // in-place forward transform of sm[0..N): output position u holds the value at
 // g * omega^{bitreverse(u)}

@@ -54,6 +54,40 @@ def _oracle_k(f, g, var):
     return R.plan(f, g, var, primes)
 
 
+def _lead_row(f, var):
+    """Coefficients of the leading row in the eliminated variable (var 1: y)."""
+    grid = [list(r) for r in f]
+    if var == 0:  # rows by powers of x
+        width = max(len(r) for r in grid)
+        grid = [[grid[j][i] if i < len(grid[j]) else 0 for j in range(len(grid))]
+                for i in range(width)]
+    for row in reversed(grid):
+        if any(row):
+            return row
+    return []
+
+
+def _check_spares(f, g, var, plan):
+    """Spare primes: the smallest K such that [0, K) holds k_need primes (plus two when a
+    leading row is not a monomial) dividing neither leading row's smallest coefficient."""
+    rows = [_lead_row(f, var), _lead_row(g, var)]
+    mins = []
+    for row in rows:
+        nz = [(abs(c).bit_length(), o, c) for o, c in enumerate(row) if c]
+        mins.append(min(nz)[2])
+    coset = 0 if all(sum(1 for c in row if c) == 1 for row in rows) else 2
+    want = plan["k_need"] + coset
+    K = plan["k_total"]
+    primes = nt.prime_table(K)
+    div = [any(c % p == 0 for c in mins) for p in primes]
+    assert K - sum(div) >= want
+    assert K == want or (K - 1) - sum(div[:-1]) < want      # the smallest such K
+    # every prime that rejects the job (dividing a whole leading row) is among them
+    for p, dv in zip(primes, div):
+        if any(all(c % p == 0 for c in row) for row in rows):
+            assert dv
+
+
 @pytest.mark.parametrize("var", [1, 0])
 def test_planner_matches_oracle(var):
     cases = [cfg1_pair(1), cfg1_pair(2), cfg2_pair(1)]
@@ -70,7 +104,7 @@ def test_planner_matches_oracle(var):
         assert ours["N"] == ref["N"]
         # the planner's bound is an upper bound within one bit of the exact one
         assert ref["k"] <= ours["k_need"] <= ref["k"] + 1
-        assert ours["k_total"] >= ours["k_need"] + 2
+        _check_spares(f, g, var, ours)
         # output limbs hold the bound
         assert 32 * ours["out_limbs"] >= (ref["bound_sq"].bit_length() + 1) // 2 + 1
 
