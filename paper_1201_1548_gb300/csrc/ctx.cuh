@@ -99,6 +99,8 @@ int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_
 // whether the reconstruction of a batch runs in the warp-per-coefficient kernel (whose
 // block size is tunable) or in the block Garner kernel (tiles of kCrtTile coefficients)
 bool crt_warp_kernel(const bs_ctx* ctx, int kmax, int lmax);
+// shared memory of the warp-per-coefficient reconstruction block
+size_t crt_warp_smem(int kmax, int lmax);
 int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const MetaBounds& mb,
                       int cls);
 

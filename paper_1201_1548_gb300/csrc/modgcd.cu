@@ -564,9 +564,7 @@ int mg_launch(bs_ctx* ctx, MgBatch& B, const bs_upoly* a, const bs_upoly* b, cha
   const int gblocks = std::min(m, 4 * ctx->sms);
   k_mg_gather<<<gblocks, 256, 0, s>>>(dj, m, Tv, 0);
   const int crt_grid = (int)std::min<int64_t>(tiles, (int64_t)4 * ctx->sms);
-  const size_t wsm = ((size_t)B.kmax * B.kmax + (size_t)B.kmax * B.lmax + (size_t)B.kmax * kCrtTile +
-                      3 * (size_t)B.kmax + (size_t)kCrtTile * B.kmax + (size_t)kCrtTile * B.lmax) *
-                     sizeof(uint32_t);
+  const size_t wsm = crt_warp_smem(B.kmax, B.lmax);
   auto crt = [&](const WorkList& wl) -> int {
     if (B.kmax <= kCrtWarpMaxK && wsm <= (size_t)ctx->smem_optin - 64) {
       launch_crt_w(crt_grid, kCrtTile, wsm, s, dc, wl, Tv, B.kmax, B.lmax);

@@ -1148,15 +1148,16 @@ __device__ __forceinline__ uint32_t ballot_sub(uint32_t x, uint32_t y, uint32_t&
   return d - ((C >> lane) & 1u);
 }
 
+// sy, sq62, sPk: y_k[q], floor(2^62 / p_q) and the limbs of P_k, staged by the block
 template <int S>
 __device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, int c,
                                             const uint32_t* Xt, const uint32_t* Msm, int L,
                                             const uint32_t* pq, const uint32_t* pinvq,
-                                            uint32_t* sd, const Tables& T) {
+                                            uint32_t* sd, const uint32_t* sy, const uint32_t* sq62,
+                                            const uint32_t* sPk) {
   const int lane = threadIdx.x & 31;
   const int k = P.k_need;
   const int cap = J->cap_limbs;
-  const uint32_t* yk = T.ws_y + T.ws_yoff[k];
   uint64_t flo = 0;
   uint32_t fhi = 0;
 #pragma unroll
@@ -1164,9 +1165,9 @@ __device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, 
     const int q = 32 * s + lane;
     if (q < k) {
       const Mod M{pq[q], pinvq[q]};
-      const uint32_t t = mmul(Xt[q * kCrtTile + c], __ldg(yk + q), M);
+      const uint32_t t = mmul(Xt[q * kCrtTile + c], sy[q], M);
       sd[q] = t;
-      const uint64_t prod = (uint64_t)t * __ldg(T.q62 + q);
+      const uint64_t prod = (uint64_t)t * sq62[q];
       flo += prod;
       fhi += (flo < prod) ? 1u : 0u;
     }
@@ -1185,7 +1186,6 @@ __device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, 
   const uint32_t rhi = fhi + (rlo < flo ? 1u : 0u);
   const uint32_t qr = (rhi << 2) | (uint32_t)(rlo >> 62);
   __syncwarp();
-  const uint32_t* Pk = T.pp + (int64_t)k * T.LPP;
   uint32_t* out = J->out + (int64_t)i * cap;
   uint32_t cin1 = 0, cin2 = 0, cq = 0, bsub = 0;
   uint32_t bprev = 0, cprev1 = 0, cprev2 = 0, qhprev = 0;
@@ -1194,14 +1194,30 @@ __device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, 
     uint64_t acc = 0;
     uint32_t ah = 0;
     if (b0 < L) {
-#pragma unroll 8
-      for (int q = 0; q < k; ++q) {
-        const uint32_t ml = l < L ? Msm[q * L + l] : 0u;
-        const uint64_t prod = (uint64_t)sd[q] * ml;
-        const uint64_t s = acc + prod;
-        ah += (s < acc) ? 1u : 0u;
-        acc = s;
+      // two independent accumulation chains (even and odd q), joined at the end
+      uint64_t a0 = 0, a1 = 0;
+      uint32_t h0 = 0, h1 = 0;
+      const int lc = l < L ? l : 0;
+      const uint32_t keep = l < L ? 0xffffffffu : 0u;
+      int q = 0;
+#pragma unroll 4
+      for (; q + 1 < k; q += 2) {
+        const uint64_t p0 = (uint64_t)sd[q] * (Msm[q * L + lc] & keep);
+        const uint64_t p1 = (uint64_t)sd[q + 1] * (Msm[(q + 1) * L + lc] & keep);
+        const uint64_t s0 = a0 + p0, s1 = a1 + p1;
+        h0 += (s0 < a0) ? 1u : 0u;
+        h1 += (s1 < a1) ? 1u : 0u;
+        a0 = s0;
+        a1 = s1;
       }
+      if (q < k) {
+        const uint64_t p0 = (uint64_t)sd[q] * (Msm[q * L + lc] & keep);
+        const uint64_t s0 = a0 + p0;
+        h0 += (s0 < a0) ? 1u : 0u;
+        a0 = s0;
+      }
+      acc = a0 + a1;
+      ah = h0 + h1 + ((acc < a0) ? 1u : 0u);
     }
     // c' = sum_i t_i M_i from the three-word column sums
     const uint32_t a = (uint32_t)acc, bw = (uint32_t)(acc >> 32), cw = ah;
@@ -1220,7 +1236,7 @@ __device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, 
     cprev2 = c30;
     cprev1 = c31;
     // q P (q < 2^13): limb l = lo(q P_l) + hi(q P_{l-1}) + carry
-    const uint64_t qp = (uint64_t)qr * (l < L && l < T.LPP ? Pk[l] : 0u);
+    const uint64_t qp = (uint64_t)qr * (l < L ? sPk[l] : 0u);
     uint32_t qh = __shfl_up_sync(0xffffffffu, (uint32_t)(qp >> 32), 1);
     const uint32_t qh31 = __shfl_sync(0xffffffffu, (uint32_t)(qp >> 32), 31);
     if (lane == 0) qh = qhprev;
@@ -1251,6 +1267,9 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
   uint32_t* selq = pinvq + kmax;
   uint32_t* sd = selq + kmax + (size_t)warp * kmax;
   uint32_t* Vw = selq + kmax + (size_t)kCrtTile * kmax + (size_t)warp * lmax;
+  uint32_t* sy = selq + kmax + (size_t)kCrtTile * kmax + (size_t)kCrtTile * lmax;  // weighted sum
+  uint32_t* sq62 = sy + kmax;
+  uint32_t* sPk = sq62 + kmax;  // kmax + 4 words
   const int64_t total = wl.off[wl.n];
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
     const int ji = find_item(wl.off, wl.n, item);
@@ -1288,10 +1307,18 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
     const bool ws = table_order && k <= T.WK;
     const int L = ws_len(k);
     if (ws) {
+      // M_k is k rows of L limbs, contiguous: one flat copy with many loads in flight
       const uint32_t* Mk = T.ws_m + T.ws_moff[k];
-      for (int j = warp; j < k; j += nthr / 32)
-#pragma unroll 4
-        for (int l = lane; l < L; l += 32) sinv[j * L + l] = __ldg(Mk + (int64_t)j * L + l);
+      const int n = k * L;
+#pragma unroll 8
+      for (int t = threadIdx.x; t < n; t += nthr) sinv[t] = __ldg(Mk + t);
+      const uint32_t* yk = T.ws_y + T.ws_yoff[k];
+      for (int t = threadIdx.x; t < k; t += nthr) {
+        sy[t] = __ldg(yk + t);
+        sq62[t] = __ldg(T.q62 + t);
+      }
+      const uint32_t* Pk = T.pp + (int64_t)k * T.LPP;
+      for (int t = threadIdx.x; t < L; t += nthr) sPk[t] = t < T.LPP ? __ldg(Pk + t) : 0u;
     } else {
       for (int a = warp; a < k; a += nthr / 32) {
         const int64_t rowa = (int64_t)selq[a] * Tg;
@@ -1312,11 +1339,11 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
       }
       if (ws) {
         switch ((k + 31) >> 5) {
-          case 1: crt_ws_warp<1>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
-          case 2: crt_ws_warp<2>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
-          case 3: crt_ws_warp<3>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
-          case 4: crt_ws_warp<4>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
-          default: crt_ws_warp<5>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, T); break;
+          case 1: crt_ws_warp<1>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, sy, sq62, sPk); break;
+          case 2: crt_ws_warp<2>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, sy, sq62, sPk); break;
+          case 3: crt_ws_warp<3>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, sy, sq62, sPk); break;
+          case 4: crt_ws_warp<4>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, sy, sq62, sPk); break;
+          default: crt_ws_warp<5>(J, P, i0 + c, c, X, sinv, L, pq, pinvq, sd, sy, sq62, sPk); break;
         }
         continue;
       }
