@@ -189,6 +189,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_step_ms(ms, dist, device):
+    """Step time of a replicas-only run: the slowest rank's mean (max over ranks)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ms, world):
+    """Whole-job resultants per second: every rank computes one resultant per step."""
+    return world * 1000.0 / ms
+
+
 def _marshal_pairs(bs, pairs):
     """Pre-marshalled C arrays of a batch (kept alive by the returned tuple)."""
     import ctypes as C
@@ -434,10 +447,8 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
     ms = statistics.mean(step_ms)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1000.0 / ms
+        ms = replica_step_ms(ms, dist, torch.device("cuda", local))
+    value = replica_value(ms, world)
     srt = sorted(step_ms)
     p50 = srt[len(srt) // 2]
     p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
