@@ -303,17 +303,31 @@ int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int v
   for (int i = 0; i < n; ++i)
     if (B.plans[i].status)
       return ctx_fail(ctx, B.plans[i].status, "planning failed for job " + std::to_string(i));
-  for (const Plan& P : B.plans) {
+  B.big.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = B.plans[i];
     if (P.trivial) continue;
     B.needT = std::max(B.needT, P.k_total);
     B.needLog = std::max(B.needLog, P.logN);
-    B.kmax = std::max(B.kmax, P.k_need);
-    B.lmax = std::max(B.lmax, P.out_limbs + 1);
+    if (P.k_need > kCrtWarpMaxK) {  // weighted sums of many primes, Garner for rejections
+      B.big[i] = 1;
+      B.kmax_big = std::max(B.kmax_big, P.k_need);
+      B.lmax_big = std::max(B.lmax_big, P.out_limbs + 1);
+    } else {
+      B.kmax = std::max(B.kmax, P.k_need);
+      B.lmax = std::max(B.lmax, P.out_limbs + 1);
+    }
     B.maxN = std::max(B.maxN, P.N);
     const int c = uni_class_of(std::max(P.me, P.ne) + 1);
     if (c < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
     ++B.cls_count[c];
     if (P.logN <= kWarpLogNMax) ++B.ecls_count[eval_class_of(P.logN)];
+  }
+  {  // the block Garner kernel serves jobs of many primes with rejected primes
+    const size_t need = ((size_t)B.kmax_big * kCrtTile + 3 * (size_t)B.kmax_big + 3 * (size_t)B.lmax_big) *
+                        sizeof(uint32_t);
+    if (need + 64 > (size_t)ctx->smem_optin)
+      return ctx_fail(ctx, BS_ERR_RANGE, "too many primes for the reconstruction stage");
   }
   B.in_f.resize(n);
   B.in_g.resize(n);
@@ -330,6 +344,10 @@ int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int v
   B.o_ioff = up.take(sizeof(int64_t) * (n + 1));
   B.o_iwoff = up.take(sizeof(int64_t) * (n + 1));
   B.o_coff = up.take(sizeof(int64_t) * (n + 1));
+  B.o_cbt = up.take(sizeof(int64_t) * (n + 1));
+  B.o_cbg = up.take(sizeof(int64_t) * (n + 1));
+  B.o_cbc = up.take(sizeof(int64_t) * (n + 1));
+  B.o_cbf = up.take(sizeof(int64_t) * (n + 1));
   for (int c = 0; c < kNumUniClasses; ++c) {
     B.o_cids[c] = up.take(sizeof(int32_t) * std::max(B.cls_count[c], 1));
     B.o_coffs[c] = up.take(sizeof(int64_t) * (B.cls_count[c] + 1));
@@ -348,6 +366,9 @@ int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int v
   B.o_vals.assign(n, 0);
   B.o_rmod.assign(n, 0);
   B.o_sel.assign(n, 0);
+  B.o_wsM.assign(n, 0);
+  B.o_wsY.assign(n, 0);
+  B.o_wsS.assign(n, 0);
   for (int i = 0; i < n; ++i) {
     const Plan& P = B.plans[i];
     if (P.trivial) continue;
@@ -356,6 +377,12 @@ int batch_plan(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g, int v
     B.o_vals[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_total * P.N);
     B.o_rmod[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_need * (P.D + 1));
     B.o_sel[i] = cmp.take(sizeof(int32_t) * P.k_need);
+    if (B.big[i]) {
+      const size_t wl = (size_t)big_ws_len(P.k_need);
+      B.o_wsM[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_need * wl);
+      B.o_wsY[i] = cmp.take(sizeof(uint32_t) * (size_t)P.k_need);
+      B.o_wsS[i] = cmp.take(sizeof(uint32_t) * 3 * (size_t)(std::max(P.D, 0) + 1) * wl);
+    }
   }
   Layout dn;
   dn.used = cmp.used;
@@ -390,6 +417,11 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   int64_t* ioff = (int64_t*)(hu + B.o_ioff);
   int64_t* iwoff = (int64_t*)(hu + B.o_iwoff);
   int64_t* coff = (int64_t*)(hu + B.o_coff);
+  int64_t* cbt = (int64_t*)(hu + B.o_cbt);
+  int64_t* cbg = (int64_t*)(hu + B.o_cbg);
+  int64_t* cbc = (int64_t*)(hu + B.o_cbc);
+  int64_t* cbf = (int64_t*)(hu + B.o_cbf);
+  cbt[0] = cbg[0] = cbc[0] = cbf[0] = 0;
   int32_t* cids[kNumUniClasses];
   int64_t* coffs[kNumUniClasses];
   int cfill[kNumUniClasses] = {0};
@@ -465,7 +497,24 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
     eoff[i + 1] = eoff[i] + ne;
     ioff[i + 1] = ioff[i] + ni;
     iwoff[i + 1] = iwoff[i] + niw;
-    coff[i + 1] = coff[i] + (J.cap_deg + crt_tile) / crt_tile;
+    int64_t nbt = 0, nbg = 0, nbc = 0, nbf = 0;
+    if (B.big[i]) {
+      const int wl = big_ws_len(P.k_need);
+      J.wsM = (uint32_t*)(base + B.o_wsM[i]);
+      J.wsY = (uint32_t*)(base + B.o_wsY[i]);
+      J.wsS = (uint32_t*)(base + B.o_wsS[i]);
+      J.wsL = wl;
+      nbt = (P.k_need + kBigTabThreads - 1) / kBigTabThreads;
+      nbg = (int64_t)((J.cap_deg + kBigGI) / kBigGI) * ((wl + kBigGL - 1) / kBigGL);
+      nbc = (J.cap_deg + kBigCarryWarps) / kBigCarryWarps;
+      nbf = (J.cap_deg + kCrtTile) / kCrtTile;
+      hj[i] = J;
+    }
+    cbt[i + 1] = cbt[i] + nbt;
+    cbg[i + 1] = cbg[i] + nbg;
+    cbc[i + 1] = cbc[i] + nbc;
+    cbf[i + 1] = cbf[i] + nbf;
+    coff[i + 1] = coff[i] + (B.big[i] ? 0 : (J.cap_deg + crt_tile) / crt_tile);
   }
   cudaStream_t s = ctx->stream;
   int rc = ctx_cuda(ctx, cudaMemcpyAsync(base, hu, B.up_bytes, cudaMemcpyHostToDevice, s), "upload");
@@ -478,6 +527,16 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   L.intt = WorkList{nullptr, (const int64_t*)(base + B.o_ioff), n};
   L.intt_w = WorkList{nullptr, (const int64_t*)(base + B.o_iwoff), n};
   L.crt = WorkList{nullptr, (const int64_t*)(base + B.o_coff), n};
+  L.crt_big_tab = WorkList{nullptr, (const int64_t*)(base + B.o_cbt), n};
+  L.crt_big_gemm = WorkList{nullptr, (const int64_t*)(base + B.o_cbg), n};
+  L.crt_big_carry = WorkList{nullptr, (const int64_t*)(base + B.o_cbc), n};
+  L.crt_big_fb = WorkList{nullptr, (const int64_t*)(base + B.o_cbf), n};
+  L.crt_big_items[0] = cbt[n];
+  L.crt_big_items[1] = cbg[n];
+  L.crt_big_items[2] = cbc[n];
+  L.crt_big_items[3] = cbf[n];
+  L.kmax_big = B.kmax_big;
+  L.lmax_big = B.lmax_big;
   for (int c = 0; c < kNumUniClasses; ++c) {
     L.uni[c] = WorkList{(const int32_t*)(base + B.o_cids[c]), (const int64_t*)(base + B.o_coffs[c]),
                         B.cls_count[c]};

@@ -24,6 +24,11 @@ struct HostBatch {
   size_t o_eids[kNumEvalClasses] = {}, o_eoffs[kNumEvalClasses] = {};
   size_t o_status = 0, o_pstat = 0, o_in = 0, up_bytes = 0;
   std::vector<size_t> o_ev, o_vals, o_rmod, o_sel, o_out;
+  // reconstruction of many primes (k_need > kCrtWarpMaxK): weighted-sum workspace and lists
+  std::vector<char> big;
+  std::vector<size_t> o_wsM, o_wsY, o_wsS;
+  size_t o_cbt = 0, o_cbg = 0, o_cbc = 0, o_cbf = 0;
+  int kmax_big = 1, lmax_big = 1;
   size_t dn_start = 0, o_status_dn = 0, dn_bytes = 0, total = 0;
   // statistics
   int64_t instances = 0, mulmods = 0, k_need_sum = 0, k_total_sum = 0;

@@ -89,7 +89,21 @@ struct Job {
   int32_t* rejected;  // counter of rejected primes (may be null)
   // workspace capacities (device-planned jobs): the plan must fit them
   int32_t cap_k_total, cap_k_need, cap_rows, cap_logN, cap_D;
+  // weighted-sum reconstruction of many primes (host batches with k_need > 160; null
+  // otherwise): wsM [k_need][wsL] M_j = P / p_j, wsY [k_need] y_j (Montgomery form),
+  // wsS [3][cap_deg + 1][wsL] column sums of sum_j t_j M_j
+  uint32_t* wsM;
+  uint32_t* wsY;
+  uint32_t* wsS;
+  int32_t wsL;
 };
+
+// Programmatic dependent launch: a stage kernel launched with programmatic stream
+// serialisation may start while its predecessor finishes; it waits for the predecessor's
+// results before touching them, and lets its own successor launch once its blocks are
+// done.  Both instructions are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // work lists: stage work of job ids[i] occupies [off[i], off[i+1]) of a flat index space
 struct WorkList {

@@ -82,6 +82,11 @@ struct MetaBounds {
 struct StageLaunch {
   const Job* jobs;
   WorkList eval, intt, intt_w, crt;
+  // reconstruction of many primes: tables, contraction, carries, Garner for rejections
+  WorkList crt_big_tab{nullptr, nullptr, 0}, crt_big_gemm{nullptr, nullptr, 0},
+      crt_big_carry{nullptr, nullptr, 0}, crt_big_fb{nullptr, nullptr, 0};
+  int64_t crt_big_items[4] = {0, 0, 0, 0};
+  int kmax_big = 1, lmax_big = 1;
   WorkList evw[kNumEvalClasses];  // warp evaluation, one list per transform-size class
   WorkList evw_any;               // warp evaluation of any size class (device plans)
   WorkList uni[kNumUniClasses];

@@ -83,6 +83,17 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
     launch_crt_w(g, L.crt_tile, wsm, s, L.jobs, L.crt, Tv, L.kmax, L.lmax);
   else if (g)
     launch_crt(g, crt_w * 32, crt_smem, s, L.jobs, L.crt, Tv, L.kmax, L.lmax, crt_staged);
+  if (L.crt_big_items[2]) {  // jobs with many primes
+    launch_bigcrt(grid_for(L.crt_big_items[0], (int64_t)sms * 8),
+                  grid_for(L.crt_big_items[1], (int64_t)sms * 8),
+                  grid_for(L.crt_big_items[2], (int64_t)sms * 8), s, L.jobs, L.crt_big_tab,
+                  L.crt_big_gemm, L.crt_big_carry, Tv);
+    size_t fsm = 0;
+    int fst = 0;
+    const int fw = crt_warps(ctx, L.kmax_big, L.lmax_big, &fsm, &fst);
+    g = grid_for(L.crt_big_items[3], (int64_t)sms * 4);
+    if (g && fw) launch_crt(g, fw * 32, fsm, s, L.jobs, L.crt_big_fb, Tv, L.kmax_big, L.lmax_big, fst, 1);
+  }
   set_launch_pdl(false);
   mark(ctx, 5, s);
 }

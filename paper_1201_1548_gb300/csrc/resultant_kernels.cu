@@ -18,18 +18,10 @@
 #include "common.cuh"
 #include "resultant_kernels.cuh"
 #include "unires.cuh"
+#include "ballot.cuh"
 #include "warp_ntt.cuh"
 
 namespace bs {
-
-// ------------------------------------------------------------------------------------
-// programmatic dependent launch: a stage kernel launched with programmatic stream
-// serialisation may start while its predecessor finishes; it waits for the predecessor's
-// results before touching them, and lets its own successor launch once its blocks are
-// done.  Both instructions are no-ops for an ordinary launch.
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ------------------------------------------------------------------------------------
 // L2 prefetch of the table ranges a job will read (the step may start with a cold L2):
@@ -809,8 +801,10 @@ __device__ __forceinline__ void crt_carry_out(const uint32_t* V, int nlimbs, int
   if (carry_lo != 0) *ovf = true;
 }
 
+// skip_big: leave table-ordered jobs with k_need > kCrtWarpMaxK to the weighted-sum
+// kernels of many primes (this kernel then serves their jobs with rejected primes)
 __global__ void __launch_bounds__(kCrtWarps * 32) k_crt(const Job* jobs, WorkList wl, Tables T,
-                                                        int kmax, int lmax, int staged) {
+                                                        int kmax, int lmax, int staged, int skip_big) {
   pdl_wait();
   extern __shared__ uint32_t smc[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -856,6 +850,10 @@ __global__ void __launch_bounds__(kCrtWarps * 32) k_crt(const Job* jobs, WorkLis
     }
     __syncthreads();
     const bool table_order = (selq[k - 1] == (uint32_t)(k - 1));
+    if (skip_big && table_order && k > kCrtWarpMaxK) {  // uniform across the block
+      __syncthreads();  // every thread has read selq before the next item restages it
+      continue;
+    }
     const int nl = min(min(P.out_limbs, lmax), T.LPP);  // limbs of the magnitude
     if (inv_in_smem) {
       // all loads of the staging are independent: unrolled so many are in flight
@@ -986,16 +984,6 @@ __global__ void __launch_bounds__(kCrtWarps * 32) k_crt(const Job* jobs, WorkLis
 // Adds the three-word column sums V_l = a_l + b_l 2^32 + c_l 2^64 (weight 2^(32 l)) into
 // limbs: the result is A + (B shifted one limb) + (C shifted two limbs), two additions
 // whose one-bit carries are resolved per 32-limb chunk with generate/propagate ballots.
-__device__ __forceinline__ uint32_t ballot_add(uint32_t x, uint32_t y, uint32_t& cin, int lane) {
-  const uint32_t s = x + y;
-  const uint32_t G = __ballot_sync(0xffffffffu, s < x);
-  const uint32_t Pm = __ballot_sync(0xffffffffu, s == 0xffffffffu) & ~G;
-  const uint32_t X = G | Pm;
-  const uint64_t S = (uint64_t)X + G + cin;
-  const uint32_t C = (uint32_t)S ^ X ^ G;
-  cin = (uint32_t)(S >> 32);
-  return s + ((C >> lane) & 1u);
-}
 
 template <int S>
 __device__ __forceinline__ void crt_coef_warp(const Job* J, const Plan& P, int i, int c,
@@ -1137,16 +1125,6 @@ __device__ __forceinline__ void crt_coef_warp(const Job* J, const Plan& P, int i
 // below k 2^-31, far inside the 1/4 margin that prod p > 4B leaves around an integer, so
 // q is exact.  c comes out directly in two's complement.  Msm holds M_k (k rows of L
 // limbs), sd receives t_i.
-__device__ __forceinline__ uint32_t ballot_sub(uint32_t x, uint32_t y, uint32_t& bin, int lane) {
-  const uint32_t d = x - y;
-  const uint32_t G = __ballot_sync(0xffffffffu, x < y);            // generates a borrow
-  const uint32_t Pm = __ballot_sync(0xffffffffu, d == 0u) & ~G;   // propagates one
-  const uint32_t X = G | Pm;
-  const uint64_t S = (uint64_t)X + G + bin;
-  const uint32_t C = (uint32_t)S ^ X ^ G;
-  bin = (uint32_t)(S >> 32);
-  return d - ((C >> lane) & 1u);
-}
 
 // sy, sq62, sPk: y_k[q], floor(2^62 / p_q) and the limbs of P_k, staged by the block
 template <int S>
@@ -1505,8 +1483,8 @@ void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkLis
   launch_k(k_intt, grid, kEvalThreads, smem, s, jobs, wl, T);
 }
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
-                Tables T, int kmax, int lmax, int staged) {
-  launch_k(k_crt, grid, threads, smem, s, jobs, wl, T, kmax, lmax, staged);
+                Tables T, int kmax, int lmax, int staged, int skip_big) {
+  launch_k(k_crt, grid, threads, smem, s, jobs, wl, T, kmax, lmax, staged, skip_big);
 }
 void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T) {
   k_plan_single<<<1, kPlanThreads, 0, s>>>(J, dst, offs, T);

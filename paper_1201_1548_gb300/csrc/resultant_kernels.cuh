@@ -44,7 +44,7 @@ constexpr int kPfIssuers = 128;   // blocks that issue one prefetch chunk each
 void launch_eval_w(int cls, int grid, int warps, cudaStream_t s, const Job* jobs, WorkList wl,
                    Tables T, PfHint pf);
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
-                Tables T, int kmax, int lmax, int staged);
+                Tables T, int kmax, int lmax, int staged, int skip_big = 0);
 void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T);
 int set_stage_smem_limits(int optin);
 // launches of the stage kernels from the calling thread use programmatic dependent launch
@@ -53,6 +53,15 @@ void set_launch_pdl(bool on);
 // raise a kernel's dynamic shared memory limit to what the opt-in size leaves next to its
 // static shared memory
 int set_dyn_smem_limit(const void* func, int optin);
+
+// weighted-sum reconstruction of many primes (k_need > kCrtWarpMaxK, host batches)
+constexpr int kBigTabThreads = 128;  // primes per table block
+constexpr int kBigGI = 32, kBigGL = 64, kBigGJ = 32;  // contraction tile: coefficients, limbs, primes
+constexpr int kBigCarryWarps = 8;    // coefficients per carry block
+// limbs of M_j = P / p_j for k primes (P < 2^(31 k))
+inline int big_ws_len(int k) { return (31 * k + 31) / 32 + 1; }
+void launch_bigcrt(int g_tab, int g_gemm, int g_carry, cudaStream_t s, const Job* jobs, WorkList tab,
+                   WorkList gemm, WorkList carry, Tables T);
 
 // degree classes of the univariate stage: max(m_e, n_e) + 1 <= class length
 constexpr int kUniClasses[] = {8, 16, 24, 33, 48, 65};

@@ -258,3 +258,29 @@ def test_autotune_batch(ctx):
         assert ctx.resultant_batch(pairs) == ref
     finally:
         ctx.set_tune()
+
+
+def test_many_primes_with_a_rejected_prime(ctx):
+    """k above the warp limit and the first table prime dividing the leading row: that
+    prime is rejected, so the selection is not the first k table primes and the block
+    Garner kernel reconstructs this job."""
+    import paper_1201_1548_gb300 as bs
+    p0 = bs.bs_prime_table(1)[0]
+    rng = _rng(210)
+    f = dense_curve(rng, 8, 600)
+    f[8] = [c * p0 for c in f[8]]
+    g = d_dy(f)
+    assert bs.bs_plan(f, g)["k_need"] > 160
+    r = ctx.resultant(f, g)
+    assert ctx.last_stats()["primes_rejected"] >= 1
+    for x0 in (0, 1, -1):
+        assert P.evaluate(r, x0) == R.res_at_point(f, g, x0)
+    p = 2147483647
+    assert P.evaluate(r, 4242) % p == R.res_at_point_modp(f, g, 4242, p)
+    # the same job inside a batch next to jobs with few and with many primes
+    small = cfg1_pair(2)
+    big = (dense_curve(rng, 8, 600), dense_curve(rng, 8, 600))
+    got = ctx.resultant_batch([small, (f, g), big])
+    assert got[0] == R.res_y(*small)
+    assert got[1] == r
+    assert got[2] == ctx.resultant(*big)
