@@ -62,8 +62,12 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   }
   g = grid_for(L.evw_any_items, (int64_t)sms * 8);
   if (g) launch_eval_w(-1, g, kEvalThreads / 32, s, L.jobs, L.evw_any, Tv, pf);
-  g = grid_for(L.eval_items, (int64_t)sms * 8);
-  if (g) launch_eval(g, tsmem, s, L.jobs, L.eval, Tv);
+  // persistent blocks of C = N / 1024 warps, about 16 warps per SM; a device plan sizes
+  // this launch from the extents and usually leaves it empty, so there it stays small
+  const int ecw = std::max(2, L.maxN >> 10);
+  const int ebps = L.kt_max < 0 ? 2 : std::max(1, 16 / ecw);
+  g = grid_for(L.eval_items, (int64_t)sms * ebps);
+  if (g) launch_eval(g, ecw, s, L.jobs, L.eval, Tv);
   mark(ctx, 2, s);
   for (int c = 0; c < kNumUniClasses; ++c) {
     const int th = L.uni_threads[c];

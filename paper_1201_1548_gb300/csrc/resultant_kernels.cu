@@ -320,25 +320,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
 // (a) + (b): reduction, coset scaling, forward transform (decimation in frequency)
 // ------------------------------------------------------------------------------------
 
-// in-place forward transform of sm[0..N): output position u holds the value at
-// g * omega^{bitreverse(u)}
-__device__ __forceinline__ void dif_ntt(uint32_t* sm, int logN, const uint32_t* tw, int logNT,
-                                        const Mod M) {
-  const int N = 1 << logN;
-  for (int lg = logN - 1; lg >= 0; --lg) {
-    const int len = 1 << lg;
-    const int stride_sh = logNT - (lg + 1);
-    for (int bf = threadIdx.x; bf < (N >> 1); bf += blockDim.x) {
-      const int j = bf & (len - 1);
-      const int i0 = ((bf >> lg) << (lg + 1)) + j;
-      const int i1 = i0 + len;
-      const uint32_t u = sm[i0], v = sm[i1];
-      sm[i0] = madd(u, v, M.p);
-      sm[i1] = mmul(msub(u, v, M.p), tw[j << stride_sh], M);
-    }
-    __syncthreads();
-  }
-}
 
 // in-place inverse transform (decimation in time) of bit-reversed input; output natural
 // order, scaled by N
@@ -361,9 +342,21 @@ __device__ __forceinline__ void dit_intt(uint32_t* sm, int logN, const uint32_t*
   }
 }
 
-__global__ void __launch_bounds__(kEvalThreads) k_eval(const Job* jobs, WorkList wl, Tables T) {
+// Transforms of N = 1024 C points (C = 2 .. 16), one block of C warps per (prime, row).
+// Thread t (of 32 C) holds the 32 points t + 32 C r in registers: the stages whose
+// partners are 1024 or more apart pair registers (twiddles from the packed table in
+// global memory); a transpose through shared memory then gives warp w the contiguous
+// points [1024 w, 1024 w + 1024) in layout A, and the warp finishes with the 1024-point
+// register transform (packed twiddles below 1024 staged in shared memory).  Blocks may
+// have more warps than a job's C; the extra warps idle.
+// Dynamic shared memory (words): [N_max transpose][1024 twiddles][C_max * 33 * 32 staging].
+__global__ void __launch_bounds__(kEvalBigMaxWarps * 32) k_eval(const Job* jobs, WorkList wl, Tables T) {
   pdl_wait();
   extern __shared__ uint32_t sm[];
+  const int cmax = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* s_tw = sm + 1024 * cmax;            // after the largest transpose buffer
+  uint32_t* sw = s_tw + 1024 + warp * (33 * 32);
   const int64_t total = wl.off[wl.n];
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
     const int ji = find_item(wl.off, wl.n, item);
@@ -375,6 +368,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(const Job* jobs, WorkList
     const int me = J->plan.me;
     const int logN = J->plan.logN;
     const int N = 1 << logN;
+    const int C = N >> 10;  // chunks of 1024 points; C <= cmax
     const bool isf = row <= me;
     const int e = isf ? row : row - me - 1;
     const Grid G = isf ? J->f : J->g;
@@ -384,21 +378,53 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(const Job* jobs, WorkList
     const uint32_t* pw = T.pw + (int64_t)q * (kMaxLimbs + 1);
     const uint32_t* mpw = T.mpw + (int64_t)q * (kMaxLimbs + 1);
     const uint32_t* cp = T.cp + (int64_t)q * T.NT;
+    const uint32_t* Pg = T.twp + (int64_t)q * T.NT;  // packed twiddles of this prime
     const int eo = ext_o(G, var);
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
-      uint32_t acc = 0;
-      for (int o = t; o <= eo; o += N) {
-        const uint32_t r = residue_m(coef_ptr(G, var, e, o), G.L, pw, mpw, M.p, M.pinv);
-        const uint32_t s = (o < T.NT) ? cp[o] : mpow(pc.g_m, (uint32_t)o, pc.one_m, M);
-        acc = madd(acc, mmul(r, s, M), M.p);
+    __syncthreads();  // the previous item is done with the shared buffers
+    for (int t = threadIdx.x; t < 1024; t += blockDim.x) s_tw[t] = __ldg(Pg + t);
+    const int tid = threadIdx.x;
+    const bool active = warp < C;
+    uint32_t v[32];
+    if (active) {
+      // residues times g^o at the points tid + 32 C r (folded modulo N)
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const int pt = tid + 32 * C * r;
+        uint32_t acc = 0;
+        for (int o = pt; o <= eo; o += N) {
+          const uint32_t x = residue_m(coef_ptr(G, var, e, o), G.L, pw, mpw, M.p, M.pinv);
+          const uint32_t s = (o < T.NT) ? __ldg(cp + o) : mpow(pc.g_m, (uint32_t)o, pc.one_m, M);
+          acc = madd(acc, mmul(x, s, M), M.p);
+        }
+        v[r] = acc;
       }
-      sm[t] = acc;
+      // stages with partners len = 512 C, 256 C, ..., 1024 apart: registers r, r + h
+#pragma unroll
+      for (int lh = 4; lh >= 1; --lh) {
+        const int h = 1 << lh;
+        if (h * C < 32) break;  // len = 32 C h < 1024: done in the chunks
+        const int len = 32 * C * h;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          if (r & h) continue;
+          const uint32_t w = __ldg(Pg + len + tid + 32 * C * (r & (h - 1)));
+          const uint32_t a = v[r], b = v[r + h];
+          v[r] = madd(a, b, M.p);
+          v[r + h] = mmul(msub(a, b, M.p), w, M);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) sm[tid + 32 * C * r] = v[r];
     }
     __syncthreads();
-    dif_ntt(sm, logN, T.tw + (int64_t)q * (T.NT >> 1), T.logNT, M);
-    uint32_t* dst = J->ev + ((int64_t)q * rows + row) * N;
-    for (int t = threadIdx.x; t < N; t += blockDim.x) dst[t] = sm[t];
-    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = sm[1024 * warp + 32 * r + lane];
+      warp_dif_1024_pk<0xffffffffu>(v, sw, s_tw, M);
+      uint32_t* dst = J->ev + ((int64_t)q * rows + row) * N + 1024 * warp;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) dst[32 * r + lane] = v[r];
+    }
   }
   pdl_trigger();
 }
@@ -1460,8 +1486,9 @@ void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const
   }
 }
 
-void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
-  launch_k(k_eval, grid, kEvalThreads, smem, s, jobs, wl, T);
+void launch_eval(int grid, int warps, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
+  const size_t smem = sizeof(uint32_t) * ((size_t)1024 * warps + 1024 + (size_t)warps * 33 * 32);
+  launch_k(k_eval, grid, warps * 32, smem, s, jobs, wl, T);
 }
 void launch_eval_w(int cls, int grid, int warps, cudaStream_t s, const Job* jobs, WorkList wl,
                    Tables T, PfHint pf) {

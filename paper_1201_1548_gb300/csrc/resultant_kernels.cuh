@@ -27,7 +27,9 @@ int uni_occupancy(int cls, int threads);
 void launch_uni(int cls, int grid, int threads, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_uni_direct(int cls, int n, cudaStream_t s, const int32_t* idx, const uint32_t* a, int da,
                        int lda, const uint32_t* b, int db, int ldb, uint32_t* res, Tables T);
-void launch_eval(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
+// transforms of N > 2^kWarpLogNMax points: blocks of `warps` = max N / 1024 warps
+constexpr int kEvalBigMaxWarps = 16;
+void launch_eval(int grid, int warps, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 void launch_intt(int grid, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 // one warp per (job, prime) for N <= 2^kWarpInttLogNMax
 void launch_intt_w(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
