@@ -524,9 +524,9 @@ __device__ __forceinline__ void eval_row_class(const Job* J, int q, int row, con
 
 // R > 0: every job of the list has N = 32 R (R = 1: N <= 32).  R = 0: any N up to
 // 2^kWarpLogNMax, dispatched per job (device-planned jobs, whose size the host does not
-// know).  Three blocks per SM: the largest class fits that register budget without spills.
+// know).  Four blocks per SM (64 registers) run the warps of several rows side by side.
 template <int R>
-__global__ void __launch_bounds__(kEvalThreads, 3) k_eval_w(const Job* jobs, WorkList wl,
+__global__ void __launch_bounds__(kEvalThreads, 4) k_eval_w(const Job* jobs, WorkList wl,
                                                                           Tables T, PfHint pf) {
   pdl_wait();
   constexpr int NS = R == 0 ? (1 << kWarpLogNMax) : 32 * R;  // largest transform size
