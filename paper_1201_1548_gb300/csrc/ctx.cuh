@@ -50,9 +50,6 @@ struct bs_ctx {
   bs::Tune tune;
   // cached executable graph of the batched stages
   cudaGraphExec_t graph_exec = nullptr;
-  // square-free / gcd scratch
-  void* extra = nullptr;
-  size_t extra_cap = 0;
   std::string err;
   bs_stats stats{};
   // per-stage timing: events 0..5 bracket plan | eval | unires | intt | crt

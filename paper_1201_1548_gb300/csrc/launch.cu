@@ -213,7 +213,4 @@ void ctx_release_extra(bs_ctx* ctx) {
     if (ctx->prof_ev[i]) cudaEventDestroy(ctx->prof_ev[i]);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   ctx->graph_exec = nullptr;
-  if (ctx->extra) cudaFree(ctx->extra);
-  ctx->extra = nullptr;
-  ctx->extra_cap = 0;
 }

@@ -1,13 +1,16 @@
 // Device stages of the modular resultant (Sec. 5.1, steps (a)-(e)):
 //
-//   k_plan_single   plan of one device-resident job (degrees, bound, primes)
-//   k_eval          (a)+(b): reduce a coefficient row mod p, scale by g^i and evaluate it
-//                   on the coset g * <omega> with a forward transform in shared memory
+//   k_plan_single   plan of one device-resident job (degrees, bound, primes, spares)
+//   k_eval_w<R>     (a)+(b): reduce a coefficient row mod p, scale by g^i and evaluate it
+//                   on the coset g * <omega>: one warp per row, N = 32 R points in
+//                   registers (R = 0: the size class is read per job)
+//   k_eval          the same for N > 1024: one block of N / 1024 warps per row
 //   k_unires<L>     (c): one univariate resultant mod p per thread, formal degrees,
 //                   detection of points where a leading coefficient vanishes
-//   k_intt          prime selection + (d): inverse transform, unscaling, degree check
-//   k_crt           (e): Garner mixed-radix digits, sign decision and conversion to
-//                   two's complement limbs, one warp per coefficient
+//   k_intt          prime selection + (d): inverse transform, unscaling, degree check,
+//                   one block per prime; k_intt_w: one warp per prime (N <= 512)
+//   k_crt_w<TILE>   (e): weighted-sum or Garner reconstruction, one warp per coefficient
+//   k_crt           (e): block Garner for many primes (see also bigcrt.cu)
 //
 // All stage kernels are persistent: the grid is a multiple of the SM count and blocks
 // stride over a flat work index whose extent is read from device memory, so the same
