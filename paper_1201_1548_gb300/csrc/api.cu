@@ -258,6 +258,10 @@ extern "C" int bs_resultant_bounds(const bs_bipoly* f, const bs_bipoly* g, int v
 // copy one result coefficient block (rows of src_limbs two's complement limbs) into a
 // caller buffer of dst_limbs, checking that each value fits
 static bool copy_coeffs(const uint32_t* src, int src_limbs, int ncoef, uint32_t* dst, int dst_limbs) {
+  if (src_limbs == dst_limbs) {  // same width: one copy
+    std::memcpy(dst, src, sizeof(uint32_t) * (size_t)ncoef * src_limbs);
+    return true;
+  }
   for (int i = 0; i < ncoef; ++i) {
     const uint32_t* s = src + (size_t)i * src_limbs;
     uint32_t* d = dst + (size_t)i * dst_limbs;
