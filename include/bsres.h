@@ -11,8 +11,9 @@
  *     reconstruct the integer coefficients by mixed-radix Chinese remaindering;
  *   - the monic gcd of two polynomials in Z_p[x] (Sec. 5.1, "Computing gcds in Z[x]",
  *     step (b));
- *   - the square-free part of a polynomial in Z[x] (Sec. 2.1, BiProject: Yun's
- *     square-free factorisation starts from gcd(R, R')).
+ *   - the square-free part of a polynomial in Z[x] and its full square-free
+ *     factorisation by Yun's algorithm (Sec. 2.1, BiProject), and the gcd in Z[x], all
+ *     by the modular route of Sec. 5.1 ("Computing gcds in Z[x]").
  *
  * Integer encoding.  Every integer coefficient is a fixed number of little-endian
  * uint32 limbs in two's complement (limb 0 is the least significant; the sign is the
@@ -203,6 +204,10 @@ int bs_prime_table(int count, uint32_t *primes);
 
 /* ---------------------------------------------------------------------------------
  * gcd and square-free part (Sec. 5.1 "Computing gcds in Z[x]"; Sec. 2.1 BiProject)
+ *
+ * The univariate inputs of bs_squarefree_part, bs_gcd_z, bs_modgcd_batch and the
+ * square-free factorisation take up to 256 limbs per coefficient (8192 bits), so a
+ * resultant's output can be passed back as input.
  * ------------------------------------------------------------------------------ */
 
 /* Monic gcd of a (degree da) and b (degree db) in Z_p[x], p prime (2 < p < 2^31),
@@ -249,6 +254,36 @@ int bs_gcd_z(bs_ctx *ctx, const bs_upoly *a, const bs_upoly *b, bs_upoly *out);
  * bounds and nothing runs.  Returns the first failing job's status. */
 int bs_modgcd_batch(bs_ctx *ctx, int n, const int *kind, const bs_upoly *a, const bs_upoly *b,
                     bs_upoly *out);
+
+/* Square-free factorisation of a non-zero R in Z[x] by Yun's algorithm (Sec. 2.1,
+ * BiProject): the primitive, square-free, pairwise coprime r_1, ..., r_s with positive
+ * leading coefficients and R = c r_1 r_2^2 ... r_s^s for an integer c; r_s is not
+ * constant, and a multiplicity below s that R does not have gives r_i = 1.  A constant R
+ * has no factors (s = 0).  Yun's algorithm runs modulo many primes; primes dividing lc(R)
+ * are skipped and only those with the minimal deg gcd(R, R') mod p are used (they agree
+ * on the factor degrees); the images lc(R) monic(r_i) are lifted by Chinese remaindering
+ * up to Mignotte's bound 2^deg(r_i) ||R||_2, and their contents removed (Sec. 5.1).
+ *
+ * r: host buffer in the layout of bs_squarefree_part.
+ * out: host buffer owned by the caller receiving the factors packed one after the other:
+ * the deg r_1 + 1 coefficients of r_1 (ascending), then those of r_2, and so on, out->limbs
+ * limbs each (sign-extended); on success out->deg = (total coefficients) - 1, or -1 for s = 0.
+ * fdeg: host array of cap_factors entries receiving deg r_1, ..., deg r_s; *nfac = s.
+ * With out->c == NULL the call only writes upper bounds (out->deg = 2 deg R - 1, out->limbs,
+ * *nfac = deg R as the factor capacity) and returns BS_OK.
+ *
+ * The call waits for the device.  Errors: BS_ERR_ARG, BS_ERR_ZERO for R = 0, BS_ERR_RANGE
+ * when 4 (deg r + 1) words exceed one block's shared memory or the bound exceeds the prime
+ * table, BS_ERR_CAPACITY when out or cap_factors is too small, BS_ERR_UNLUCKY when fewer
+ * than the needed primes agree on the minimal gcd degree and the factor degrees. */
+int bs_squarefree_factorization(bs_ctx *ctx, const bs_upoly *r, int cap_factors, int32_t *fdeg,
+                                int32_t *nfac, bs_upoly *out);
+
+/* n factorisations in one pass of launches: job j reads r[j] and writes out[j], nfac[j]
+ * and fdeg[j * cap_factors ...].  If any out[j].c is NULL, every job receives its upper
+ * bounds and nothing runs.  Returns the first failing job's status. */
+int bs_squarefree_factorization_batch(bs_ctx *ctx, int n, const bs_upoly *r, int cap_factors,
+                                      int32_t *fdeg, int32_t *nfac, bs_upoly *out);
 
 /* Launch shapes of the batched stages (bs_autotune_batch). */
 typedef struct {

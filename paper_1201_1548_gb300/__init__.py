@@ -31,6 +31,16 @@ from ._abi import (  # noqa: F401
     bs_squarefree_part,
     EXPORTED_SYMBOLS,
     BS_PENDING,
+    BS_OK,
+    BS_ERR_ARG,
+    BS_ERR_NOMEM,
+    BS_ERR_UNLUCKY,
+    BS_ERR_TIMEOUT,
+    BS_ERR_CUDA,
+    BS_ERR_ZERO,
+    BS_ERR_RANGE,
+    BS_ERR_INTERNAL,
+    BS_ERR_CAPACITY,
     JOB_RESULTANT,
     JOB_GCD,
     JOB_SQFREE,

@@ -19,6 +19,7 @@ EXPORTED_SYMBOLS = [
     "bs_gcd_modp", "bs_squarefree_part", "bs_plan", "bs_alu_probe", "bs_profile",
     "bs_stage_times", "bs_resultant_device_noalloc", "bs_gcd_z", "bs_modgcd_batch",
     "bs_autotune_batch", "bs_set_tune", "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
+    "bs_squarefree_factorization", "bs_squarefree_factorization_batch",
 ]
 
 
@@ -76,6 +77,9 @@ class _ServeInfo(C.Structure):
 
 
 BS_PENDING = 10
+# status codes of include/bsres.h
+(BS_OK, BS_ERR_ARG, BS_ERR_NOMEM, BS_ERR_UNLUCKY, BS_ERR_TIMEOUT, BS_ERR_CUDA, BS_ERR_ZERO,
+ BS_ERR_RANGE, BS_ERR_INTERNAL, BS_ERR_CAPACITY) = range(10)
 JOB_RESULTANT, JOB_GCD, JOB_SQFREE = 0, 1, 2
 
 
@@ -126,6 +130,8 @@ def load_library():
                                       C.POINTER(_TuneInfo)]
     lib.bs_set_tune.argtypes = [P, C.POINTER(_TuneInfo)]
     lib.bs_modgcd_batch.argtypes = [P, I, P, P, P, P]
+    lib.bs_squarefree_factorization.argtypes = [P, C.POINTER(_Upoly), I, P, P, C.POINTER(_Upoly)]
+    lib.bs_squarefree_factorization_batch.argtypes = [P, I, P, I, P, P, P]
     lib.bs_serve_start.argtypes = [P, I, I, C.c_size_t]
     lib.bs_serve_stop.argtypes = [P]
     lib.bs_submit.argtypes = [P, C.POINTER(_Job), C.POINTER(C.c_uint64)]
@@ -361,6 +367,46 @@ class Context:
                                              C.cast(out, C.c_void_p)))
         return [limbs_to_ints(bufs[j], out[j].deg + 1, out[j].limbs) if out[j].deg >= 0 else []
                 for j in range(n)]
+
+    def squarefree_factorization(self, r):
+        """Yun's square-free factorisation of the ascending integer list r: the list
+        [r_1, ..., r_s] of primitive factors (positive leading coefficients) with
+        r = c * prod r_i**i; a constant has no factors."""
+        return self.squarefree_factorization_batch([r])[0]
+
+    def squarefree_factorization_batch(self, polys):
+        n = len(polys)
+        keep = []
+        inp = (_Upoly * n)()
+        for j, r in enumerate(polys):
+            arr, L = ints_to_limbs(r)
+            keep.append(arr)
+            inp[j] = _Upoly(len(r) - 1, L, arr.ctypes.data)
+        out = (_Upoly * n)()
+        for j in range(n):
+            out[j] = _Upoly(0, 0, None)
+        nfac = np.zeros(n, dtype=np.int32)
+        args = lambda cap, fdeg: (self.h, n, C.cast(inp, C.c_void_p), int(cap),
+                                  fdeg.ctypes.data, nfac.ctypes.data, C.cast(out, C.c_void_p))
+        fdeg = np.zeros(1, dtype=np.int32)
+        self._check(self.lib.bs_squarefree_factorization_batch(*args(0, fdeg)))
+        cap = max(1, int(nfac.max()) if n else 1)
+        fdeg = np.zeros(n * cap, dtype=np.int32)
+        bufs = []
+        for j in range(n):
+            buf = np.zeros((max(out[j].deg, 0) + 1) * max(out[j].limbs, 1), dtype=np.uint32)
+            bufs.append(buf)
+            out[j] = _Upoly(out[j].deg, max(out[j].limbs, 1), buf.ctypes.data)
+        self._check(self.lib.bs_squarefree_factorization_batch(*args(cap, fdeg)))
+        res = []
+        for j in range(n):
+            coefs = limbs_to_ints(bufs[j], out[j].deg + 1, out[j].limbs) if out[j].deg >= 0 else []
+            facs, pos = [], 0
+            for d in fdeg[j * cap: j * cap + int(nfac[j])]:
+                facs.append(coefs[pos: pos + int(d) + 1])
+                pos += int(d) + 1
+            res.append(facs)
+        return res
 
     # ---- serving loop -----------------------------------------------------------------
     def serve_start(self, slots=3, max_batch=64, arena_bytes=0):

@@ -55,6 +55,7 @@ struct MgBatch {
   std::vector<std::vector<uint32_t>> special_out;
   std::vector<int> gen;  // indices of the jobs that run on the device
   int kmax = 1, lmax = 1, needT = 1;
+  int in_limbs = 1;  // widest input coefficient
   int64_t items = 0;
   size_t smem = 0;
   int threads = 32;

@@ -23,6 +23,7 @@
 
 #include "batch.cuh"
 #include "ctx.cuh"
+#include "modpoly.cuh"
 #include "wbig.cuh"
 
 namespace bs {
@@ -48,49 +49,6 @@ struct MgJob {
   Job* crt;           // [2] reconstructions of H and of the result
 };
 
-// ---- images: one block per (job, prime) -----------------------------------------------
-__device__ __forceinline__ uint32_t reduce_coef(const uint32_t* c, int L, const uint32_t* pw,
-                                                const uint32_t* mpw, const PrimeConst& pc) {
-  uint32_t acc = 0;
-  for (int l = 0; l < L; ++l) acc = madd(acc, redc((uint64_t)c[l] * pw[l], pc.p, pc.pinv), pc.p);
-  if (c[L - 1] >> 31) acc = msub(acc, mpw[L], pc.p);
-  return acc;  // Montgomery form
-}
-
-// division-free Euclid on X (degree la) and Y (degree lb) in shared memory; returns the
-// pointer holding the gcd and its degree in *dgo (the gcd is not normalised)
-__device__ uint32_t* smem_euclid(uint32_t* X, int la, uint32_t* Y, int lb, const Mod M, int* dgo,
-                                 int* s_top) {
-  while (true) {
-    if (la < lb) {
-      uint32_t* t = X;
-      X = Y;
-      Y = t;
-      const int u = la;
-      la = lb;
-      lb = u;
-    }
-    if (lb < 0) break;
-    const int sh = la - lb;
-    const uint32_t a0 = X[la], b0 = Y[lb];
-    const uint32_t na0 = mneg(a0, M.p);
-    for (int i = threadIdx.x; i < la; i += blockDim.x) {
-      const uint32_t bi = (i >= sh) ? Y[i - sh] : 0u;
-      X[i] = redc((uint64_t)b0 * X[i] + (uint64_t)na0 * bi, M.p, M.pinv);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int l = la - 1;
-      while (l >= 0 && X[l] == 0) --l;
-      *s_top = l;
-    }
-    __syncthreads();
-    la = *s_top;
-    __syncthreads();
-  }
-  *dgo = la;
-  return X;
-}
 
 __global__ void k_mg_images(const MgJob* jobs, WorkList wl, Tables T) {
   extern __shared__ uint32_t sm[];
@@ -247,12 +205,6 @@ __global__ void k_mg_content(const MgJob* jobs, int n, int K) {
 }
 
 // ---- per selected prime: m (s c)^-1 mod p, s the sign of lc(a) -------------------------
-__device__ __forceinline__ uint32_t mag_mod(const uint32_t* c, int L, uint32_t p) {
-  uint64_t acc = 0;
-  for (int l = L - 1; l >= 0; --l) acc = ((acc << 32) | c[l]) % p;
-  return (uint32_t)acc;
-}
-
 __global__ void k_mg_cinv(const MgJob* jobs, int n, Tables T) {
   for (int ji = blockIdx.x; ji < n; ji += gridDim.x) {
     const MgJob& J = jobs[ji];
@@ -273,37 +225,6 @@ __global__ void k_mg_cinv(const MgJob* jobs, int n, Tables T) {
 }
 
 // ---- host side ---------------------------------------------------------------------------
-static bool limbs_zero(const uint32_t* c, int L) {
-  for (int l = 0; l < L; ++l)
-    if (c[l]) return false;
-  return true;
-}
-
-static int trimmed_degree(const bs_upoly& u) {
-  int d = u.deg;
-  while (d >= 0 && limbs_zero(u.c + (size_t)d * u.limbs, u.limbs)) --d;
-  return d;
-}
-
-// log2 ||u||_2 (Q16, rounded up) over the first d + 1 coefficients
-static int64_t log2_norm2_q16(const bs_upoly& u, int d) {
-  UF s2{0u, 0};
-  for (int i = 0; i <= d; ++i) {
-    bool nz;
-    int bits;
-    const UF m = mag_uf(u.c + (size_t)i * u.limbs, u.limbs, &nz, &bits);
-    if (nz) s2 = uf_add(s2, uf_mul(m, m));
-  }
-  return s2.m ? (uf_log2_q16_up(s2) + 1) / 2 : 0;
-}
-
-static int lc_bits(const bs_upoly& u, int d) {
-  bool nz;
-  int bits = 0;
-  mag_uf(u.c + (size_t)d * u.limbs, u.limbs, &nz, &bits);
-  return bits;
-}
-
 // result = sign(lc) * u (positive leading coefficient), written as L limbs per coefficient
 static void normalised_copy(const bs_upoly& u, int d, std::vector<uint32_t>* out, int* L) {
   *L = u.limbs + 1;  // negating the most negative value needs one more limb
@@ -353,7 +274,7 @@ int mg_plan(bs_ctx* ctx, int n, const int* kind, const bs_upoly* a, const bs_upo
     const bs_upoly* pa = a + j;
     const bs_upoly* pb = b ? b + j : nullptr;
     auto bad = [](const bs_upoly* u) {
-      return !u || u->deg < -1 || u->limbs < 1 || u->limbs > kMaxLimbs || (u->deg >= 0 && !u->c);
+      return !u || u->deg < -1 || u->limbs < 1 || u->limbs > kMaxUniLimbs || (u->deg >= 0 && !u->c);
     };
     if (bad(pa) || (kd == kMgGcd && bad(pb))) return ctx_fail(ctx, BS_ERR_ARG, "bad polynomial");
     int da = trimmed_degree(*pa);
@@ -415,6 +336,7 @@ int mg_plan(bs_ctx* ctx, int n, const int* kind, const bs_upoly* a, const bs_upo
     B.smem = std::max(B.smem, words * sizeof(uint32_t));
     maxdeg = std::max(maxdeg, std::max(da, db));
     in_words += (size_t)(da + 1) * A.limbs + (kd == kMgGcd ? (size_t)(db + 1) * Bp->limbs : 0);
+    B.in_limbs = std::max(B.in_limbs, std::max(A.limbs, kd == kMgGcd ? Bp->limbs : 1));
     B.items += kt;
   }
   if (B.smem > (size_t)ctx->smem_optin - 64)
@@ -578,7 +500,7 @@ int mg_launch(bs_ctx* ctx, MgBatch& B, const bs_upoly* a, const bs_upoly* b, cha
     return 0;
   };
   if (crt(wl1)) return ctx_fail(ctx, BS_ERR_RANGE, "too many primes for the reconstruction stage");
-  const int K = (std::max(B.lmax - 1, kMaxLimbs) + 31) / 32;  // <= 8: out_limbs <= 256
+  const int K = (std::max(B.lmax - 1, B.in_limbs) + 31) / 32;  // <= 8: 256 limbs at most
   k_mg_content<<<(m + 3) / 4, 128, 0, s>>>(dj, m, K);
   k_mg_cinv<<<gblocks, 128, 0, s>>>(dj, m, Tv);
   k_mg_gather<<<gblocks, 256, 0, s>>>(dj, m, Tv, 1);
@@ -587,24 +509,6 @@ int mg_launch(bs_ctx* ctx, MgBatch& B, const bs_upoly* a, const bs_upoly* b, cha
   if (rc) return rc;
   return ctx_cuda(ctx, cudaMemcpyAsync(hd, base + B.dn_start, B.dn_bytes, cudaMemcpyDeviceToHost, s),
                   "download");
-}
-
-// write `deg + 1` coefficients of src_limbs each into out (capacity checked)
-static int put_result(bs_ctx* ctx, const uint32_t* src, int src_limbs, int deg, bs_upoly* out) {
-  if (deg > out->deg) return ctx_fail(ctx, BS_ERR_CAPACITY, "output degree capacity too small");
-  for (int i = 0; i <= deg; ++i) {
-    const uint32_t* s = src + (size_t)i * src_limbs;
-    uint32_t* d = out->c + (size_t)i * out->limbs;
-    const uint32_t ext = (s[src_limbs - 1] >> 31) ? 0xffffffffu : 0u;
-    for (int l = 0; l < out->limbs; ++l) d[l] = l < src_limbs ? s[l] : ext;
-    const uint32_t kept = (d[out->limbs - 1] >> 31) ? 0xffffffffu : 0u;
-    for (int l = out->limbs; l < src_limbs; ++l)
-      if (s[l] != kept) return ctx_fail(ctx, BS_ERR_CAPACITY, "output limb capacity too small");
-  }
-  for (int i = deg + 1; i <= out->deg; ++i)
-    std::memset(out->c + (size_t)i * out->limbs, 0, sizeof(uint32_t) * out->limbs);
-  out->deg = deg;
-  return 0;
 }
 
 int mg_finish(bs_ctx* ctx, const MgBatch& B, const char* hd, bs_upoly* out, int* job_status) {

@@ -22,6 +22,7 @@ namespace bs {
 constexpr int kLogNMax = 14;             // transform sizes up to 2^14 (p = 1 mod 2^14)
 constexpr int kNMax = 1 << kLogNMax;
 constexpr int kMaxLimbs = 64;            // input coefficients up to 2048 bits
+constexpr int kMaxUniLimbs = 256;        // univariate inputs of the gcd pipelines: 8192 bits
 constexpr int kUniMaxLen = 129;          // univariate stage: degrees up to 128
 constexpr int kWsMaxK = 256;             // weighted-sum reconstruction up to 256 primes
 

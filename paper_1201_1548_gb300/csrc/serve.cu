@@ -379,7 +379,7 @@ extern "C" int bs_serve_stop(bs_ctx* ctx) {
 }
 
 static int copy_upoly(const bs_upoly* u, bs_upoly* dst, std::vector<uint32_t>* store) {
-  if (!u || u->deg < -1 || u->limbs < 1 || u->limbs > kMaxLimbs || (u->deg >= 0 && !u->c)) return 1;
+  if (!u || u->deg < -1 || u->limbs < 1 || u->limbs > kMaxUniLimbs || (u->deg >= 0 && !u->c)) return 1;
   store->assign(u->c, u->c + (size_t)(u->deg + 1) * u->limbs);
   *dst = bs_upoly{u->deg, u->limbs, store->data()};
   return 0;
