@@ -1,0 +1,142 @@
+"""Pins for oracle.subresultant: a hand-expanded determinant, the gcd-degree criterion
+quoted in Sec. 3.3, the subresultant polynomial as a multiple of the gcd, specialisation
+to points and primes, and the fiber count N against direct counting on split curves."""
+
+import random
+
+import numpy as np
+
+from oracle import gcd as G
+from oracle import poly as P
+from oracle import resultant as R
+from oracle import subresultant as S
+from oracle.numtheory import prime_table
+from workloads import dense_curve
+
+
+def _rand(rng, d, lo=-20, hi=20):
+    a = [rng.randrange(lo, hi + 1) for _ in range(d + 1)]
+    a[-1] = a[-1] or 1
+    return a
+
+
+def test_hand_expanded_examples():
+    # a = y^3, b = y^2 - 1: Res = a(1) a(-1) = -1; sr_1 = det [[1,0,0],[1,0,-1],[0,1,0]] = 1
+    assert S.psc_univariate([0, 0, 0, 1], [-1, 0, 1]) == [-1, 1]
+    # a = (y + 1)(y + 2), b = y + 1: a common root, Res = 0
+    assert S.psc_univariate([2, 3, 1], [1, 1]) == [0]
+    # a = y^2 + p y + q, b = y^2 + r y + s (m = n = 2): sr_1 = det [[1, p], [1, r]] = r - p
+    assert S.psc_univariate([5, 3, 1], [7, -4, 1])[1] == -4 - 3
+    # m = 3, n = 2, i = 1: the 3 x 3 determinant [[a3,a2,a1],[b2,b1,b0],[0,b2,b1]]
+    a, b = [4, -1, 2, 3], [5, 7, -2]
+    a3, a2, a1 = 3, 2, -1
+    b2, b1, b0 = -2, 7, 5
+    want = a3 * (b1 * b1 - b0 * b2) - a2 * (b2 * b1 - 0) + a1 * (b2 * b2 - 0)
+    assert S.psc_univariate(a, b)[1] == want
+
+
+def test_sr0_is_the_resultant():
+    rng = random.Random(11)
+    for _ in range(20):
+        a = _rand(rng, rng.randrange(1, 7))
+        b = _rand(rng, rng.randrange(1, 7))
+        assert S.psc_univariate(a, b)[0] == R.res_univariate(a, b)
+
+
+def test_gcd_degree_criterion():
+    # deg gcd(a, b) = k  <=>  sr_0 = ... = sr_(k-1) = 0 and sr_k != 0 (over Q, Sec. 3.3)
+    rng = random.Random(12)
+    seen = set()
+    for t in range(60):
+        k = t % 4
+        c = _rand(rng, k) if k else [1]
+        u = _rand(rng, rng.randrange(1, 5))
+        v = _rand(rng, rng.randrange(1, 5))
+        a, b = P.mul(c, u), P.mul(c, v)
+        if P.deg(G.gcd_q(a, b)) != k:
+            continue                          # u and v happened to share a factor
+        sr = S.psc_univariate(a, b)
+        q = min(P.deg(a), P.deg(b))
+        assert all(x == 0 for x in sr[:k]), t
+        if k < q:
+            assert sr[k] != 0, t
+        seen.add(k)
+    assert seen == {0, 1, 2, 3}
+
+
+def test_subresultant_polynomial_is_a_multiple_of_the_gcd():
+    rng = random.Random(13)
+    for t in range(24):
+        k = 1 + t % 3
+        c = _rand(rng, k)
+        u = _rand(rng, rng.randrange(1, 4))
+        v = _rand(rng, rng.randrange(1, 4))
+        a, b = P.mul(c, u), P.mul(c, v)
+        g = G.gcd_z(a, b)
+        if P.deg(g) != k or k >= min(P.deg(a), P.deg(b)):
+            continue
+        for i in range(k):
+            assert S.subresultant_poly(a, b, i) == [], (t, i)
+        sk = S.subresultant_poly(a, b, k)
+        assert P.deg(sk) == k and sk[-1] == S.psc_univariate(a, b)[k]
+        assert P.primitive_part(sk) == P.primitive_part(g)
+
+
+def test_specialisation_to_primes():
+    rng = random.Random(14)
+    p = prime_table(1)[0]
+    for _ in range(12):
+        a = _rand(rng, rng.randrange(1, 7), -10**12, 10**12)
+        b = _rand(rng, rng.randrange(1, 7), -10**12, 10**12)
+        assert S.psc_univariate_modp(a, b, p) == [x % p for x in S.psc_univariate(a, b)]
+
+
+def test_bivariate_routes_and_points_agree():
+    rng = np.random.Generator(np.random.PCG64(15))
+    for t in range(5):
+        f = dense_curve(rng, 2 + t % 3, 8)
+        g = dense_curve(rng, 2 + (t + 1) % 3, 8)
+        zx = S.psc_y(f, g, route="zx")
+        pts = S.psc_y(f, g, route="points")
+        assert zx == pts, t
+        D = R.degree_bound(f, g)
+        for i, s in enumerate(zx):
+            assert P.deg(s) <= D
+            for x0 in (-3, 0, 5):
+                a, b = R.specialise(f, x0), R.specialise(g, x0)
+                assert P.evaluate(s, x0) == S.psc_univariate(a, b)[i]
+
+
+def test_fiber_count_on_split_curves():
+    # f = prod (y - a_k(x)) with linear branches: the x-critical values are where branches
+    # meet, and N counts the distinct branch values there
+    cases = [
+        [[0, 1], [0, -1], [0, 2]],                 # three lines through the origin
+        [[0, 1], [0, -1], [2, 1], [1, 0]],
+        [[1, 1], [3, -1], [0, 2], [4, -2], [-2, 3]],
+    ]
+    rng = random.Random(16)
+    for _ in range(3):
+        cases.append([[rng.randrange(-4, 5), rng.randrange(-3, 4)] for _ in range(4)])
+    for branches in cases:
+        # distinct branches only (f square-free)
+        if len({tuple(b) for b in branches}) < len(branches):
+            continue
+        f = S.split_curve(branches)
+        degs, N = S.fiber_decomposition(f)
+        assert N == S.split_curve_fiber_count(branches), branches
+        assert sum(degs) == P.deg(G.squarefree_part(R.res_y(f, S.d_dy(f))))
+        p = prime_table(3)[2]
+        _, lb = S.fiber_lower_bound_modp(f, p)
+        assert lb == N                             # a generic prime is not unlucky here
+
+
+def test_fiber_lower_bound_with_an_unlucky_prime():
+    # three lines through the origin and the parallel lines y = 7, y = 0: modulo 7 the
+    # last two coincide, every fiber mod 7 has fewer distinct roots and the bound drops
+    branches = [[0, 1], [0, -1], [0, 2], [7, 0], [0, 0]]
+    f = S.split_curve(branches)
+    _, N = S.fiber_decomposition(f)
+    assert N == S.split_curve_fiber_count(branches) == 14
+    _, lb7 = S.fiber_lower_bound_modp(f, 7)
+    assert lb7 < N
