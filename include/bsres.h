@@ -285,6 +285,29 @@ int bs_squarefree_factorization(bs_ctx *ctx, const bs_upoly *r, int cap_factors,
 int bs_squarefree_factorization_batch(bs_ctx *ctx, int n, const bs_upoly *r, int cap_factors,
                                       int32_t *fdeg, int32_t *nfac, bs_upoly *out);
 
+/* ---------------------------------------------------------------------------------
+ * Principal subresultant coefficients (Sec. 3.3, "(Exact) Computation of N")
+ * ------------------------------------------------------------------------------ */
+
+/* sr_0, ..., sr_(q-1) of f and g with respect to the eliminated variable (var as in
+ * bs_resultant), q = min(m_e, n_e) for the actual degrees m_e, n_e (q = 0 when either
+ * polynomial is zero or constant in that variable).  sr_i is the coefficient of the i-th
+ * power in the i-th subresultant: the determinant of the Sylvester-like matrix with
+ * n_e - i shifted rows of f and m_e - i shifted rows of g whose columns run from the
+ * highest power down to the i-th; sr_0 is the resultant.  Computed exactly, by the modular
+ * route of the resultant (same primes, points, rejection rule and bounds: each sr_i is a
+ * minor of the Sylvester matrix).
+ *
+ * out: caller-owned array of cap_q host polynomials; out[i] receives sr_i in the layout
+ * of bs_resultant (out[i].deg = -1 for the zero polynomial).  *q receives q.  With out ==
+ * NULL or out[0].c == NULL the call is a size query: *q and, for i < min(q, cap_q), upper
+ * bounds in out[i].deg and out[i].limbs.  The call waits for the device.
+ * Errors: BS_ERR_ARG, BS_ERR_RANGE (degree in the eliminated variable above 64, transform
+ * or prime table too small), BS_ERR_CAPACITY (cap_q < q or an output too small),
+ * BS_ERR_UNLUCKY. */
+int bs_psc(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var, int cap_q, int32_t *q,
+           bs_upoly *out);
+
 /* Launch shapes of the batched stages (bs_autotune_batch). */
 typedef struct {
   int32_t eval_warps;          /* rows (one warp each) per evaluation block, 1..8 */

@@ -19,7 +19,7 @@ EXPORTED_SYMBOLS = [
     "bs_gcd_modp", "bs_squarefree_part", "bs_plan", "bs_alu_probe", "bs_profile",
     "bs_stage_times", "bs_resultant_device_noalloc", "bs_gcd_z", "bs_modgcd_batch",
     "bs_autotune_batch", "bs_set_tune", "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
-    "bs_squarefree_factorization", "bs_squarefree_factorization_batch",
+    "bs_squarefree_factorization", "bs_squarefree_factorization_batch", "bs_psc",
 ]
 
 
@@ -132,6 +132,7 @@ def load_library():
     lib.bs_modgcd_batch.argtypes = [P, I, P, P, P, P]
     lib.bs_squarefree_factorization.argtypes = [P, C.POINTER(_Upoly), I, P, P, C.POINTER(_Upoly)]
     lib.bs_squarefree_factorization_batch.argtypes = [P, I, P, I, P, P, P]
+    lib.bs_psc.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, I, C.POINTER(C.c_int32), P]
     lib.bs_serve_start.argtypes = [P, I, I, C.c_size_t]
     lib.bs_serve_stop.argtypes = [P]
     lib.bs_submit.argtypes = [P, C.POINTER(_Job), C.POINTER(C.c_uint64)]
@@ -236,6 +237,32 @@ class Context:
     def resultant(self, f, g, var=1):
         """res(f, g; y) (var=1) or res(f, g; x) (var=0) as a list of Python ints."""
         return self.resultant_batch([(f, g)], var=var, graph=False)[0]
+
+    def psc(self, f, g, var=1):
+        """[sr_0, ..., sr_(q-1)] of f and g with respect to y (var=1) or x (var=0), each a list
+        of Python ints ([] for the zero polynomial)."""
+        af, dxf, dyf, Lf = bipoly_to_limbs(f)
+        ag, dxg, dyg, Lg = bipoly_to_limbs(g)
+        fb, gb = _bip(af, dxf, dyf, Lf), _bip(ag, dxg, dyg, Lg)
+        q = C.c_int32(0)
+        self._check(self.lib.bs_psc(self.h, C.byref(fb), C.byref(gb), int(var), 0, C.byref(q), None))
+        n = q.value
+        if n == 0:
+            return []
+        outs = (_Upoly * n)()
+        for i in range(n):
+            outs[i] = _Upoly(0, 0, None)
+        self._check(self.lib.bs_psc(self.h, C.byref(fb), C.byref(gb), int(var), n, C.byref(q),
+                                    C.cast(outs, C.c_void_p)))
+        bufs = []
+        for i in range(n):
+            buf = np.zeros((max(outs[i].deg, 0) + 1) * outs[i].limbs, dtype=np.uint32)
+            bufs.append(buf)
+            outs[i] = _Upoly(max(outs[i].deg, 0), outs[i].limbs, buf.ctypes.data)
+        self._check(self.lib.bs_psc(self.h, C.byref(fb), C.byref(gb), int(var), n, C.byref(q),
+                                    C.cast(outs, C.c_void_p)))
+        return [limbs_to_ints(bufs[i], outs[i].deg + 1, outs[i].limbs) if outs[i].deg >= 0 else []
+                for i in range(n)]
 
     def resultant_batch(self, pairs, var=1, graph=True):
         n = len(pairs)

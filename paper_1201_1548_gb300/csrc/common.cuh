@@ -96,6 +96,10 @@ struct Job {
   uint32_t* wsY;
   uint32_t* wsS;
   int32_t wsL;
+  // principal subresultant coefficients (psc jobs; 0 otherwise): the univariate stage
+  // writes sr_i of instance t to vals[i * psc_stride + t], i < npsc
+  int32_t npsc;
+  int64_t psc_stride;
 };
 
 // Programmatic dependent launch: a stage kernel launched with programmatic stream
