@@ -308,6 +308,29 @@ int bs_squarefree_factorization_batch(bs_ctx *ctx, int n, const bs_upoly *r, int
 int bs_psc(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var, int cap_q, int32_t *q,
            bs_upoly *out);
 
+/* The psc sequence modulo one prime (Sec. 3.3, "Computation of N^-"): sr_i mod p for the
+ * first table prime p that the rejection rule of the resultant accepts (p divides no
+ * leading coefficient of f and g; *p receives it).  *q as for bs_psc.  With coef == NULL
+ * a size query: *q and *dmax (the degree bound; residues need dmax + 1 words per index).
+ * Otherwise *dmax is the caller's capacity (at least the bound): coef[i * (dmax + 1) + j]
+ * receives coefficient j of sr_i mod p in [0, p), deg[i] its degree (-1 for zero).
+ * Errors as for bs_psc. */
+int bs_psc_modp(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var, int32_t *q,
+                int32_t *dmax, int32_t *deg, uint32_t *coef, uint32_t *p);
+
+/* The number N of distinct points of the curve f = 0 over its critical values with
+ * respect to the eliminated variable (var = 1: over the roots of R = res(f, f_y; y)), and
+ * the square-free decomposition R* = R_1 R_2 ... by fibers (Sec. 3.3): R_i(alpha) = 0
+ * exactly when f(alpha, y) has n_y - i distinct roots, N = sum_i (n_y - i) deg R_i.
+ * mode 0: exact (psc's in Z[x], gcds in Z[x]); mode 1: the lower bound N^- from the same
+ * chain over Z_p for one prime (*p receives it; 0 in mode 0).  f must have a constant
+ * leading coefficient in the eliminated variable (no vertical asymptote) and at most 63
+ * limbs per coefficient.  degs[i - 1] = deg R_i for i = 1..*s (cap entries available).
+ * Errors: BS_ERR_ARG (non-constant leading coefficient, bad arguments), BS_ERR_ZERO (f = 0,
+ * or R = 0: f is not square-free), BS_ERR_CAPACITY (cap < s), BS_ERR_RANGE, BS_ERR_UNLUCKY. */
+int bs_fiber_count(bs_ctx *ctx, const bs_bipoly *f, int var, int mode, int cap, int32_t *degs,
+                   int32_t *s, int64_t *N, uint32_t *p);
+
 /* Launch shapes of the batched stages (bs_autotune_batch). */
 typedef struct {
   int32_t eval_warps;          /* rows (one warp each) per evaluation block, 1..8 */

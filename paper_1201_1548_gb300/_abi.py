@@ -20,6 +20,7 @@ EXPORTED_SYMBOLS = [
     "bs_stage_times", "bs_resultant_device_noalloc", "bs_gcd_z", "bs_modgcd_batch",
     "bs_autotune_batch", "bs_set_tune", "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
     "bs_squarefree_factorization", "bs_squarefree_factorization_batch", "bs_psc",
+    "bs_psc_modp", "bs_fiber_count",
 ]
 
 
@@ -133,6 +134,10 @@ def load_library():
     lib.bs_squarefree_factorization.argtypes = [P, C.POINTER(_Upoly), I, P, P, C.POINTER(_Upoly)]
     lib.bs_squarefree_factorization_batch.argtypes = [P, I, P, I, P, P, P]
     lib.bs_psc.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, I, C.POINTER(C.c_int32), P]
+    lib.bs_psc_modp.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, C.POINTER(C.c_int32),
+                                C.POINTER(C.c_int32), P, P, C.POINTER(C.c_uint32)]
+    lib.bs_fiber_count.argtypes = [P, C.POINTER(_Bipoly), I, I, I, P, C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_uint32)]
     lib.bs_serve_start.argtypes = [P, I, I, C.c_size_t]
     lib.bs_serve_stop.argtypes = [P]
     lib.bs_submit.argtypes = [P, C.POINTER(_Job), C.POINTER(C.c_uint64)]
@@ -263,6 +268,36 @@ class Context:
                                     C.cast(outs, C.c_void_p)))
         return [limbs_to_ints(bufs[i], outs[i].deg + 1, outs[i].limbs) if outs[i].deg >= 0 else []
                 for i in range(n)]
+
+    def psc_modp(self, f, g, var=1):
+        """(p, [sr_0 mod p, ...]) for the first accepted table prime p (ascending residues)."""
+        af, dxf, dyf, Lf = bipoly_to_limbs(f)
+        ag, dxg, dyg, Lg = bipoly_to_limbs(g)
+        fb, gb = _bip(af, dxf, dyf, Lf), _bip(ag, dxg, dyg, Lg)
+        q, dmax, p = C.c_int32(0), C.c_int32(0), C.c_uint32(0)
+        self._check(self.lib.bs_psc_modp(self.h, C.byref(fb), C.byref(gb), int(var), C.byref(q),
+                                         C.byref(dmax), None, None, C.byref(p)))
+        n = q.value
+        if n == 0:
+            return 0, []
+        deg = np.zeros(n, dtype=np.int32)
+        coef = np.zeros(n * (dmax.value + 1), dtype=np.uint32)
+        self._check(self.lib.bs_psc_modp(self.h, C.byref(fb), C.byref(gb), int(var), C.byref(q),
+                                         C.byref(dmax), deg.ctypes.data, coef.ctypes.data, C.byref(p)))
+        w = dmax.value + 1
+        return int(p.value), [[int(x) for x in coef[i * w: i * w + int(deg[i]) + 1]] for i in range(n)]
+
+    def fiber_count(self, f, var=1, mode=0):
+        """(degs, N, p): deg R_1, deg R_2, ... of the decomposition of R* by fibers, the point
+        count N (mode 0, exact) or its lower bound N^- for one prime p (mode 1)."""
+        af, dxf, dyf, Lf = bipoly_to_limbs(f)
+        fb = _bip(af, dxf, dyf, Lf)
+        cap = max(dxf, dyf) + 2
+        degs = np.zeros(cap, dtype=np.int32)
+        s, N, p = C.c_int32(0), C.c_int64(0), C.c_uint32(0)
+        self._check(self.lib.bs_fiber_count(self.h, C.byref(fb), int(var), int(mode), cap,
+                                            degs.ctypes.data, C.byref(s), C.byref(N), C.byref(p)))
+        return [int(x) for x in degs[: s.value]], int(N.value), int(p.value)
 
     def resultant_batch(self, pairs, var=1, graph=True):
         n = len(pairs)

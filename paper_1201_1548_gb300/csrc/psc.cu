@@ -74,6 +74,7 @@ static void launch_psc(int cls, int grid, int threads, cudaStream_t s, const Job
 // ---- host side ---------------------------------------------------------------------------
 struct PscPlan {
   Plan P;
+  bool modp = false;  // one good prime, residues only (no reconstruction)
   int q = 0, rows = 0;
   size_t o_jobs = 0, o_ev_off = 0, o_psc_off = 0, o_ids = 0, o_intt_off = 0, o_crt_off = 0;
   size_t o_status = 0, o_pstat = 0, o_in = 0, up_bytes = 0;
@@ -88,12 +89,17 @@ static int check_grid(bs_ctx* ctx, const bs_bipoly* p) {
   return 0;
 }
 
-static int psc_plan(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, PscPlan* pp) {
+static int psc_plan(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, bool modp, PscPlan* pp) {
   PscPlan& S = *pp;
+  S.modp = modp;
   const HostPrimes& H = host_primes();
   const Grid gf{f->c, f->deg_x, f->deg_y, f->limbs}, gg{g->c, g->deg_x, g->deg_y, g->limbs};
   S.P = plan_host(gf, gg, var, H.lg_prefix.data(), (int)H.p.size(), H.p.data());
   if (S.P.status) return ctx_fail(ctx, S.P.status, "planning failed");
+  if (modp && !S.P.trivial) {  // the first good prime only; the spares stay
+    S.P.k_total = S.P.k_total - S.P.k_need + 1;
+    S.P.k_need = 1;
+  }
   S.q = S.P.trivial ? 0 : std::min(S.P.me, S.P.ne);
   if (S.q <= 0) {
     S.q = 0;
@@ -123,12 +129,19 @@ static int psc_plan(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var
   cmp.used = S.up_bytes;
   S.o_ev = cmp.take(sizeof(uint32_t) * (size_t)P.k_total * S.rows * P.N);
   S.o_vals = cmp.take(sizeof(uint32_t) * (size_t)q * P.k_total * P.N);
-  S.o_rmod = cmp.take(sizeof(uint32_t) * (size_t)q * P.k_need * (P.D + 1));
-  S.o_sel = cmp.take(sizeof(int32_t) * (size_t)q * P.k_need);
+  if (!modp) {
+    S.o_rmod = cmp.take(sizeof(uint32_t) * (size_t)q * P.k_need * (P.D + 1));
+    S.o_sel = cmp.take(sizeof(int32_t) * (size_t)q * P.k_need);
+  }
   Layout dn;
   dn.used = cmp.used;
   S.dn_start = dn.take(0);
-  S.o_out = dn.take(sizeof(uint32_t) * (size_t)q * (P.D + 1) * P.out_limbs);
+  if (modp) {  // the residues and the selected prime are the result
+    S.o_rmod = dn.take(sizeof(uint32_t) * (size_t)q * (P.D + 1));
+    S.o_sel = dn.take(sizeof(int32_t) * (size_t)q);
+  } else {
+    S.o_out = dn.take(sizeof(uint32_t) * (size_t)q * (P.D + 1) * P.out_limbs);
+  }
   S.o_status_dn = dn.take(sizeof(int32_t) * 4);
   S.total = dn.used;
   S.dn_bytes = S.total - S.dn_start;
@@ -174,7 +187,7 @@ static int psc_launch(bs_ctx* ctx, const PscPlan& S, const bs_bipoly* f, const b
     J.rmod = (uint32_t*)(base + S.o_rmod) + (size_t)i * P.k_need * (P.D + 1);
     J.sel = (int32_t*)(base + S.o_sel) + (size_t)i * P.k_need;
     J.pstat = (int32_t*)(base + S.o_pstat);
-    J.out = (uint32_t*)(base + S.o_out) + (size_t)i * (P.D + 1) * P.out_limbs;
+    J.out = S.modp ? nullptr : (uint32_t*)(base + S.o_out) + (size_t)i * (P.D + 1) * P.out_limbs;
     J.cap_deg = P.D;
     J.cap_limbs = P.out_limbs;
     J.status = status;
@@ -220,6 +233,7 @@ static int psc_launch(bs_ctx* ctx, const PscPlan& S, const bs_bipoly* f, const b
     launch_intt((int)std::min<int64_t>(ioff[q], (int64_t)sms * 8), 2 * sizeof(uint32_t) * (size_t)P.N, s, dj,
                 wl_i, Tv);
   const WorkList wl_c{(const int32_t*)(base + S.o_ids), (const int64_t*)(base + S.o_crt_off), q};
+  if (!S.modp) {  // the modular form stops at the residues
   const int crt_grid = (int)std::min<int64_t>(coff[q], (int64_t)sms * 4);
   const int kmax = P.k_need, lmax = P.out_limbs + 1;
   const size_t wsm = crt_warp_smem(kmax, lmax);
@@ -232,6 +246,7 @@ static int psc_launch(bs_ctx* ctx, const PscPlan& S, const bs_bipoly* f, const b
       return ctx_fail(ctx, BS_ERR_RANGE, "too many primes for the reconstruction stage");
     const int w = (int)std::min<size_t>(kCrtWarps, ((size_t)ctx->smem_optin - 64 - fixed) / per);
     launch_crt(crt_grid, w * 32, fixed + per * w, s, dj, wl_c, Tv, kmax, lmax, 0);
+  }
   }
   rc = ctx_cuda(ctx, cudaGetLastError(), "launch");
   if (rc) return rc;
@@ -270,7 +285,7 @@ static int run_psc(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var,
   if (rc) return rc;
   cudaSetDevice(ctx->device);
   PscPlan S;
-  rc = psc_plan(ctx, f, g, var, &S);
+  rc = psc_plan(ctx, f, g, var, false, &S);
   if (rc) return rc;
   *q_out = S.q;
   if (S.q == 0) return BS_OK;
@@ -297,9 +312,61 @@ static int run_psc(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var,
   return psc_finish(ctx, S, (const char*)ctx->h_down, out);
 }
 
+static int run_psc_modp(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, int32_t* q_out,
+                        int32_t* dmax, int32_t* deg, uint32_t* coef, uint32_t* p_out) {
+  if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
+  int rc = check_grid(ctx, f);
+  if (!rc) rc = check_grid(ctx, g);
+  if (rc) return rc;
+  cudaSetDevice(ctx->device);
+  PscPlan S;
+  rc = psc_plan(ctx, f, g, var, true, &S);
+  if (rc) return rc;
+  *q_out = S.q;
+  if (S.q == 0) return BS_OK;
+  if (!coef) {  // size query
+    *dmax = S.P.D;
+    return BS_OK;
+  }
+  if (!deg || *dmax < S.P.D) return ctx_fail(ctx, BS_ERR_CAPACITY, "residue capacity too small");
+  const int cap = *dmax + 1;
+  rc = ctx->tabs->ensure(S.P.k_total, S.P.logN, ctx->stream);
+  if (rc) return ctx_fail(ctx, rc, "table setup failed");
+  rc = ensure_workspace(ctx, S.total);
+  if (rc) return rc;
+  rc = ensure_pinned(ctx, S.up_bytes, S.dn_bytes);
+  if (rc) return rc;
+  rc = psc_launch(ctx, S, f, g, var, (char*)ctx->ws, (char*)ctx->h_up, (char*)ctx->h_down);
+  if (rc) return rc;
+  rc = ctx_cuda(ctx, cudaStreamSynchronize(ctx->stream), "stream");
+  if (rc) return rc;
+  const char* hd = (const char*)ctx->h_down;
+  const int32_t* st = (const int32_t*)(hd + (S.o_status_dn - S.dn_start));
+  if (st[0]) return ctx_fail(ctx, st[0], "device stage reported a failure");
+  const int32_t* sel = (const int32_t*)(hd + (S.o_sel - S.dn_start));
+  *p_out = host_primes().p[sel[0]];
+  const int D = S.P.D;
+  for (int i = 0; i < S.q; ++i) {
+    const uint32_t* src = (const uint32_t*)(hd + (S.o_rmod - S.dn_start)) + (size_t)i * (D + 1);
+    int d = D;
+    while (d >= 0 && src[d] == 0u) --d;
+    deg[i] = d;
+    std::memcpy(coef + (size_t)i * cap, src, sizeof(uint32_t) * (D + 1));
+    std::memset(coef + (size_t)i * cap + D + 1, 0, sizeof(uint32_t) * (cap - D - 1));
+  }
+  return BS_OK;
+}
+
 }  // namespace bs
 
 using namespace bs;
+
+extern "C" int bs_psc_modp(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, int32_t* q,
+                           int32_t* dmax, int32_t* deg, uint32_t* coef, uint32_t* p) {
+  if (!ctx) return BS_ERR_ARG;
+  if (!f || !g || !q || !dmax || !p || (var != 0 && var != 1)) return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
+  return run_psc_modp(ctx, f, g, var, q, dmax, deg, coef, p);
+}
 
 extern "C" int bs_psc(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, int cap_q, int32_t* q,
                       bs_upoly* out) {

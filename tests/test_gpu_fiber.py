@@ -1,0 +1,90 @@
+"""The fiber counts of Sec. 3.3 on the device against the oracle: the psc sequence modulo
+one prime, the exact point count N with its decomposition of R*, and the lower bound N^-,
+on split curves (whose fibers are counted directly) and dense curves."""
+
+import numpy as np
+import pytest
+
+import paper_1201_1548_gb300 as bs
+from oracle import resultant as R
+from oracle import subresultant as S
+from workloads import dense_curve
+
+pytestmark = pytest.mark.gpu
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def test_psc_modp_matches_oracle(ctx):
+    rng = _rng(61)
+    for t in range(8):
+        f = dense_curve(rng, int(rng.integers(2, 7)), int(rng.integers(4, 60)))
+        g = dense_curve(rng, int(rng.integers(2, 7)), int(rng.integers(4, 60)))
+        p, res = ctx.psc_modp(f, g)
+        assert p == bs.bs_prime_table(1)[0]           # no leading coefficient vanishes mod p
+        assert res == S.psc_y_modp(f, g, p), t
+
+
+def test_psc_modp_skips_a_rejected_prime(ctx):
+    p0 = bs.bs_prime_table(1)[0]
+    rng = _rng(62)
+    f = dense_curve(rng, 4, 12)
+    f[-1] = [c * p0 for c in f[-1]]                    # lc_y f = 0 mod the first prime
+    g = S.d_dy(f)
+    p, res = ctx.psc_modp(f, g)
+    assert p != p0
+    assert res == S.psc_y_modp(f, g, p)
+
+
+SPLIT = [
+    [[0, 1], [0, -1], [0, 2]],                          # three lines through the origin
+    [[0, 1], [0, -1], [2, 1], [1, 0]],
+    [[1, 1], [3, -1], [0, 2], [4, -2], [-2, 3]],
+    [[0, 1], [0, -1], [0, 2], [0, 3], [5, 0]],          # four concurrent lines
+]
+
+
+@pytest.mark.parametrize("branches", SPLIT)
+def test_fiber_count_split_curves(ctx, branches):
+    f = S.split_curve(branches)
+    want_degs, want_N = S.fiber_decomposition(f)
+    assert want_N == S.split_curve_fiber_count(branches)
+    degs, N, p = ctx.fiber_count(f)
+    assert (degs, N, p) == (want_degs, want_N, 0)
+    degs1, lb, p1 = ctx.fiber_count(f, mode=1)
+    assert p1 > 0
+    assert (degs1, lb) == S.fiber_lower_bound_modp(f, p1)
+    assert lb <= N
+
+
+def test_fiber_count_dense_curves(ctx):
+    rng = _rng(63)
+    for t in range(5):
+        f = dense_curve(rng, 3 + t % 3, 12)           # constant leading coefficient in y
+        want = S.fiber_decomposition(f)
+        degs, N, _ = ctx.fiber_count(f)
+        assert (degs, N) == want, t
+        degs1, lb, p = ctx.fiber_count(f, mode=1)
+        assert (degs1, lb) == S.fiber_lower_bound_modp(f, p), t
+
+
+def test_fiber_count_in_x(ctx):
+    f = S.split_curve([[0, 1], [0, -1], [3, 2]])
+    ft = R.transpose(f)                                 # the same curve with x and y exchanged
+    assert ctx.fiber_count(ft, var=0) == ctx.fiber_count(f, var=1)
+
+
+def test_fiber_count_rejects_bad_curves(ctx):
+    # a vertical asymptote: the leading coefficient in y is x
+    with pytest.raises(bs.BsError) as e:
+        ctx.fiber_count([[1, 0], [0, 0], [0, 1]])
+    assert e.value.code == bs.BS_ERR_ARG
+    # a square factor: R = res(f, f_y) = 0
+    f = S.split_curve([[0, 1], [0, 1], [2, 0]])
+    with pytest.raises(bs.BsError) as e:
+        ctx.fiber_count(f)
+    assert e.value.code == bs.BS_ERR_ZERO
+    # linear in y: no critical values
+    assert ctx.fiber_count([[1, 2, 3], [1, 0, 0]]) == ([], 0, 0)
