@@ -298,6 +298,103 @@ def _bench_batched(bs, ctx, reps=3):
             "modp_univariate_resultants_per_s": st.instances / tb}
 
 
+def _bench_projection(bs, ctx, f, g, R, reps=3):
+    """The projection steps after the resultant on the degree-32 curve (host buffers, one C
+    call each, best of `reps` after a warm-up): the square-free part and Yun's
+    factorisation of R = res(f, f_y), the 31 principal subresultant coefficients of f and
+    f_y (exact and modulo one prime), and the fiber counts N (exact) and N^- (one prime)."""
+    import ctypes as C
+    import numpy as np
+    lib = ctx.lib
+
+    def best(fn):
+        fn()
+        out = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            out.append(time.perf_counter() - t0)
+        return min(out) * 1e3
+
+    Ra, RL = bs.ints_to_limbs(R)
+    Ru = bs._abi._Upoly(len(R) - 1, RL, Ra.ctypes.data)
+    q = bs._abi._Upoly(0, 0, None)
+    lib.bs_squarefree_part(ctx.h, C.byref(Ru), C.byref(q))
+    sq_buf = np.zeros((q.deg + 1) * q.limbs, dtype=np.uint32)
+    sq_cap = (q.deg, q.limbs)
+
+    def sqf():
+        o = bs._abi._Upoly(sq_cap[0], sq_cap[1], sq_buf.ctypes.data)
+        if lib.bs_squarefree_part(ctx.h, C.byref(Ru), C.byref(o)):
+            raise SystemExit("bs_squarefree_part failed")
+
+    nf = np.zeros(1, dtype=np.int32)
+    yq = bs._abi._Upoly(0, 0, None)
+    lib.bs_squarefree_factorization(ctx.h, C.byref(Ru), 0, None, nf.ctypes.data, C.byref(yq))
+    y_buf = np.zeros((yq.deg + 1) * yq.limbs, dtype=np.uint32)
+    fdeg = np.zeros(max(int(nf[0]), 1), dtype=np.int32)
+    y_cap = (yq.deg, yq.limbs, int(nf[0]))
+
+    def yun():
+        o = bs._abi._Upoly(y_cap[0], y_cap[1], y_buf.ctypes.data)
+        if lib.bs_squarefree_factorization(ctx.h, C.byref(Ru), y_cap[2], fdeg.ctypes.data,
+                                           nf.ctypes.data, C.byref(o)):
+            raise SystemExit("bs_squarefree_factorization failed")
+
+    af, dxf, dyf, Lf = bs.bipoly_to_limbs(f)
+    ag, dxg, dyg, Lg = bs.bipoly_to_limbs(g)
+    fb, gb = bs._abi._bip(af, dxf, dyf, Lf), bs._abi._bip(ag, dxg, dyg, Lg)
+    nq = C.c_int32(0)
+    lib.bs_psc(ctx.h, C.byref(fb), C.byref(gb), 1, 0, C.byref(nq), None)
+    n = nq.value
+    outs = (bs._abi._Upoly * n)()
+    for i in range(n):
+        outs[i] = bs._abi._Upoly(0, 0, None)
+    lib.bs_psc(ctx.h, C.byref(fb), C.byref(gb), 1, n, C.byref(nq), C.cast(outs, C.c_void_p))
+    caps = [(outs[i].deg, outs[i].limbs) for i in range(n)]
+    pbufs = [np.zeros((d + 1) * L, dtype=np.uint32) for d, L in caps]
+
+    def psc():
+        for i in range(n):
+            outs[i] = bs._abi._Upoly(caps[i][0], caps[i][1], pbufs[i].ctypes.data)
+        if lib.bs_psc(ctx.h, C.byref(fb), C.byref(gb), 1, n, C.byref(nq), C.cast(outs, C.c_void_p)):
+            raise SystemExit("bs_psc failed")
+
+    dmax, pp = C.c_int32(0), C.c_uint32(0)
+    lib.bs_psc_modp(ctx.h, C.byref(fb), C.byref(gb), 1, C.byref(nq), C.byref(dmax), None, None,
+                    C.byref(pp))
+    mdeg = np.zeros(n, dtype=np.int32)
+    mcoef = np.zeros(n * (dmax.value + 1), dtype=np.uint32)
+
+    def psc_modp():
+        if lib.bs_psc_modp(ctx.h, C.byref(fb), C.byref(gb), 1, C.byref(nq), C.byref(dmax),
+                           mdeg.ctypes.data, mcoef.ctypes.data, C.byref(pp)):
+            raise SystemExit("bs_psc_modp failed")
+
+    degs = np.zeros(64, dtype=np.int32)
+    s_, N_, p_ = C.c_int32(0), C.c_int64(0), C.c_uint32(0)
+    counts = {}
+
+    def fiber(mode):
+        def run():
+            if lib.bs_fiber_count(ctx.h, C.byref(fb), 1, mode, 64, degs.ctypes.data, C.byref(s_),
+                                  C.byref(N_), C.byref(p_)):
+                raise SystemExit("bs_fiber_count failed")
+            counts[mode] = (int(N_.value), [int(x) for x in degs[: s_.value]])
+        return run
+
+    res = {"workload": "R = res(f, f_y), f dense total degree 32, signed 32-bit, seed 1 "
+                       "(deg R = %d, host buffers)" % (len(R) - 1),
+           "ms_squarefree_part": best(sqf), "ms_yun": best(yun), "ms_psc_exact": best(psc),
+           "ms_psc_one_prime": best(psc_modp), "ms_fiber_count_exact": best(fiber(0)),
+           "ms_fiber_lower_bound": best(fiber(1))}
+    res["yun_factor_degrees"] = [int(x) for x in fdeg[: int(nf[0])]]
+    res["psc_count"] = n
+    res["fiber_N"], res["fiber_degs"] = counts[0]
+    res["fiber_N_lower"] = counts[1][0]
+    return res
+
+
 def _bench_served(bs, jobs=96, seed=1):
     """cfg5: Poisson arrivals of resultant and gcd jobs (total degree 6-64, 16-256-bit
     coefficients) into the serving loop.  First a closed-loop pass (everything submitted
@@ -519,10 +616,11 @@ def run_ours(args):
     h2d = (af.nbytes + ag.nbytes)
     d2h = (deg + 1) * plan["out_limbs"] * 4
 
-    batched = served = None
+    batched = served = projection = None
     if rank == 0 and not args.no_extras:
         batched = _bench_batched(bs, ctx)
         served = _bench_served(bs)
+        projection = _bench_projection(bs, ctx, f, g, ctx.resultant(f, g))
 
     cpu = None
     if want_cpu:
@@ -546,7 +644,7 @@ def run_ours(args):
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": 6 * args.steps,
                 "cpu_baseline": cpu,
-                "batched": batched, "served": served}
+                "batched": batched, "served": served, "projection": projection}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

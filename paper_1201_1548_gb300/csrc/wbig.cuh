@@ -3,9 +3,9 @@
 //
 // A non-negative integer of up to 32 K limbs is spread over the lanes: lane l, slot s
 // holds limb 32 s + l.  Comparisons, subtraction and shifts resolve carries across lanes
-// with ballots.  The gcd is Stein's binary algorithm; once the running gcd fits in 32
-// bits every further coefficient is reduced modulo it with a Horner pass (lane 0) and the
-// gcd finishes in 32-bit arithmetic.
+// with ballots.  The gcd is Stein's binary algorithm; once the running gcd fits in 64
+// bits every further coefficient is reduced modulo it by the whole warp and the gcd
+// finishes in 64-bit arithmetic.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -164,54 +164,88 @@ __device__ __forceinline__ void wb_load_abs(WBig<K>& a, const uint32_t* c, int L
   }
 }
 
-__device__ __forceinline__ uint32_t gcd32(uint32_t a, uint32_t b) {
+__device__ __forceinline__ uint64_t gcd64(uint64_t a, uint64_t b) {
   while (b) {
-    const uint32_t t = a % b;
+    const uint64_t t = a % b;
     a = b;
     b = t;
   }
   return a;
 }
 
-// |c| mod m for a two's complement coefficient of L limbs (m >= 1)
-__device__ __forceinline__ uint32_t abs_mod32(const uint32_t* c, int L, uint32_t m) {
-  const bool neg = (c[L - 1] >> 31) != 0;
-  uint64_t r = 0;
-  for (int l = L - 1; l >= 0; --l) r = ((r << 32) | c[l]) % m;
-  if (neg) {  // value = raw - 2^(32 L), so |value| = 2^(32 L) - raw
-    uint64_t t = 1 % m;
-    for (int l = 0; l < L; ++l) t = (t << 32) % m;
-    r = (t + m - r) % m;
+__device__ __forceinline__ uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) {
+  return (uint64_t)(((unsigned __int128)a * b) % m);
+}
+
+__device__ __forceinline__ uint64_t addmod64(uint64_t a, uint64_t b, uint64_t m) {
+  const uint64_t s = a + b;  // a, b < m < 2^64: the sum may wrap once
+  return (s < a || s >= m) ? s - m : s;
+}
+
+// Residues used to reduce a warp-wide integer modulo m (2 <= m < 2^64): W = 2^(32 * 32) mod m
+// steps between the slots of one lane, P = 2^(32 * lane) mod m places the lane.
+struct Mod64Pow {
+  uint64_t m = 0, W = 0, P = 0;
+  __device__ void set(uint64_t mod) {
+    m = mod;
+    const uint64_t t32 = ((uint64_t)1 << 32) % m;  // 2^32 mod m
+    uint64_t w = t32;
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i) w = mulmod64(w, w, m);  // (2^32)^32
+    W = w;
+    uint64_t pl = 1 % m, b = t32;
+    for (int e = threadIdx.x & 31; e; e >>= 1) {  // (2^32)^lane
+      if (e & 1) pl = mulmod64(pl, b, m);
+      b = mulmod64(b, b, m);
+    }
+    P = pl;
   }
-  return (uint32_t)r;
+};
+
+// a mod m for a warp-wide non-negative integer (every lane receives the result)
+template <int K>
+__device__ __forceinline__ uint64_t wb_mod64(const WBig<K>& a, const Mod64Pow& mp) {
+  uint64_t acc = 0;
+#pragma unroll
+  for (int s = K - 1; s >= 0; --s) acc = addmod64(mulmod64(acc, mp.W, mp.m), a.v[s] % mp.m, mp.m);
+  acc = mulmod64(acc, mp.P, mp.m);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc = addmod64(acc, __shfl_xor_sync(0xffffffffu, acc, o), mp.m);
+  return acc;
 }
 
 // Running gcd of integers, held by one warp.  g = 0 stands for "no coefficient yet".
+// Once the gcd fits in 64 bits every further coefficient is reduced modulo it by the
+// whole warp (Horner's rule per lane over its limbs, then a shuffle sum of the lanes'
+// shares) and the gcd continues in 64-bit arithmetic; until then Stein's binary
+// algorithm runs on the warp-wide integers.
 template <int K>
 struct ContentAcc {
   WBig<K> g;
-  bool small = false;  // g fits in 32 bits and lives in g32
-  uint32_t g32 = 0;
+  bool small = false;  // g fits in 64 bits and lives in g64
+  uint64_t g64 = 0;
+  Mod64Pow mp;
   bool started = false;
 
-  __device__ __forceinline__ bool is_one() const { return small && g32 == 1u; }
+  __device__ __forceinline__ bool is_one() const { return small && g64 == 1u; }
 
   // fold the n coefficients c[i * L .. i * L + L - 1] into the gcd
   __device__ void fold(const uint32_t* c, int n, int L) {
-    const int lane = threadIdx.x & 31;
     for (int i = 0; i < n; ++i) {
       const uint32_t* ci = c + (int64_t)i * L;
-      if (small) {
-        if (g32 == 1u) return;
-        uint32_t r = 0;
-        if (lane == 0) r = abs_mod32(ci, L, g32);
-        r = __shfl_sync(0xffffffffu, r, 0);
-        g32 = gcd32(g32, r);
-        continue;
-      }
+      if (small && g64 == 1u) return;
       WBig<K> b;
       wb_load_abs<K>(b, ci, L);
       if (wb_is_zero<K>(b)) continue;
+      if (small) {
+        const uint64_t r = wb_mod64<K>(b, mp);
+        const uint64_t ng = gcd64(g64, r);
+        if (ng != g64) {
+          g64 = ng;
+          if (g64 > 1) mp.set(g64);
+        }
+        continue;
+      }
       if (!started) {
         g = b;
         started = true;
@@ -232,9 +266,12 @@ struct ContentAcc {
         }
         wb_shl<K>(g, sh);
       }
-      if (wb_top<K>(g) <= 0) {
+      if (wb_top<K>(g) <= 1) {
         small = true;
-        g32 = __shfl_sync(0xffffffffu, g.v[0], 0);
+        const uint64_t lo = __shfl_sync(0xffffffffu, g.v[0], 0);
+        const uint64_t hi = __shfl_sync(0xffffffffu, g.v[0], 1);
+        g64 = lo | (hi << 32);
+        if (g64 > 1) mp.set(g64);
       }
     }
   }
@@ -243,7 +280,7 @@ struct ContentAcc {
   __device__ void store(uint32_t* out, int Lout) const {
     const int lane = threadIdx.x & 31;
     if (small) {
-      for (int l = lane; l < Lout; l += 32) out[l] = (l == 0) ? g32 : 0u;
+      for (int l = lane; l < Lout; l += 32) out[l] = (l == 0) ? (uint32_t)g64 : (l == 1) ? (uint32_t)(g64 >> 32) : 0u;
       return;
     }
 #pragma unroll

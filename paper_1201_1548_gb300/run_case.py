@@ -6,6 +6,9 @@
     python -m paper_1201_1548_gb300.run_case batch4096 [reps]
         4096 pairs of total degrees 4..24 and 8..64-bit coefficients through
         bs_resultant_batch (one graph launch per repetition).
+    python -m paper_1201_1548_gb300.run_case projection32 [reps]
+        the square-free part, Yun's factorisation and the psc sequence of the degree-32
+        curve's resultant R = res(f, f_y) (deg 992), one call each per repetition.
 
 Each run checks its result against the host entry point once and prints "ok".
 """
@@ -61,7 +64,29 @@ def _batch4096(reps):
             raise SystemExit(f"batched and single results differ at pair {i}")
 
 
-CASES = {"discriminant32": _discriminant32, "batch4096": _batch4096}
+def _projection32(reps):
+    import time
+
+    import paper_1201_1548_gb300 as bs
+    from workloads import cfg2_pair
+
+    f, g = cfg2_pair(1)
+    ctx = bs.Context(0)
+    R = ctx.resultant(f, g)
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        sq = ctx.squarefree_part(R)
+        t1 = time.perf_counter()
+        fac = ctx.squarefree_factorization(R)
+        t2 = time.perf_counter()
+        ps = ctx.psc(f, g)
+        t3 = time.perf_counter()
+        print(f"sqf {1e3 * (t1 - t0):.2f} ms  yun {1e3 * (t2 - t1):.2f} ms  psc {1e3 * (t3 - t2):.2f} ms")
+    if fac[-1] != sq and len(fac) == 1 or ps[0] != R:
+        raise SystemExit("inconsistent projection results")
+
+
+CASES = {"discriminant32": _discriminant32, "batch4096": _batch4096, "projection32": _projection32}
 
 
 def main(argv):

@@ -188,3 +188,19 @@ def test_yun_wide_and_long_certified(ctx):
     assert got == [P.primitive_part(v), P.primitive_part(u)]
     _certify(r, got)
     assert ctx.squarefree_part(r) == P.primitive_part(_product(u, v))
+
+
+def test_contents_across_the_64_bit_boundary(ctx):
+    # the images' contents are lc(R) / lc(r_i) times the content of R: multipliers of 20,
+    # 40, 60 and 100 bits take the 32-bit, 64-bit and multi-limb paths of the warp gcd
+    rng = _rng(50)
+    u = random_univariate(rng, 5, 40)
+    v = random_univariate(rng, 4, 40)
+    base = _product(u, u, v)
+    for bits in (20, 40, 60, 100):
+        C = (1 << bits) - 3 * bits
+        r = [C * x for x in base]
+        assert ctx.squarefree_factorization(r) == G.yun(r), bits
+        assert ctx.squarefree_part(r) == G.squarefree_part(r), bits
+        a, b = [C * x for x in _product(u, v)], [(C + 2) * x for x in _product(u, u)]
+        assert ctx.gcd_z(a, b) == G.gcd_z(a, b), bits
