@@ -249,9 +249,13 @@ int bs_squarefree_part(bs_ctx *ctx, const bs_upoly *r, bs_upoly *out);
 int bs_gcd_z(bs_ctx *ctx, const bs_upoly *a, const bs_upoly *b, bs_upoly *out);
 
 /* n modular gcd jobs in one pass of launches: kind[j] = 0 computes gcd(a[j], b[j]) as
- * bs_gcd_z, kind[j] = 1 the square-free part of a[j] as bs_squarefree_part (b may be
- * NULL when every kind is 1).  If any out[j].c is NULL, every out[j] receives its upper
- * bounds and nothing runs.  Returns the first failing job's status. */
+ * bs_gcd_z, kind[j] = 1 the square-free part of a[j] as bs_squarefree_part, kind[j] = 2
+ * the exact quotient a[j] / b[j] (b[j] must divide a[j] in Z[x]: a remainder modulo a
+ * prime is reported as BS_ERR_ARG, a quotient that is not integral is not detected; the
+ * images a mod p / b mod p for primes not dividing lc(b) are lifted under Mignotte's bound
+ * 2^deg(q) ||a||_2).  b may be NULL when every kind is 1.  If any out[j].c is NULL, every
+ * out[j] receives its upper bounds and nothing runs.  Returns the first failing job's
+ * status. */
 int bs_modgcd_batch(bs_ctx *ctx, int n, const int *kind, const bs_upoly *a, const bs_upoly *b,
                     bs_upoly *out);
 
@@ -330,6 +334,20 @@ int bs_psc_modp(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var, in
  * or R = 0: f is not square-free), BS_ERR_CAPACITY (cap < s), BS_ERR_RANGE, BS_ERR_UNLUCKY. */
 int bs_fiber_count(bs_ctx *ctx, const bs_bipoly *f, int var, int mode, int cap, int32_t *degs,
                    int32_t *s, int64_t *N, uint32_t *p);
+
+/* Content of f with respect to the eliminated variable (var as in bs_resultant): h = the
+ * gcd in Z[x] of f's coefficients f_0, ..., f_n (polynomials in the other variable), with
+ * a positive leading coefficient, and optionally the primitive part f / h as its rows
+ * (Sec. 4: a non-constant content defines vertical lines, which the curve analysis
+ * divides out first).  The gcds (a pairwise tree, batched) and the quotients run on the
+ * device by the modular route.
+ * h: caller-owned output in the layout of bs_squarefree_part.  rows: NULL, or an array of
+ * cap_rows outputs receiving (f / h)_0, ..., (f / h)_n; *nrows = n + 1 (n the degree in the
+ * eliminated variable).  With h->c == NULL, or rows[0].c == NULL when rows are asked for,
+ * a size query: *nrows and upper bounds in h and rows[e].
+ * Errors: BS_ERR_ARG, BS_ERR_ZERO (f = 0), BS_ERR_CAPACITY, BS_ERR_RANGE, BS_ERR_UNLUCKY. */
+int bs_content(bs_ctx *ctx, const bs_bipoly *f, int var, bs_upoly *h, int cap_rows, bs_upoly *rows,
+               int32_t *nrows);
 
 /* Launch shapes of the batched stages (bs_autotune_batch). */
 typedef struct {

@@ -9,6 +9,8 @@
   R = c * prod r_i**i.
 * square-free part R* = pp(R / gcd(R, R')) with a positive leading coefficient
   (Sec. 3.3 uses deg R* as the number of distinct roots of R).
+* content of a bivariate polynomial with respect to one variable: the gcd in Z[x] of its
+  coefficient rows, positive leading coefficient (Sec. 4 divides it out first).
 """
 
 from __future__ import annotations
@@ -135,3 +137,18 @@ def yun(r):
     while out and len(out[-1]) == 1:
         out.pop()
     return out
+
+
+def content_rows(rows):
+    """gcd in Z[x] of the polynomials `rows` (the coefficients of f in the eliminated
+    variable), with a positive leading coefficient; [] if every row is zero."""
+    g = []
+    for r in rows:
+        g = gcd_z(g, r)
+    return g
+
+
+def primitive_rows(rows):
+    """(h, [row / h]): the content and the rows of the primitive part."""
+    h = content_rows(rows)
+    return h, [P.exact_div_z(r, h) for r in rows]

@@ -20,7 +20,7 @@ EXPORTED_SYMBOLS = [
     "bs_stage_times", "bs_resultant_device_noalloc", "bs_gcd_z", "bs_modgcd_batch",
     "bs_autotune_batch", "bs_set_tune", "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
     "bs_squarefree_factorization", "bs_squarefree_factorization_batch", "bs_psc",
-    "bs_psc_modp", "bs_fiber_count",
+    "bs_psc_modp", "bs_fiber_count", "bs_content",
 ]
 
 
@@ -136,6 +136,7 @@ def load_library():
     lib.bs_psc.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, I, C.POINTER(C.c_int32), P]
     lib.bs_psc_modp.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, C.POINTER(C.c_int32),
                                 C.POINTER(C.c_int32), P, P, C.POINTER(C.c_uint32)]
+    lib.bs_content.argtypes = [P, C.POINTER(_Bipoly), I, C.POINTER(_Upoly), I, P, C.POINTER(C.c_int32)]
     lib.bs_fiber_count.argtypes = [P, C.POINTER(_Bipoly), I, I, I, P, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int64), C.POINTER(C.c_uint32)]
     lib.bs_serve_start.argtypes = [P, I, I, C.c_size_t]
@@ -286,6 +287,30 @@ class Context:
                                          C.byref(dmax), deg.ctypes.data, coef.ctypes.data, C.byref(p)))
         w = dmax.value + 1
         return int(p.value), [[int(x) for x in coef[i * w: i * w + int(deg[i]) + 1]] for i in range(n)]
+
+    def content(self, f, var=1):
+        """(h, rows): the content of f with respect to y (var=1) or x (var=0) and the rows of
+        the primitive part f / h, ascending integer lists ([] for zero)."""
+        af, dxf, dyf, Lf = bipoly_to_limbs(f)
+        fb = _bip(af, dxf, dyf, Lf)
+        n = (dyf if var else dxf) + 1
+        h = _Upoly(0, 0, None)
+        rows = (_Upoly * n)()
+        for i in range(n):
+            rows[i] = _Upoly(0, 0, None)
+        nr = C.c_int32(0)
+        self._check(self.lib.bs_content(self.h, C.byref(fb), int(var), C.byref(h), n,
+                                         C.cast(rows, C.c_void_p), C.byref(nr)))
+        hb = np.zeros((h.deg + 1) * h.limbs, dtype=np.uint32)
+        h = _Upoly(h.deg, h.limbs, hb.ctypes.data)
+        bufs = []
+        for i in range(nr.value):
+            bufs.append(np.zeros((rows[i].deg + 1) * rows[i].limbs, dtype=np.uint32))
+            rows[i] = _Upoly(rows[i].deg, rows[i].limbs, bufs[i].ctypes.data)
+        self._check(self.lib.bs_content(self.h, C.byref(fb), int(var), C.byref(h), nr.value,
+                                         C.cast(rows, C.c_void_p), C.byref(nr)))
+        conv = lambda u, b: limbs_to_ints(b, u.deg + 1, u.limbs) if u.deg >= 0 else []
+        return conv(h, hb), [conv(rows[i], bufs[i]) for i in range(nr.value)]
 
     def fiber_count(self, f, var=1, mode=0):
         """(degs, N, p): deg R_1, deg R_2, ... of the decomposition of R* by fibers, the point

@@ -28,7 +28,7 @@
 
 namespace bs {
 
-enum : int32_t { kMgGcd = 0, kMgSqf = 1 };
+enum : int32_t { kMgGcd = 0, kMgSqf = 1, kMgDiv = 2 };
 
 struct MgJob {
   const uint32_t* A;  // [(da + 1) * La] limbs of a
@@ -65,14 +65,14 @@ __global__ void k_mg_images(const MgJob* jobs, WorkList wl, Tables T) {
     const int da = J.da;
     uint32_t* sA = sm;
     uint32_t* sB = sA + da + 1;
-    const int nb = (J.kind == kMgGcd) ? J.db + 1 : da;  // a' has degree < da
+    const int nb = (J.kind != kMgSqf) ? J.db + 1 : da;  // a' has degree < da
     uint32_t* sR = sB + (nb > 0 ? nb : 1);              // square-free part: a kept for the division
     for (int i = threadIdx.x; i <= da; i += blockDim.x) {
       const uint32_t v = reduce_coef(J.A + (int64_t)i * J.La, J.La, pw, mpw, pc);
       sA[i] = v;
       if (J.kind == kMgSqf) sR[i] = v;
     }
-    if (J.kind == kMgGcd)
+    if (J.kind != kMgSqf)
       for (int i = threadIdx.x; i <= J.db; i += blockDim.x)
         sB[i] = reduce_coef(J.B + (int64_t)i * J.Lb, J.Lb, pw, mpw, pc);
     __syncthreads();
@@ -81,7 +81,7 @@ __global__ void k_mg_images(const MgJob* jobs, WorkList wl, Tables T) {
         sB[i] = mmul(sA[i + 1], redc((uint64_t)(uint32_t)(i + 1) * pc.r2, M.p, M.pinv), M);
     __syncthreads();
     const uint32_t lca = sA[da];
-    const int lbd = (J.kind == kMgGcd) ? J.db : da - 1;
+    const int lbd = (J.kind != kMgSqf) ? J.db : da - 1;
     if (threadIdx.x == 0) {
       int lb = lbd;
       while (lb >= 0 && sB[lb] == 0) --lb;
@@ -91,10 +91,29 @@ __global__ void k_mg_images(const MgJob* jobs, WorkList wl, Tables T) {
     __syncthreads();
     // a prime dividing lc(a) or lc(b) is skipped (for a' the leading coefficient is
     // da lc(a), and p > da)
-    const bool bad = (lca == 0u) || (J.kind == kMgGcd && s_lb != J.db);
+    const bool bad = (J.kind == kMgDiv) ? (s_lb != J.db)
+                                        : (lca == 0u) || (J.kind == kMgGcd && s_lb != J.db);
     uint32_t* Qo = J.Qp + (int64_t)q * (J.cap + 1);
     if (bad) {
       if (threadIdx.x == 0) J.dg[q] = -2;
+      __syncthreads();
+      continue;
+    }
+    if (J.kind == kMgDiv) {  // a / b mod p, one quotient coefficient per step; -3: a remainder
+      const int db = J.db, dq = da - db;
+      const uint32_t ilb = minv(sB[db], pc.one_m, M);
+      for (int s = dq; s >= 0; --s) {
+        const uint32_t qc = mmul(sA[s + db], ilb, M);
+        __syncthreads();
+        for (int i = threadIdx.x; i < db; i += blockDim.x) sA[s + i] = msub(sA[s + i], mmul(qc, sB[i], M), M.p);
+        if (threadIdx.x == 0) Qo[s] = redc((uint64_t)qc, M.p, M.pinv);
+        __syncthreads();
+      }
+      bool rem = false;
+      for (int i = threadIdx.x; i < db; i += blockDim.x) rem = rem || (sA[i] != 0u);
+      rem = __syncthreads_or(rem);
+      for (int i = dq + 1 + threadIdx.x; i <= J.cap; i += blockDim.x) Qo[i] = 0u;
+      if (threadIdx.x == 0) J.dg[q] = rem ? -3 : 0;
       __syncthreads();
       continue;
     }
@@ -138,15 +157,17 @@ __global__ void k_mg_select(const MgJob* jobs, int n) {
   int r = 0;
   for (int q = 0; q < J.k_total && r < J.k_need; ++q)
     if (J.dg[q] == mind) J.sel[r++] = q;
-  const int degH = (r == 0) ? -1 : (J.kind == kMgGcd ? mind : J.da - mind);
+  const int degH = (r == 0) ? -1 : (J.kind == kMgGcd ? mind : J.kind == kMgDiv ? J.da - J.db : J.da - mind);
   J.info[0] = degH;
   J.info[1] = r;
   J.info[2] = (r == 0) ? -1 : mind;
-  const bool ok = r == J.k_need;
-  J.info[3] = ok ? 0 : kErrUnlucky;  // the job's status word (the reconstructions may add to it)
+  bool inexact = false;  // a remainder modulo some prime: b does not divide a
+  for (int q = 0; q < J.k_total; ++q) inexact = inexact || J.dg[q] == -3;
+  const bool ok = r == J.k_need && !inexact;
+  J.info[3] = inexact ? kErrArg : ok ? 0 : kErrUnlucky;  // the job's status word (the reconstructions may add to it)
   for (int t = 0; t < 2; ++t) {
     J.crt[t].plan.D = ok ? degH : 0;
-    J.crt[t].plan.status = ok ? 0 : kErrUnlucky;
+    J.crt[t].plan.status = J.info[3];
   }
 }
 
@@ -176,6 +197,10 @@ __global__ void k_mg_gather(const MgJob* jobs, int n, Tables T, int second) {
 template <int K>
 __device__ void mg_content_job(const MgJob& J) {
   if (J.info[3] != 0) return;
+  if (J.kind == kMgDiv) {  // the quotient is the result as it is
+    for (int l = threadIdx.x & 31; l < J.Lc; l += 32) J.content[l] = J.cmul[l] = (l == 0) ? 1u : 0u;
+    return;
+  }
   const int dh = J.info[0];
   ContentAcc<K> h;
   h.fold(J.crt[0].out, dh + 1, J.Lc);
@@ -209,7 +234,7 @@ __global__ void k_mg_cinv(const MgJob* jobs, int n, Tables T) {
   for (int ji = blockIdx.x; ji < n; ji += gridDim.x) {
     const MgJob& J = jobs[ji];
     if (J.info[3] != 0) continue;
-    const bool neg = (J.A[(int64_t)J.da * J.La + J.La - 1] >> 31) != 0;
+    const bool neg = J.kind != kMgDiv && (J.A[(int64_t)J.da * J.La + J.La - 1] >> 31) != 0;
     for (int r = threadIdx.x; r < J.k_need; r += blockDim.x) {
       const int q = J.sel[r];
       const PrimeConst pc = T.pc[q];
@@ -270,16 +295,24 @@ int mg_plan(bs_ctx* ctx, int n, const int* kind, const bs_upoly* a, const bs_upo
   int maxdeg = 0;
   for (int j = 0; j < n; ++j) {
     const int kd = kind[j];
-    if (kd != kMgGcd && kd != kMgSqf) return ctx_fail(ctx, BS_ERR_ARG, "unknown job kind");
+    if (kd != kMgGcd && kd != kMgSqf && kd != kMgDiv) return ctx_fail(ctx, BS_ERR_ARG, "unknown job kind");
     const bs_upoly* pa = a + j;
     const bs_upoly* pb = b ? b + j : nullptr;
     auto bad = [](const bs_upoly* u) {
       return !u || u->deg < -1 || u->limbs < 1 || u->limbs > kMaxUniLimbs || (u->deg >= 0 && !u->c);
     };
-    if (bad(pa) || (kd == kMgGcd && bad(pb))) return ctx_fail(ctx, BS_ERR_ARG, "bad polynomial");
+    if (bad(pa) || (kd != kMgSqf && bad(pb))) return ctx_fail(ctx, BS_ERR_ARG, "bad polynomial");
     int da = trimmed_degree(*pa);
-    int db = kd == kMgGcd ? trimmed_degree(*pb) : -1;
-    if (kd == kMgSqf) {
+    int db = kd != kMgSqf ? trimmed_degree(*pb) : -1;
+    if (kd == kMgDiv) {
+      if (db < 0) return ctx_fail(ctx, BS_ERR_ARG, "division by the zero polynomial");
+      if (da >= 0 && da < db) return ctx_fail(ctx, BS_ERR_ARG, "the division is not exact");
+      if (da < 0) {  // 0 / b = 0
+        B.special[j] = 1;
+        B.special_deg[j] = -1;
+        continue;
+      }
+    } else if (kd == kMgSqf) {
       if (da < 0) return ctx_fail(ctx, BS_ERR_ZERO, "square-free part of the zero polynomial");
       if (da == 0) {
         B.special[j] = 1;
@@ -315,12 +348,12 @@ int mg_plan(bs_ctx* ctx, int n, const int* kind, const bs_upoly* a, const bs_upo
     }
     const bs_upoly& A = B.swap[j] ? *pb : *pa;
     const bs_upoly* Bp = B.swap[j] ? pa : pb;
-    const int cap = kd == kMgGcd ? std::min(da, db) : da;
+    const int cap = kd == kMgGcd ? std::min(da, db) : kd == kMgDiv ? da - db : da;
     const int64_t bits = (int64_t)cap + (l2a + 65535) / 65536 + 1;  // |H| < 2^bits
     const int64_t need = (bits + 2) * 65536;
     if (H.lg_prefix[T] < need) return ctx_fail(ctx, BS_ERR_RANGE, "bound exceeds the prime table");
     const int k = std::max(1, prime_count_host(H.lg_prefix.data(), T, need));
-    const int lcb = lc_bits(A, da) + (kd == kMgGcd ? lc_bits(*Bp, db) : 0);
+    const int lcb = (kd == kMgDiv ? 0 : lc_bits(A, da)) + (kd != kMgSqf ? lc_bits(*Bp, db) : 0);
     const int kt = std::min(T, k + 4 + k / 8 + lcb / 30);
     if ((bits + 2 + 31) / 32 > 256) return ctx_fail(ctx, BS_ERR_RANGE, "coefficients above 8192 bits");
     B.da[j] = da;
@@ -332,11 +365,11 @@ int mg_plan(bs_ctx* ctx, int n, const int* kind, const bs_upoly* a, const bs_upo
     B.kmax = std::max(B.kmax, k);
     B.lmax = std::max(B.lmax, B.out_limbs[j] + 1);
     B.needT = std::max(B.needT, kt);
-    const size_t words = kd == kMgGcd ? (size_t)(da + 1) + (db + 1) + 1 : (size_t)3 * (da + 1);
+    const size_t words = kd != kMgSqf ? (size_t)(da + 1) + (db + 1) + 1 : (size_t)3 * (da + 1);
     B.smem = std::max(B.smem, words * sizeof(uint32_t));
     maxdeg = std::max(maxdeg, std::max(da, db));
-    in_words += (size_t)(da + 1) * A.limbs + (kd == kMgGcd ? (size_t)(db + 1) * Bp->limbs : 0);
-    B.in_limbs = std::max(B.in_limbs, std::max(A.limbs, kd == kMgGcd ? Bp->limbs : 1));
+    in_words += (size_t)(da + 1) * A.limbs + (kd != kMgSqf ? (size_t)(db + 1) * Bp->limbs : 0);
+    B.in_limbs = std::max(B.in_limbs, std::max(A.limbs, kd != kMgSqf ? Bp->limbs : 1));
     B.items += kt;
   }
   if (B.smem > (size_t)ctx->smem_optin - 64)
@@ -412,7 +445,7 @@ int mg_launch(bs_ctx* ctx, MgBatch& B, const bs_upoly* a, const bs_upoly* b, cha
   for (int j = 0; j < n; ++j) {
     if (B.special[j]) continue;
     const bs_upoly& A = B.swap[j] ? b[j] : a[j];
-    const bs_upoly* Bp = B.kind[j] == kMgGcd ? (B.swap[j] ? a + j : b + j) : nullptr;
+    const bs_upoly* Bp = B.kind[j] != kMgSqf ? (B.swap[j] ? a + j : b + j) : nullptr;
     MgJob J;
     std::memset(&J, 0, sizeof(J));
     std::memcpy(in + pos, A.c, sizeof(uint32_t) * (size_t)(B.da[j] + 1) * A.limbs);

@@ -117,3 +117,20 @@ def test_sympy_cross_check_gcd():
         if coeffs[-1] < 0:
             coeffs = [-t for t in coeffs]
         assert G.gcd_z(a, b) == coeffs
+
+
+def test_content_rows_divides_and_leaves_a_primitive_part():
+    # the content divides every row, the quotients have content 1, lc(h) > 0
+    rng = random.Random(7)
+    for t in range(10):
+        h0 = _rand(rng, rng.randrange(0, 4))
+        c = rng.choice([1, -1, 6, -35])
+        rows = [P.scale(P.mul(h0, _rand(rng, rng.randrange(0, 4))), c) for _ in range(rng.randrange(1, 5))]
+        if t % 3 == 0:
+            rows.insert(1, [])                                   # a zero row
+        h, q = G.primitive_rows(rows)
+        assert h[-1] > 0
+        assert all(P.mul(h, qi) == P.trim(r) for qi, r in zip(q, rows))
+        assert G.content_rows(q) == [1]
+        # h is a multiple of the planted factor
+        assert not P.divmod_q(h, h0)[1]
