@@ -16,6 +16,9 @@ Test infrastructure only: plain, slow, exact.
   R_i = S_(i-1) / S_i, and N = sum_i (n_y - i) deg R_i counts the distinct points of the
   curve over its x-critical values (Sec. 3.3).  The same chain over Z_p for one prime p
   gives the lower bound N^- = sum_i (n_y - i) deg R_i^(p).
+* Teissier's Q = res(f_x*, f_y*; y) with f_x*, f_y* the cofactors of h = gcd(f_x, f_y) in
+  Z[x, y] (the primitive pseudo-remainder sequence), and the upper bound
+  N^+ = deg R* n_y - deg R + deg gcd(R^inf mod p, Q mod p) (Sec. 3.3).
 """
 
 from __future__ import annotations
@@ -24,6 +27,7 @@ from fractions import Fraction
 
 from . import gcd as G
 from . import poly as P
+from . import resultant as R
 from .resultant import degree_bound, interpolate_consecutive, y_rows
 from .sylvester import IntRing, PolyRing, det_bareiss, det_modp
 
@@ -195,3 +199,113 @@ def split_curve_fiber_count(branches):
                 continue
             xs.add((d2 - d1) / (c1 - c2))
     return sum(len({d + c * x for d, c in lin}) for x in xs)
+
+
+# ---- bivariate gcd and Teissier's Q (Sec. 3.3, computation of n_alpha^+) ---------------
+# A bivariate polynomial is a list of rows in Z[x] by powers of y (trailing zero rows
+# trimmed), the layout of y_rows.
+
+def _rows(f):
+    return y_rows(f)
+
+
+def _content_rows(A):
+    return G.content_rows(A)
+
+
+def _scale_rows(A, c):
+    return [P.mul(r, c) for r in A]
+
+
+def _div_rows(A, c):
+    return [P.exact_div_z(r, c) for r in A]
+
+
+def _pprem(A, B):
+    """Pseudo-remainder of A by B in Z[x][y]: lc(B)^(deg A - deg B + 1) A mod B."""
+    A = [list(r) for r in A]
+    db = len(B) - 1
+    lb = B[-1]
+    while len(A) - 1 >= db and A:
+        da = len(A) - 1
+        la = A[-1]
+        A = [P.mul(r, lb) for r in A]                        # scale, then cancel the top
+        for i in range(db + 1):
+            A[da - db + i] = P.sub(A[da - db + i], P.mul(la, B[i]))
+        while A and not P.trim(A[-1]):
+            A.pop()
+    return A
+
+
+def bigcd_y(A, B):
+    """gcd of A and B in Z[x][y] by the primitive pseudo-remainder sequence: the gcd of the
+    contents (in Z[x]) times the primitive part of the last nonzero remainder, with a
+    positive leading coefficient."""
+    A, B = _rows(A), _rows(B)
+    if not A:
+        return B
+    if not B:
+        return A
+    ca, cb = _content_rows(A), _content_rows(B)
+    c = G.gcd_z(ca, cb)
+    A, B = _div_rows(A, ca), _div_rows(B, cb)
+    if len(A) < len(B):
+        A, B = B, A
+    while B and len(B) > 1:
+        Rm = _pprem(A, B)
+        A, B = B, (_div_rows(Rm, _content_rows(Rm)) if Rm else [])
+    g = B if B else A
+    if len(g) == 1:                                          # a constant in y: pp is 1
+        g = [[1]]
+    g = _div_rows(g, _content_rows(g))
+    if g[-1][-1] < 0:
+        g = _scale_rows(g, [-1])
+    return _scale_rows(g, c)
+
+
+def bidiv_exact(A, H):
+    """A / H in Z[x][y] (exact)."""
+    A, H = [list(r) for r in _rows(A)], _rows(H)
+    dh = len(H) - 1
+    Q = [[] for _ in range(len(A) - dh)]
+    for k in range(len(A) - 1 - dh, -1, -1):
+        c = P.exact_div_z(A[k + dh], H[-1])
+        Q[k] = c
+        for i in range(dh + 1):
+            A[k + i] = P.sub(A[k + i], P.mul(c, H[i]))
+    assert not any(P.trim(r) for r in A), "inexact bivariate division"
+    return Q
+
+
+def d_dx(f):
+    rows = y_rows(f)
+    return [P.derivative(r) for r in rows]
+
+
+def teissier_q(f):
+    """(Q, d): Q = res(f_x*, f_y*; y) with f_x* = f_x / h, f_y* = f_y / h, h = gcd(f_x, f_y),
+    and d = deg_y h."""
+    fx, fy = d_dx(f), d_dy(f)
+    h = bigcd_y(fx, fy)
+    fxs, fys = bidiv_exact(fx, h), bidiv_exact(fy, h)
+    return R.res_y(fxs, fys), len(h) - 1
+
+
+def fiber_upper_bound_modp(f, p):
+    """N^+ of Sec. 3.3 for the prime p: deg R* n_y - deg R + deg gcd(R^inf mod p, Q mod p),
+    where the last term sums the multiplicities in Q of the common roots:
+    T_1 = gcd(R* mod p, Q mod p), T_k = gcd(T_(k-1), Q^(k-1) mod p)."""
+    fy = d_dy(f)
+    n_y = len(y_rows(f)) - 1
+    Rr = R.res_y(f, fy)
+    Rs = G.squarefree_part(Rr)
+    Q, _ = teissier_q(f)
+    Qp = P.mod_p(Q, p)
+    T = G.gcd_modp(P.mod_p(Rs, p), Qp, p)
+    total = 0
+    dQ = Qp
+    while P.deg(T) > 0:
+        total += P.deg(T)
+        dQ = P.mod_p(P.derivative(dQ), p)
+        T = G.gcd_modp(T, dQ, p)
+    return P.deg(Rs) * n_y - P.deg(Rr) + total

@@ -5,6 +5,7 @@ to points and primes, and the fiber count N against direct counting on split cur
 import random
 
 import numpy as np
+import pytest
 
 from oracle import gcd as G
 from oracle import poly as P
@@ -140,3 +141,88 @@ def test_fiber_lower_bound_with_an_unlucky_prime():
     assert N == S.split_curve_fiber_count(branches) == 14
     _, lb7 = S.fiber_lower_bound_modp(f, 7)
     assert lb7 < N
+
+
+def _compose(c1d, a, b):
+    """c(a x + b y) as rows by powers of y."""
+    def add(A, B):
+        n = max(len(A), len(B))
+        return [P.add(A[i] if i < len(A) else [], B[i] if i < len(B) else []) for i in range(n)]
+
+    def mul(A, B):
+        out = [[] for _ in range(len(A) + len(B) - 1)]
+        for i, r in enumerate(A):
+            for j, q in enumerate(B):
+                out[i + j] = P.add(out[i + j], P.mul(r, q))
+        return out
+    acc, pw, lin = [[]], [[1]], [[0, a], [b]]
+    for c in c1d:
+        acc = add(acc, [P.scale(r, c) for r in pw])
+        pw = mul(pw, lin)
+    return acc, add, mul
+
+
+def test_bivariate_gcd_planted_factors():
+    rng = np.random.Generator(np.random.PCG64(17))
+    for t in range(6):
+        H = dense_curve(rng, 1 + t % 2, 4)
+        U = dense_curve(rng, 2, 4)
+        V = dense_curve(rng, 2, 4)
+        _, add, mul = _compose([1], 1, 1)
+        A, B = mul(H, U), mul(H, V)
+        g = S.bigcd_y(A, B)
+        # g divides both, the cofactors are coprime, and g is a multiple of H
+        ca, cb = S.bidiv_exact(A, g), S.bidiv_exact(B, g)
+        assert S.bigcd_y(ca, cb) == [[1]]
+        S.bidiv_exact(g, H)
+
+
+def test_bivariate_gcd_against_sympy():
+    sympy = pytest.importorskip("sympy")
+    x, y = sympy.symbols("x y")
+    rng = np.random.Generator(np.random.PCG64(18))
+
+    def to_expr(F):
+        return sum(c * x**i * y**j for j, r in enumerate(F) for i, c in enumerate(r))
+    for t in range(4):
+        H, U, V = (dense_curve(rng, 2, 4) for _ in range(3))
+        _, add, mul = _compose([1], 1, 1)
+        A, B = mul(H, U), mul(H, V)
+        want = sympy.Poly(sympy.gcd(to_expr(A), to_expr(B)), x, y)
+        got = sympy.Poly(to_expr(S.bigcd_y(A, B)), x, y)
+        assert got == want or got == -want, t
+
+
+def test_teissier_q_closed_form():
+    # f = P(s)^2 K(t) + c with s = x + y, t = x - y: f_x = P (2 P' K + P K'),
+    # f_y = P (2 P' K - P K'), so Q = res_y(2 P' K + P K', 2 P' K - P K') up to a constant
+    rng = random.Random(19)
+    for t in range(5):
+        pc = [rng.randrange(-4, 5) or 1 for _ in range(rng.randrange(2, 4))]
+        kc = [rng.randrange(-4, 5) or 1 for _ in range(rng.randrange(2, 4))]
+        Pp, add, mul = _compose(pc, 1, 1)
+        dP, _, _ = _compose(P.derivative(pc), 1, 1)
+        Kk, _, _ = _compose(kc, 1, -1)
+        dK, _, _ = _compose(P.derivative(kc), 1, -1)
+        f = add(mul(mul(Pp, Pp), Kk), [[rng.randrange(1, 9)]])
+        two = [[2]]
+        a = add(mul(mul(two, dP), Kk), mul(Pp, dK))
+        b = add(mul(mul(two, dP), Kk), [P.scale(r, -1) for r in mul(Pp, dK)])
+        Q, d = S.teissier_q(f)
+        assert d == len(Pp) - 1
+        assert P.primitive_part(Q) == P.primitive_part(R.res_y(a, b)), t
+        # the first principal subresultant coefficient of f_x, f_y that is not zero is
+        # a constant multiple of Q (the cofactor property of subresultants)
+        sr = S.psc_y(S.d_dx(f), S.d_dy(f))
+        assert all(not P.trim(s) for s in sr[:d]) and P.primitive_part(sr[d]) == P.primitive_part(Q)
+
+
+def test_fiber_bounds_bracket_N():
+    p = prime_table(1)[0]
+    for branches in ([[0, 1], [0, -1], [2, 1], [1, 0]], [[1, 1], [3, -1], [0, 2], [4, -2]]):
+        f = S.split_curve(branches)
+        _, N = S.fiber_decomposition(f)
+        _, lb = S.fiber_lower_bound_modp(f, p)
+        ub = S.fiber_upper_bound_modp(f, p)
+        assert lb <= N <= ub
+        assert ub == N          # lines in general position: f_x*, f_y* meet only on C
