@@ -327,7 +327,9 @@ int bs_psc_modp(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var, in
  * the square-free decomposition R* = R_1 R_2 ... by fibers (Sec. 3.3): R_i(alpha) = 0
  * exactly when f(alpha, y) has n_y - i distinct roots, N = sum_i (n_y - i) deg R_i.
  * mode 0: exact (psc's in Z[x], gcds in Z[x]); mode 1: the lower bound N^- from the same
- * chain over Z_p for one prime (*p receives it; 0 in mode 0).  f must have a constant
+ * chain over Z_p for one prime (*p receives it; 0 in mode 0); mode 2: the upper bound
+ * N^+ = deg R* n_y - deg R + deg gcd(R^inf mod p, Q mod p) with Teissier's Q (see
+ * bs_teissier_q) for one prime p (*p receives it; *s = 0).  f must have a constant
  * leading coefficient in the eliminated variable (no vertical asymptote) and at most 63
  * limbs per coefficient.  degs[i - 1] = deg R_i for i = 1..*s (cap entries available).
  * Errors: BS_ERR_ARG (non-constant leading coefficient, bad arguments), BS_ERR_ZERO (f = 0,
@@ -348,6 +350,17 @@ int bs_fiber_count(bs_ctx *ctx, const bs_bipoly *f, int var, int mode, int cap, 
  * Errors: BS_ERR_ARG, BS_ERR_ZERO (f = 0), BS_ERR_CAPACITY, BS_ERR_RANGE, BS_ERR_UNLUCKY. */
 int bs_content(bs_ctx *ctx, const bs_bipoly *f, int var, bs_upoly *h, int cap_rows, bs_upoly *rows,
                int32_t *nrows);
+
+/* Teissier's Q = res(f_x*, f_y*; y) of Sec. 3.3, where f_x* = f_x / h, f_y* = f_y / h and
+ * h = gcd(f_x, f_y) in Z[x, y] (for var = 0 the roles of x and y are exchanged), up to a
+ * nonzero constant factor.  With lc(f) constant in the eliminated variable (required:
+ * BS_ERR_ARG otherwise), h has a constant leading coefficient and the first principal
+ * subresultant coefficient of f_x and f_y that is not identically zero, sr_d, is a
+ * constant multiple of Q with d = deg h (the cofactor property of subresultants); Q is
+ * returned as that sr_d (the constant 1 when every sr_i vanishes), *d = d.
+ * Q: caller-owned output in the layout of bs_squarefree_part; Q->c == NULL is a size query
+ * (it computes the sequence).  Errors as for bs_psc, BS_ERR_ZERO for f = 0. */
+int bs_teissier_q(bs_ctx *ctx, const bs_bipoly *f, int var, bs_upoly *Q, int32_t *d);
 
 /* Launch shapes of the batched stages (bs_autotune_batch). */
 typedef struct {

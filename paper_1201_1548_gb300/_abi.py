@@ -20,7 +20,7 @@ EXPORTED_SYMBOLS = [
     "bs_stage_times", "bs_resultant_device_noalloc", "bs_gcd_z", "bs_modgcd_batch",
     "bs_autotune_batch", "bs_set_tune", "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
     "bs_squarefree_factorization", "bs_squarefree_factorization_batch", "bs_psc",
-    "bs_psc_modp", "bs_fiber_count", "bs_content",
+    "bs_psc_modp", "bs_fiber_count", "bs_content", "bs_teissier_q",
 ]
 
 
@@ -137,6 +137,7 @@ def load_library():
     lib.bs_psc_modp.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, C.POINTER(C.c_int32),
                                 C.POINTER(C.c_int32), P, P, C.POINTER(C.c_uint32)]
     lib.bs_content.argtypes = [P, C.POINTER(_Bipoly), I, C.POINTER(_Upoly), I, P, C.POINTER(C.c_int32)]
+    lib.bs_teissier_q.argtypes = [P, C.POINTER(_Bipoly), I, C.POINTER(_Upoly), C.POINTER(C.c_int32)]
     lib.bs_fiber_count.argtypes = [P, C.POINTER(_Bipoly), I, I, I, P, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int64), C.POINTER(C.c_uint32)]
     lib.bs_serve_start.argtypes = [P, I, I, C.c_size_t]
@@ -312,9 +313,22 @@ class Context:
         conv = lambda u, b: limbs_to_ints(b, u.deg + 1, u.limbs) if u.deg >= 0 else []
         return conv(h, hb), [conv(rows[i], bufs[i]) for i in range(nr.value)]
 
+    def teissier_q(self, f, var=1):
+        """(Q, d): Teissier's Q up to a nonzero constant (the d-th principal subresultant
+        coefficient of f_x and f_y, d = deg gcd(f_x, f_y))."""
+        af, dxf, dyf, Lf = bipoly_to_limbs(f)
+        fb = _bip(af, dxf, dyf, Lf)
+        q, d = _Upoly(0, 0, None), C.c_int32(0)
+        self._check(self.lib.bs_teissier_q(self.h, C.byref(fb), int(var), C.byref(q), C.byref(d)))
+        buf = np.zeros((max(q.deg, 0) + 1) * q.limbs, dtype=np.uint32)
+        q = _Upoly(max(q.deg, 0), q.limbs, buf.ctypes.data)
+        self._check(self.lib.bs_teissier_q(self.h, C.byref(fb), int(var), C.byref(q), C.byref(d)))
+        return (limbs_to_ints(buf, q.deg + 1, q.limbs) if q.deg >= 0 else []), int(d.value)
+
     def fiber_count(self, f, var=1, mode=0):
         """(degs, N, p): deg R_1, deg R_2, ... of the decomposition of R* by fibers, the point
-        count N (mode 0, exact) or its lower bound N^- for one prime p (mode 1)."""
+        count N (mode 0, exact), its lower bound N^- (mode 1) or upper bound N^+ (mode 2, no
+        degrees) for one prime p."""
         af, dxf, dyf, Lf = bipoly_to_limbs(f)
         fb = _bip(af, dxf, dyf, Lf)
         cap = max(dxf, dyf) + 2

@@ -103,6 +103,55 @@ static uint32_t residue_of(const uint32_t* c, int L, uint32_t p) {
   return (uint32_t)r;
 }
 
+// the exact psc sequence of (a, b) as owned host polynomials
+static int psc_owned(bs_ctx* ctx, const bs_bipoly* a, const bs_bipoly* b, int var, std::vector<HostPoly>* out) {
+  int32_t q = 0;
+  int rc = bs_psc(ctx, a, b, var, 0, &q, nullptr);
+  if (rc) return rc;
+  out->assign(q, HostPoly{});
+  if (q == 0) return BS_OK;
+  std::vector<bs_upoly> sr(q, bs_upoly{0, 0, nullptr});
+  rc = bs_psc(ctx, a, b, var, q, &q, sr.data());
+  if (rc) return rc;
+  for (int i = 0; i < q; ++i) {
+    (*out)[i].c.assign((size_t)(std::max(sr[i].deg, 0) + 1) * sr[i].limbs, 0u);
+    sr[i].c = (*out)[i].c.data();
+  }
+  rc = bs_psc(ctx, a, b, var, q, &q, sr.data());
+  if (rc) return rc;
+  for (int i = 0; i < q; ++i) {
+    (*out)[i].u = sr[i];
+    (*out)[i].u.c = (*out)[i].c.data();
+  }
+  return BS_OK;
+}
+
+// Teissier's Q up to a nonzero constant: with lc(f) constant in the eliminated variable,
+// h = gcd(f_x, f_y) has a constant leading coefficient, and at every point the first
+// principal subresultant coefficient of f_x and f_y that is not identically zero, sr_d
+// with d = deg h, is that constant's power times res(f_x / h, f_y / h) (the cofactor
+// property of subresultants); so Q is sr_d as a polynomial (1 when all sr_i vanish).
+static int teissier(bs_ctx* ctx, const bs_bipoly* f, int var, HostPoly* Q, int* d_out) {
+  std::vector<uint32_t> xbuf, ybuf;
+  bs_bipoly fx, fy;
+  grid_derivative(*f, 1 - var, &xbuf, &fx);
+  grid_derivative(*f, var, &ybuf, &fy);
+  std::vector<HostPoly> sr;
+  int rc = psc_owned(ctx, &fx, &fy, var, &sr);
+  if (rc) return rc;
+  int d = 0;
+  while (d < (int)sr.size() && sr[d].u.deg < 0) ++d;
+  *d_out = d;
+  if (d < (int)sr.size()) {
+    *Q = std::move(sr[d]);
+    Q->u.c = Q->c.data();
+  } else {
+    Q->c.assign(1, 1u);
+    Q->u = bs_upoly{0, 1, Q->c.data()};
+  }
+  return BS_OK;
+}
+
 static int run_fiber(bs_ctx* ctx, const bs_bipoly* f, int var, int mode, int cap, int32_t* degs, int32_t* s_out,
                      int64_t* N_out, uint32_t* p_out) {
   if (!f || f->deg_x < 0 || f->deg_y < 0 || f->limbs < 1 || !f->c)
@@ -120,6 +169,67 @@ static int run_fiber(bs_ctx* ctx, const bs_bipoly* f, int var, int mode, int cap
   bs_bipoly g;
   grid_derivative(*f, var, &gbuf, &g);
   int rc;
+  if (mode == 2) {  // N^+ = deg R* n_y - deg R + deg gcd(R^inf mod p, Q mod p)
+    std::vector<uint32_t> xbuf;
+    bs_bipoly fx;
+    grid_derivative(*f, 1 - var, &xbuf, &fx);
+    int32_t q = 0, dmax = 0;
+    uint32_t p = 0;
+    rc = bs_psc_modp(ctx, &fx, &g, var, &q, &dmax, nullptr, nullptr, &p);
+    if (rc) return rc;
+    std::vector<int32_t> dq(std::max(q, 1));
+    std::vector<uint32_t> coef((size_t)std::max(q, 1) * (dmax + 1));
+    if (q > 0) {
+      rc = bs_psc_modp(ctx, &fx, &g, var, &q, &dmax, dq.data(), coef.data(), &p);
+      if (rc) return rc;
+    }
+    int d = 0;
+    while (d < q && dq[d] < 0) ++d;
+    std::vector<uint32_t> Qp;
+    if (d < q)
+      Qp.assign(coef.begin() + (size_t)d * (dmax + 1), coef.begin() + (size_t)d * (dmax + 1) + dq[d] + 1);
+    else
+      Qp.assign(1, 1u);
+    if (p == 0) p = host_primes().p[0];  // q = 0: f_x or f_y constant in the variable
+    HostPoly Rr;
+    rc = fetch(&Rr, [&](bs_upoly* o) { return bs_resultant(ctx, f, &g, var, o); });
+    if (rc) return rc;
+    int dr = Rr.u.deg;
+    while (dr >= 0 && limbs_zero(Rr.u.c + (size_t)dr * Rr.u.limbs, Rr.u.limbs)) --dr;
+    if (dr < 0) return ctx_fail(ctx, BS_ERR_ZERO, "res(f, f_y) = 0: f is not square-free");
+    Rr.u.deg = dr;
+    HostPoly Rs;
+    rc = fetch(&Rs, [&](bs_upoly* o) { return bs_squarefree_part(ctx, &Rr.u, o); });
+    if (rc) return rc;
+    std::vector<uint32_t> S(Rs.u.deg + 1);
+    for (int i = 0; i <= Rs.u.deg; ++i) S[i] = residue_of(Rs.u.c + (size_t)i * Rs.u.limbs, Rs.u.limbs, p);
+    int ds = Rs.u.deg;
+    while (ds >= 0 && S[ds] == 0u) --ds;
+    // T_1 = gcd(R* mod p, Q mod p), T_k = gcd(T_(k-1), Q^(k-1) mod p): sum deg T_k counts
+    // the common roots with their multiplicities in Q
+    int64_t total = 0;
+    std::vector<uint32_t> T(std::max<size_t>(S.size(), Qp.size()) + 1);
+    int dt = -1;
+    rc = bs_gcd_modp(ctx, S.data(), ds, Qp.data(), (int)Qp.size() - 1, p, T.data(), &dt);
+    if (rc) return rc;
+    std::vector<uint32_t> dQ = Qp, G(T.size());
+    while (dt > 0) {
+      total += dt;
+      for (size_t i = 0; i + 1 < dQ.size(); ++i)  // the derivative mod p
+        dQ[i] = (uint32_t)((uint64_t)dQ[i + 1] * (uint64_t)((i + 1) % p) % p);
+      dQ.pop_back();
+      int ddq = (int)dQ.size() - 1;
+      while (ddq >= 0 && dQ[ddq] == 0u) --ddq;
+      int dg = -1;
+      rc = bs_gcd_modp(ctx, T.data(), dt, dQ.data(), ddq, p, G.data(), &dg);
+      if (rc) return rc;
+      std::copy(G.begin(), G.begin() + (dg + 1), T.begin());
+      dt = dg;
+    }
+    *N_out = (int64_t)Rs.u.deg * ny - dr + total;
+    *p_out = p;
+    return BS_OK;
+  }
   std::vector<int32_t> dl;  // deg S_0, deg S_1, ...
   if (mode == 0) {
     // exact: the psc's, R* and the chain of gcds in Z[x]
@@ -208,9 +318,31 @@ using namespace bs;
 extern "C" int bs_fiber_count(bs_ctx* ctx, const bs_bipoly* f, int var, int mode, int cap, int32_t* degs,
                               int32_t* s, int64_t* N, uint32_t* p) {
   if (!ctx) return BS_ERR_ARG;
-  if (!f || (var != 0 && var != 1) || (mode != 0 && mode != 1) || cap < 0 || (cap > 0 && !degs) || !s || !N ||
+  if (!f || (var != 0 && var != 1) || mode < 0 || mode > 2 || cap < 0 || (cap > 0 && !degs) || !s || !N ||
       !p)
     return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
   if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
   return run_fiber(ctx, f, var, mode, cap, degs, s, N, p);
+}
+
+extern "C" int bs_teissier_q(bs_ctx* ctx, const bs_bipoly* f, int var, bs_upoly* Q, int32_t* d) {
+  if (!ctx) return BS_ERR_ARG;
+  if (!f || !Q || !d || (var != 0 && var != 1)) return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
+  if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
+  if (f->deg_x < 0 || f->deg_y < 0 || f->limbs < 1 || !f->c) return ctx_fail(ctx, BS_ERR_ARG, "bad bivariate polynomial");
+  if (f->limbs >= kMaxLimbs) return ctx_fail(ctx, BS_ERR_RANGE, "the derivatives need more than 64 limbs");
+  bool clc = true;
+  if (lead_degree(*f, var, &clc) < 0) return ctx_fail(ctx, BS_ERR_ZERO, "the zero polynomial");
+  if (!clc) return ctx_fail(ctx, BS_ERR_ARG, "the leading coefficient is not constant (vertical asymptote)");
+  HostPoly q;
+  int dd = 0;
+  int rc = teissier(ctx, f, var, &q, &dd);
+  if (rc) return rc;
+  *d = dd;
+  if (!Q->c) {  // size query
+    Q->deg = q.u.deg;
+    Q->limbs = q.u.limbs;
+    return BS_OK;
+  }
+  return put_result(ctx, q.u.c, q.u.limbs, q.u.deg, Q);
 }

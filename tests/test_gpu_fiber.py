@@ -88,3 +88,75 @@ def test_fiber_count_rejects_bad_curves(ctx):
     assert e.value.code == bs.BS_ERR_ZERO
     # linear in y: no critical values
     assert ctx.fiber_count([[1, 2, 3], [1, 0, 0]]) == ([], 0, 0)
+
+
+def _compose(c1d, a, b):
+    """c(a x + b y) as rows by powers of y, with the row helpers."""
+    from oracle import poly as P
+
+    def add(A, B):
+        n = max(len(A), len(B))
+        return [P.add(A[i] if i < len(A) else [], B[i] if i < len(B) else []) for i in range(n)]
+
+    def mul(A, B):
+        out = [[] for _ in range(len(A) + len(B) - 1)]
+        for i, r in enumerate(A):
+            for j, q in enumerate(B):
+                out[i + j] = P.add(out[i + j], P.mul(r, q))
+        return out
+    acc, pw, lin = [[]], [[1]], [[0, a], [b]]
+    for c in c1d:
+        acc = add(acc, [P.scale(r, c) for r in pw])
+        pw = mul(pw, lin)
+    return acc, add, mul
+
+
+def _grid(rows):
+    w = max(len(r) for r in rows)
+    return [list(r) + [0] * (w - len(r)) for r in rows]
+
+
+def test_teissier_q_with_a_common_factor(ctx):
+    # f = P(x+y)^2 K(x-y) + c: f_x and f_y share P(x+y), d = deg P
+    from oracle import poly as P
+    import random
+    rng = random.Random(64)
+    for t in range(4):
+        pc = [rng.randrange(-4, 5) or 1 for _ in range(rng.randrange(2, 4))]
+        kc = [rng.randrange(-4, 5) or 1 for _ in range(rng.randrange(2, 4))]
+        Pp, add, mul = _compose(pc, 1, 1)
+        Kk, _, _ = _compose(kc, 1, -1)
+        f = _grid(add(mul(mul(Pp, Pp), Kk), [[rng.randrange(1, 9)]]))
+        Q, d = ctx.teissier_q(f)
+        want, wd = S.teissier_q(f)
+        assert d == wd == len(pc) - 1, t
+        assert P.primitive_part(Q) == P.primitive_part(want), t
+
+
+def test_teissier_q_dense_curves(ctx):
+    from oracle import poly as P
+    rng = _rng(65)
+    for t in range(4):
+        f = dense_curve(rng, 3 + t % 2, 10)
+        Q, d = ctx.teissier_q(f)
+        want, wd = S.teissier_q(f)
+        assert d == wd == 0 and P.primitive_part(Q) == P.primitive_part(want), t
+
+
+@pytest.mark.parametrize("branches", SPLIT)
+def test_fiber_upper_bound(ctx, branches):
+    f = S.split_curve(branches)
+    _, N, _ = ctx.fiber_count(f)
+    degs, ub, p = ctx.fiber_count(f, mode=2)
+    assert degs == [] and p > 0
+    assert ub == S.fiber_upper_bound_modp(f, p)
+    _, lb, _ = ctx.fiber_count(f, mode=1)
+    assert lb <= N <= ub
+
+
+def test_fiber_upper_bound_dense(ctx):
+    rng = _rng(66)
+    for t in range(3):
+        f = dense_curve(rng, 3 + t % 2, 10)
+        _, ub, p = ctx.fiber_count(f, mode=2)
+        assert ub == S.fiber_upper_bound_modp(f, p), t
