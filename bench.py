@@ -97,10 +97,19 @@ def _cpu_baseline(f, g, pool, cores, npts):
     bits = (bound_sq(f, g).bit_length() + 1) // 2
     t_int = _oracle_interp_time(D, bits)
     per_res = t_pts * (D + 1) / npts + t_int
+    # the same route on one core: two point determinants in this process
+    from oracle.resultant import res_at_point
+    t0 = time.perf_counter()
+    for x in (-(D // 2), 1):
+        res_at_point(f, g, x)
+    t_one = (time.perf_counter() - t0) / 2
+    single = 1.0 / (t_one * (D + 1) + t_int)
     return {"value": 1.0 / per_res, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": single,
             "sample": f"{npts} of the {D + 1} exact Bareiss point determinants (63x63 over Z) "
                       f"on {cores} processes, scaled to all {D + 1} points, plus one exact "
-                      f"interpolation of {D + 1} values ({t_pts:.2f} s + {t_int:.2f} s)"}
+                      f"interpolation of {D + 1} values ({t_pts:.2f} s + {t_int:.2f} s); "
+                      f"single core: 2 determinants in one process ({t_one:.2f} s each)"}
 
 
 def run_reference(args):
