@@ -6,7 +6,9 @@
 // mod 2^32, the low words of t and m*p agree, so (t - m*p) / 2^32 = hi(t) - hi(m*p),
 // which lies in (-p, p) and needs one conditional correction.
 //
-// Values are kept in [0, p).  "Montgomery form" of x is x * 2^32 mod p.
+// Values are kept in [0, p).  "Montgomery form" of x is x * 2^32 mod p.  Every correction
+// is an unsigned minimum of a value and its shift by p (a wrapped difference exceeds
+// 2^31 > p), which needs no predicate.
 #pragma once
 #include <stdint.h>
 
@@ -38,7 +40,8 @@ BS_HD uint32_t redc(uint64_t t, uint32_t p, uint32_t pinv) {
   uint32_t m = tl * pinv;
   uint32_t h = umulhi32(m, p);
   uint32_t r = th - h;
-  return (th < h) ? r + p : r;
+  uint32_t r2 = r + p;  // th < h: r wrapped past 2^31 and r + p is the residue; else r < p
+  return r2 < r ? r2 : r;
 }
 
 // t < 2^32 * 1.5p (e.g. a sum of three products of values < p): fold the high word
@@ -51,7 +54,8 @@ BS_HD uint32_t redc_wide(uint64_t t, uint32_t p, uint32_t pinv) {
   uint32_t m = tl * pinv;
   uint32_t h = umulhi32(m, p);
   uint32_t r = th - h;
-  return (th < h) ? r + p : r;
+  uint32_t r2 = r + p;
+  return r2 < r ? r2 : r;
 }
 
 BS_HD uint32_t mmul(uint32_t a, uint32_t b, const Mod& M) {
@@ -66,7 +70,8 @@ BS_HD uint32_t madd(uint32_t a, uint32_t b, uint32_t p) {
 
 BS_HD uint32_t msub(uint32_t a, uint32_t b, uint32_t p) {
   uint32_t d = a - b;
-  return (a < b) ? d + p : d;
+  uint32_t d2 = d + p;  // a < b: d wrapped and d + p is the residue; else d < p < d + p
+  return d2 < d ? d2 : d;
 }
 
 BS_HD uint32_t mneg(uint32_t a, uint32_t p) { return a ? p - a : 0; }
