@@ -33,7 +33,7 @@ UNIT = "resultants/s"
 WORKLOAD = "res_y(f, df/dy), f dense total degree 32, signed 32-bit coefficients, seed 1"
 SEED = 1
 # DRAM bytes (read + write) of one k_unires<33> launch of this workload, from one ncu capture
-# (caches flushed between passes, as ncu does); profiles/k_unires_cfg2.md
+# (caches flushed between passes, as ncu does)
 K3_DRAM_BYTES = 21613568
 
 
