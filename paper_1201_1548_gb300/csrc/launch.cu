@@ -79,7 +79,7 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   g = grid_for((L.intt_w_items + kInttWarps - 1) / kInttWarps, (int64_t)sms * 8);
   if (g) launch_intt_w(g, s, L.jobs, L.intt_w, Tv);
   g = grid_for(L.intt_items, (int64_t)sms * 8);
-  if (g) launch_intt(g, 2 * tsmem, s, L.jobs, L.intt, Tv);  // values + packed twiddles
+  if (g) launch_intt(g, kInttSmemWords * tsmem, s, L.jobs, L.intt, Tv);
   mark(ctx, 4, s);
   g = grid_for(L.crt_items, (int64_t)sms * L.crt_blocks_per_sm);
   const size_t wsm = crt_warp_smem(L.kmax, L.lmax);
@@ -108,7 +108,7 @@ bool crt_warp_kernel(const bs_ctx* ctx, int kmax, int lmax) {
 
 int launch_stages(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, bool use_graph) {
   cudaStream_t s = ctx->stream;
-  if (2 * (size_t)L.maxN * sizeof(uint32_t) > (size_t)ctx->smem_optin)  // interpolation block
+  if (kInttSmemWords * (size_t)L.maxN * sizeof(uint32_t) > (size_t)ctx->smem_optin)  // interpolation block
     return ctx_fail(ctx, kErrRange, "transform size exceeds shared memory");
   size_t crt_smem = 0;
   int crt_staged = 0;
@@ -160,7 +160,7 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   cudaStream_t s = ctx->stream;
   const Tables Tv = ctx->tabs->view();
   const int N = 1 << mb.logN;
-  if (2 * (size_t)N * sizeof(uint32_t) > (size_t)ctx->smem_optin)  // interpolation block
+  if (kInttSmemWords * (size_t)N * sizeof(uint32_t) > (size_t)ctx->smem_optin)  // interpolation block
     return ctx_fail(ctx, kErrRange, "transform size exceeds shared memory");
   if (ctx->profile)
     for (int i = 0; i < kProfEvents; ++i) ctx->prof_rec[i] = false;

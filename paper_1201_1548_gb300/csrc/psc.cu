@@ -108,7 +108,7 @@ static int psc_plan(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var
   const Plan& P = S.P;
   if (uni_class_of(std::max(P.me, P.ne) + 1) < 0)
     return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
-  if (2 * (size_t)P.N * sizeof(uint32_t) > (size_t)ctx->smem_optin)
+  if (kInttSmemWords * (size_t)P.N * sizeof(uint32_t) > (size_t)ctx->smem_optin)
     return ctx_fail(ctx, BS_ERR_RANGE, "transform size exceeds shared memory");
   S.rows = (P.me + 1) + (P.ne + 1);
   S.in_f = (int64_t)(f->deg_y + 1) * (f->deg_x + 1) * f->limbs;
@@ -230,7 +230,7 @@ static int psc_launch(bs_ctx* ctx, const PscPlan& S, const bs_bipoly* f, const b
     launch_intt_w((int)std::min<int64_t>((ioff[q] + kInttWarps - 1) / kInttWarps, (int64_t)sms * 8), s, dj,
                   wl_i, Tv);
   else
-    launch_intt((int)std::min<int64_t>(ioff[q], (int64_t)sms * 8), 2 * sizeof(uint32_t) * (size_t)P.N, s, dj,
+    launch_intt((int)std::min<int64_t>(ioff[q], (int64_t)sms * 8), kInttSmemWords * sizeof(uint32_t) * (size_t)P.N, s, dj,
                 wl_i, Tv);
   const WorkList wl_c{(const int32_t*)(base + S.o_ids), (const int64_t*)(base + S.o_crt_off), q};
   if (!S.modp) {  // the modular form stops at the residues

@@ -654,6 +654,23 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
       s_good = 0;
     }
     __syncthreads();
+    // stage the values, this prime's packed inverse twiddles and inverse coset powers
+    // before the selection, so that all loads are in flight together (a prime that turns
+    // out to be rejected or not needed skips the transform)
+    const int logN = J->plan.logN;
+    const int N = 1 << logN;
+    uint32_t* sit = sm + N;
+    uint32_t* sic = sit + N;
+    {
+      const uint32_t* src = J->vals + ((int64_t)q << logN);
+      const uint32_t* itq = T.itwp + (int64_t)q * T.NT;
+      const uint32_t* icq = T.icp + (int64_t)q * T.NT;
+      for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        sm[t] = src[t];
+        sit[t] = __ldg(itq + t);
+        sic[t] = __ldg(icq + t);
+      }
+    }
     int cnt = 0;
     for (int j = threadIdx.x; j < q; j += blockDim.x) cnt += (J->pstat[j] == 0);
     if (cnt) atomicAdd(&s_rank, cnt);
@@ -671,28 +688,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
     const bool good = J->pstat[q] == 0;
     __syncthreads();
     if (!good || r >= k_need) continue;
-    const int logN = J->plan.logN;
-    const int N = 1 << logN;
     const int D = J->plan.D;
     const PrimeConst pc = T.pc[q];
     const Mod M{pc.p, pc.pinv};
-    const uint32_t* src = J->vals + ((int64_t)q << logN);
-    for (int t = threadIdx.x; t < N; t += blockDim.x) sm[t] = src[t];
-    __syncthreads();
-    // this prime's packed inverse twiddles, staged after the values
-    uint32_t* sit = sm + N;
-    {
-      const uint32_t* itq = T.itwp + (int64_t)q * T.NT;
-      for (int t = threadIdx.x; t < N; t += blockDim.x) sit[t] = __ldg(itq + t);
-    }
-    __syncthreads();
     dit_intt(sm, logN, sit, M);
-    const uint32_t* icp = T.icp + (int64_t)q * T.NT;
     const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
     uint32_t* dst = J->rmod + (int64_t)r * (D + 1);
     bool bad = false;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      const uint32_t v = mmul(mmul(sm[i], icp[i], M), ni, M);
+      const uint32_t v = mmul(mmul(sm[i], sic[i], M), ni, M);
       if (i <= D)
         dst[i] = v;
       else if (v != 0)
@@ -1308,12 +1312,10 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
       const int j = t / kCrtTile, c = t - j * kCrtTile;
       X[t] = (c < nvalid) ? J->rmod[(int64_t)j * (D + 1) + i0 + c] : 0u;
     }
-    __syncthreads();
-    const bool table_order = (selq[k - 1] == (uint32_t)(k - 1));
-    // weighted-sum path for table-ordered jobs with tabulated k; Garner otherwise
-    const bool ws = table_order && k <= T.WK;
     const int L = ws_len(k);
-    if (ws) {
+    if (k <= T.WK) {
+      // weighted-sum tables, staged with the residues (they depend on k only; the Garner
+      // path below overwrites them when the selected primes are not the first k):
       // M_k is k rows of L limbs, contiguous: one flat copy with many loads in flight
       const uint32_t* Mk = T.ws_m + T.ws_moff[k];
       const int n = k * L;
@@ -1326,7 +1328,12 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
       }
       const uint32_t* Pk = T.pp + (int64_t)k * T.LPP;
       for (int t = threadIdx.x; t < L; t += nthr) sPk[t] = t < T.LPP ? __ldg(Pk + t) : 0u;
-    } else {
+    }
+    __syncthreads();
+    const bool table_order = (selq[k - 1] == (uint32_t)(k - 1));
+    // weighted-sum path for table-ordered jobs with tabulated k; Garner otherwise
+    const bool ws = table_order && k <= T.WK;
+    if (!ws) {
       for (int a = warp; a < k; a += nthr / 32) {
         const int64_t rowa = (int64_t)selq[a] * Tg;
 #pragma unroll 4

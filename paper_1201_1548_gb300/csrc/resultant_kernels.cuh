@@ -18,6 +18,7 @@ constexpr int kOffEvalW = 0, kOffEvalS = 2, kOffUni = 4, kOffInttW = 6, kOffIntt
               kOffCrt = 10, kNumOffs = 12;
 constexpr int kInttWarps = 4;     // warps (primes) of a warp-interpolation block
 constexpr int kWarpInttLogNMax = 9;  // interpolations up to 2^9 points run one per warp
+constexpr int kInttSmemWords = 3;  // words per point of an interpolation block: values, twiddles, coset powers
 // size classes of the warp evaluation kernels: N <= 32, 64, 128, 256, 512, 1024
 constexpr int kNumEvalClasses = 6;
 inline int eval_class_of(int logN) { return logN <= 5 ? 0 : logN - 5; }
