@@ -373,6 +373,40 @@ BS_HD int exact_prime_total(int k_need, bool lc_monomials, int table_size, IsDiv
   }
 }
 
+// row statistics for coefficients of at most two limbs (host): the magnitudes are summed
+// exactly in 128 bits and rounded up to an upper float once per row
+inline RowStat row_stat_narrow(const Grid& g, int var, int e) {
+  RowStat s{UF{0u, 0}, -1, 0};
+  unsigned __int128 sum = 0;
+  const int eo = ext_o(g, var);
+  for (int o = 0; o <= eo; ++o) {
+    const uint32_t* c = coef_ptr(g, var, e, o);
+    uint64_t mag;
+    if (g.L == 1) {
+      const int64_t v = (int32_t)c[0];
+      mag = (uint64_t)(v < 0 ? -v : v);
+    } else {
+      const uint64_t raw = ((uint64_t)c[1] << 32) | c[0];
+      mag = (raw >> 63) ? ~raw + 1 : raw;  // |INT64_MIN| = 2^63 is representable
+    }
+    if (!mag) continue;
+    sum += mag;
+    s.max_o = o;
+    const int bits = 64 - clz64(mag);
+    if (s.min_bits == 0 || bits < s.min_bits) s.min_bits = bits;
+  }
+  const uint64_t hi = (uint64_t)(sum >> 64), lo = (uint64_t)sum;
+  if (!hi) {
+    s.l1 = uf_make(lo, 0, false);
+  } else {  // keep the top 64 bits, round up by the rest
+    const int sh = 64 - clz64(hi);
+    const uint64_t top = (hi << (64 - sh)) | (lo >> sh);
+    const bool sticky = (lo << (64 - sh)) != 0;
+    s.l1 = uf_make(top, sh, sticky);
+  }
+  return s;
+}
+
 // host version: scan both grids
 inline Plan plan_host(const Grid& f, const Grid& g, int var, const int64_t* lg_prefix,
                       int table_size, const uint32_t* primes = nullptr) {
@@ -384,7 +418,7 @@ inline Plan plan_host(const Grid& f, const Grid& g, int var, const int64_t* lg_p
     *lcb = 0;
     int ee = ext_e(h, var);
     for (int e = 0; e <= ee; ++e) {
-      RowStat rs = row_stat(h, var, e);
+      RowStat rs = h.L <= 2 ? row_stat_narrow(h, var, e) : row_stat(h, var, e);
       if (rs.max_o < 0) continue;
       *S = uf_add(*S, uf_mul(rs.l1, rs.l1));
       *m = e;
