@@ -8,10 +8,15 @@
 namespace bs {
 
 // calls body(i) for every i in [0, n); uses up to 16 threads when n >= min_parallel
+// the host's hardware threads, read once (the query reads the system's CPU list)
+inline unsigned host_threads() {
+  static const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  return hw;
+}
+
 template <class F>
 void parallel_for(int n, int min_parallel, F body) {
-  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const int threads = (n >= min_parallel) ? (int)std::min<unsigned>(16u, hw) : 1;
+  const int threads = (n >= min_parallel) ? (int)std::min<unsigned>(16u, host_threads()) : 1;
   if (threads <= 1) {
     for (int i = 0; i < n; ++i) body(i);
     return;
