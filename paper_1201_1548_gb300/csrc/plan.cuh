@@ -373,6 +373,25 @@ BS_HD int exact_prime_total(int k_need, bool lc_monomials, int table_size, IsDiv
   }
 }
 
+// upper float of the exact value hi 2^64 + lo
+BS_HD UF uf_from_u128(uint64_t hi, uint64_t lo) {
+  if (!hi) return uf_make(lo, 0, false);
+  const int sh = 64 - clz64(hi);  // keep the top 64 bits, round up by the rest
+  const uint64_t top = (hi << (64 - sh)) | (lo >> sh);
+  const bool sticky = (lo << (64 - sh)) != 0;
+  return uf_make(top, sh, sticky);
+}
+
+// |c| of a two's complement coefficient of one or two limbs
+BS_HD uint64_t mag_narrow(const uint32_t* c, int L) {
+  if (L == 1) {
+    const int64_t v = (int32_t)c[0];
+    return (uint64_t)(v < 0 ? -v : v);
+  }
+  const uint64_t raw = ((uint64_t)c[1] << 32) | c[0];
+  return (raw >> 63) ? ~raw + 1 : raw;  // |INT64_MIN| = 2^63 is representable
+}
+
 // row statistics for coefficients of at most two limbs (host): the magnitudes are summed
 // exactly in 128 bits and rounded up to an upper float once per row
 inline RowStat row_stat_narrow(const Grid& g, int var, int e) {
@@ -380,30 +399,14 @@ inline RowStat row_stat_narrow(const Grid& g, int var, int e) {
   unsigned __int128 sum = 0;
   const int eo = ext_o(g, var);
   for (int o = 0; o <= eo; ++o) {
-    const uint32_t* c = coef_ptr(g, var, e, o);
-    uint64_t mag;
-    if (g.L == 1) {
-      const int64_t v = (int32_t)c[0];
-      mag = (uint64_t)(v < 0 ? -v : v);
-    } else {
-      const uint64_t raw = ((uint64_t)c[1] << 32) | c[0];
-      mag = (raw >> 63) ? ~raw + 1 : raw;  // |INT64_MIN| = 2^63 is representable
-    }
+    const uint64_t mag = mag_narrow(coef_ptr(g, var, e, o), g.L);
     if (!mag) continue;
     sum += mag;
     s.max_o = o;
     const int bits = 64 - clz64(mag);
     if (s.min_bits == 0 || bits < s.min_bits) s.min_bits = bits;
   }
-  const uint64_t hi = (uint64_t)(sum >> 64), lo = (uint64_t)sum;
-  if (!hi) {
-    s.l1 = uf_make(lo, 0, false);
-  } else {  // keep the top 64 bits, round up by the rest
-    const int sh = 64 - clz64(hi);
-    const uint64_t top = (hi << (64 - sh)) | (lo >> sh);
-    const bool sticky = (lo << (64 - sh)) != 0;
-    s.l1 = uf_make(top, sh, sticky);
-  }
+  s.l1 = uf_from_u128((uint64_t)(sum >> 64), (uint64_t)sum);
   return s;
 }
 

@@ -140,7 +140,35 @@ __device__ void summarise_half(const Grid& h, int var, int tid, PolySummary* out
     const int e = e0 + tid / 8;
     UF l1{0u, 0};
     int mo = -1, mb = 0, cnt = 0, mbo = 0;
-    if (e <= ee) {
+    if (h.L <= 2) {
+      // narrow coefficients: exact 128-bit sums of the magnitudes, one rounding per row
+      uint64_t slo = 0, shi = 0;
+      if (e <= ee) {
+        for (int o = sub; o <= eo; o += 8) {
+          const uint64_t mag = mag_narrow(coef_ptr(h, var, e, o), h.L);
+          if (mag) {
+            slo += mag;
+            shi += (slo < mag) ? 1u : 0u;
+            mo = o;
+            ++cnt;
+            const int bits = 64 - clz64(mag);
+            if (mb == 0 || bits < mb) {
+              mb = bits;
+              mbo = o;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int x = 4; x > 0; x >>= 1) {
+        const uint64_t olo = __shfl_xor_sync(0xffffffffu, slo, x);
+        const uint64_t ohi = __shfl_xor_sync(0xffffffffu, shi, x);
+        const uint64_t nlo = slo + olo;
+        shi = shi + ohi + ((nlo < slo) ? 1u : 0u);
+        slo = nlo;
+      }
+      l1 = uf_from_u128(shi, slo);
+    } else if (e <= ee) {
       for (int o = sub; o <= eo; o += 8) {
         bool nz;
         int bits;
@@ -158,7 +186,7 @@ __device__ void summarise_half(const Grid& h, int var, int tid, PolySummary* out
     }
 #pragma unroll
     for (int x = 4; x > 0; x >>= 1) {
-      l1 = uf_add(l1, shfl_uf(l1, x));
+      if (h.L > 2) l1 = uf_add(l1, shfl_uf(l1, x));
       mo = max(mo, __shfl_xor_sync(0xffffffffu, mo, x));
       cnt += __shfl_xor_sync(0xffffffffu, cnt, x);
       const int ob = __shfl_xor_sync(0xffffffffu, mb, x);
