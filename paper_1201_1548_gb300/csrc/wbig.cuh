@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ballot.cuh"
+
 namespace bs {
 
 template <int K>
@@ -183,9 +185,13 @@ __device__ __forceinline__ uint64_t addmod64(uint64_t a, uint64_t b, uint64_t m)
 }
 
 // Residues used to reduce a warp-wide integer modulo m (2 <= m < 2^64): W = 2^(32 * 32) mod m
-// steps between the slots of one lane, P = 2^(32 * lane) mod m places the lane.
+// steps between the slots of one lane, P = 2^(32 * lane) mod m places the lane.  For
+// m < 2^63 the products by these fixed factors use Shoup's method (V. Shoup, NTL): with
+// w' = floor(w 2^64 / m), a w mod m = a w - hi(a w') m, less m at most once, which needs
+// no division; larger moduli fall back to 128-bit remainders.
 struct Mod64Pow {
-  uint64_t m = 0, W = 0, P = 0;
+  uint64_t m = 0, W = 0, P = 0, Ws = 0, Ps = 0;
+  bool shoup = false;
   __device__ void set(uint64_t mod) {
     m = mod;
     const uint64_t t32 = ((uint64_t)1 << 32) % m;  // 2^32 mod m
@@ -199,19 +205,173 @@ struct Mod64Pow {
       b = mulmod64(b, b, m);
     }
     P = pl;
+    shoup = m < ((uint64_t)1 << 63);
+    if (shoup) {
+      Ws = (uint64_t)(((unsigned __int128)W << 64) / m);
+      Ps = (uint64_t)(((unsigned __int128)P << 64) / m);
+    }
+  }
+  // a w mod m for the fixed factor w (ws its Shoup companion)
+  __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t w, uint64_t ws) const {
+    if (!shoup) return mulmod64(a % m, w, m);
+    const uint64_t q = __umul64hi(a, ws);
+    const uint64_t r = a * w - q * m;  // in [0, 2m) < 2^64
+    return r >= m ? r - m : r;
   }
 };
 
-// a mod m for a warp-wide non-negative integer (every lane receives the result)
 template <int K>
 __device__ __forceinline__ uint64_t wb_mod64(const WBig<K>& a, const Mod64Pow& mp) {
+  const bool wide = mp.m > 0xffffffffull;  // every limb is already below m
   uint64_t acc = 0;
 #pragma unroll
-  for (int s = K - 1; s >= 0; --s) acc = addmod64(mulmod64(acc, mp.W, mp.m), a.v[s] % mp.m, mp.m);
-  acc = mulmod64(acc, mp.P, mp.m);
+  for (int s = K - 1; s >= 0; --s) {
+    const uint64_t limb = wide ? a.v[s] : (uint64_t)(a.v[s] % (uint32_t)mp.m);
+    acc = addmod64(mp.mul(acc, mp.W, mp.Ws), limb, mp.m);
+  }
+  acc = mp.mul(acc, mp.P, mp.Ps);
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc = addmod64(acc, __shfl_xor_sync(0xffffffffu, acc, o), mp.m);
   return acc;
+}
+
+// limb l of a (0 beyond the number's 32 K limbs), on every lane
+template <int K>
+__device__ __forceinline__ uint32_t wb_limb(const WBig<K>& a, int l) {
+  uint32_t x = 0;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const uint32_t y = __shfl_sync(0xffffffffu, a.v[s], l & 31);
+    if ((l >> 5) == s) x = y;
+  }
+  return x;
+}
+
+// bit length (0 for zero)
+template <int K>
+__device__ __forceinline__ int wb_bits(const WBig<K>& a) {
+  const int top = wb_top<K>(a);
+  if (top < 0) return 0;
+  return 32 * top + 32 - __clz((int)wb_limb<K>(a, top));
+}
+
+// 31 bits of a starting at bit s >= 0
+template <int K>
+__device__ __forceinline__ uint32_t wb_bits31(const WBig<K>& a, int s) {
+  const int l = s >> 5, r = s & 31;
+  const uint32_t lo = wb_limb<K>(a, l), hi = wb_limb<K>(a, l + 1);
+  const uint32_t w = r ? (lo >> r) | (hi << (32 - r)) : lo;
+  return w & 0x7fffffffu;
+}
+
+// x * s for a 32-bit s; the product must fit in 32 K limbs
+template <int K>
+__device__ __forceinline__ void wb_mul_small(const WBig<K>& x, uint32_t s, WBig<K>& out) {
+  const int lane = threadIdx.x & 31;
+  uint32_t cin = 0, hprev = 0;  // carry into the chunk; high word of the limb below the chunk
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const uint64_t p = (uint64_t)x.v[t] * s;
+    const uint32_t lo = (uint32_t)p, hi = (uint32_t)(p >> 32);
+    uint32_t hin = __shfl_up_sync(0xffffffffu, hi, 1);
+    const uint32_t h31 = __shfl_sync(0xffffffffu, hi, 31);
+    if (lane == 0) hin = hprev;
+    hprev = h31;
+    out.v[t] = ballot_add(lo, hin, cin, lane);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void wb_strip2(WBig<K>& a) {
+  if (!wb_is_zero<K>(a)) wb_shr<K>(a, wb_ctz<K>(a));
+}
+
+// gcd of odd u and v (in place in u).  Lehmer's method on the leading 31 bits (Knuth,
+// TAOCP vol. 2, Algorithm 4.5.2L): single-precision Euclid steps on the leading words
+// give a cofactor matrix whose quotients are the true ones while both tests agree; it is
+// applied to the full numbers as |A| u - |B| v or |B| v - |A| u (the cofactors of a row
+// have opposite signs or one of them is zero; the sign of the second decides).  Factors of two are stripped after every step (the gcd is odd).  A round that
+// makes no progress takes one binary step (Stein) instead; once v fits in 64 bits the gcd
+// finishes in 64-bit arithmetic.
+template <int K>
+__device__ void wb_gcd_odd(WBig<K>& u, WBig<K>& v) {
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < (1 << 22); ++it) {  // every round removes at least one bit
+    if (wb_gt<K>(v, u)) {
+      const WBig<K> t = u;
+      u = v;
+      v = t;
+    }
+    if (wb_is_zero<K>(v)) return;
+    const int nu = wb_bits<K>(u), nv = wb_bits<K>(v);
+    if (nv <= 64) {  // u mod v and the rest in 64-bit arithmetic
+      const uint64_t m = (uint64_t)wb_limb<K>(v, 0) | ((uint64_t)wb_limb<K>(v, 1) << 32);
+      uint64_t g = 1;
+      if (m > 1) {
+        Mod64Pow mp;
+        mp.set(m);
+        g = gcd64(m, wb_mod64<K>(u, mp));
+      }
+#pragma unroll
+      for (int s = 0; s < K; ++s) u.v[s] = (s == 0 && lane == 0) ? (uint32_t)g : (s == 0 && lane == 1) ? (uint32_t)(g >> 32) : 0u;
+      return;
+    }
+    bool stepped = false;
+    if (nu - nv < 31 && nu + 31 <= 32 * 32 * K) {
+      const int sh = nu - 31;
+      int64_t x = wb_bits31<K>(u, sh), y = wb_bits31<K>(v, sh);
+      int64_t A = 1, B = 0, C = 0, D = 1;
+      for (int k = 0; k < 64; ++k) {
+        if (y + C == 0 || y + D == 0) break;
+        const int64_t q = (x + A) / (y + C), q2 = (x + B) / (y + D);
+        if (q != q2) break;
+        int64_t t = A - q * C;
+        A = C;
+        C = t;
+        t = B - q * D;
+        B = D;
+        D = t;
+        t = x - q * y;
+        x = y;
+        y = t;
+      }
+      if (B != 0) {
+        WBig<K> X, Y, nu2, nv2;
+        wb_mul_small<K>(u, (uint32_t)(A < 0 ? -A : A), X);
+        wb_mul_small<K>(v, (uint32_t)(B < 0 ? -B : B), Y);
+        if (B <= 0) {  // A >= 0 >= B (A may be 0 only with B > 0)
+          nu2 = X;
+          wb_sub<K>(nu2, Y);
+        } else {
+          nu2 = Y;
+          wb_sub<K>(nu2, X);
+        }
+        wb_mul_small<K>(u, (uint32_t)(C < 0 ? -C : C), X);
+        wb_mul_small<K>(v, (uint32_t)(D < 0 ? -D : D), Y);
+        if (D <= 0) {
+          nv2 = X;
+          wb_sub<K>(nv2, Y);
+        } else {
+          nv2 = Y;
+          wb_sub<K>(nv2, X);
+        }
+        u = nu2;
+        v = nv2;
+        wb_strip2<K>(u);
+        wb_strip2<K>(v);
+        if (wb_is_zero<K>(v)) return;  // u is the gcd
+        if (wb_is_zero<K>(u)) {
+          u = v;
+          return;
+        }
+        stepped = true;
+      }
+    }
+    if (!stepped) {  // binary step: u - v is even and nonzero (u > v, both odd)
+      wb_sub<K>(u, v);
+      wb_strip2<K>(u);
+    }
+  }
 }
 
 // Running gcd of integers, held by one warp.  g = 0 stands for "no coefficient yet".
@@ -231,39 +391,21 @@ struct ContentAcc {
 
   // fold the n coefficients c[i * L .. i * L + L - 1] into the gcd
   __device__ void fold(const uint32_t* c, int n, int L) {
-    for (int i = 0; i < n; ++i) {
-      const uint32_t* ci = c + (int64_t)i * L;
-      if (small && g64 == 1u) return;
+    int i = 0;
+    for (; i < n && !small; ++i) {  // warp-wide gcds until the gcd fits in 64 bits
       WBig<K> b;
-      wb_load_abs<K>(b, ci, L);
+      wb_load_abs<K>(b, c + (int64_t)i * L, L);
       if (wb_is_zero<K>(b)) continue;
-      if (small) {
-        const uint64_t r = wb_mod64<K>(b, mp);
-        const uint64_t ng = gcd64(g64, r);
-        if (ng != g64) {
-          g64 = ng;
-          if (g64 > 1) mp.set(g64);
-        }
-        continue;
-      }
       if (!started) {
         g = b;
         started = true;
       } else {
-        // Stein's binary gcd of g and b
+        // gcd of the odd parts, times the common power of two
         const int tg = wb_ctz<K>(g), tb = wb_ctz<K>(b);
         const int sh = tg < tb ? tg : tb;
         wb_shr<K>(g, tg);
-        for (int it = 0; it < (1 << 20); ++it) {  // each pass removes at least one bit
-          wb_shr<K>(b, wb_ctz<K>(b));
-          if (wb_gt<K>(g, b)) {
-            const WBig<K> t = g;
-            g = b;
-            b = t;
-          }
-          wb_sub<K>(b, g);
-          if (wb_is_zero<K>(b)) break;
-        }
+        wb_shr<K>(b, tb);
+        wb_gcd_odd<K>(g, b);
         wb_shl<K>(g, sh);
       }
       if (wb_top<K>(g) <= 1) {
@@ -273,6 +415,25 @@ struct ContentAcc {
         g64 = lo | (hi << 32);
         if (g64 > 1) mp.set(g64);
       }
+    }
+    // four coefficients at a time, their loads and reductions in flight together; a
+    // residue modulo the gcd before an update still gives the right gcd after it (the new
+    // gcd divides the old one)
+    constexpr int B4 = K <= 4 ? 4 : 2;
+    for (; i < n; i += B4) {
+      if (g64 == 1u) return;
+      WBig<K> b[B4];
+#pragma unroll
+      for (int j = 0; j < B4; ++j)
+        if (i + j < n) wb_load_abs<K>(b[j], c + (int64_t)(i + j) * L, L);
+      uint64_t r[B4];
+#pragma unroll
+      for (int j = 0; j < B4; ++j) r[j] = (i + j < n) ? wb_mod64<K>(b[j], mp) : 0u;
+      const uint64_t g0 = g64;
+#pragma unroll
+      for (int j = 0; j < B4; ++j)
+        if (r[j]) g64 = gcd64(g64, r[j]);
+      if (g64 != g0 && g64 > 1) mp.set(g64);
     }
   }
 
