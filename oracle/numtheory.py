@@ -3,9 +3,8 @@
 The prime table follows this definition (the same one the CUDA planner implements on
 its own): all primes p with 2**30 < p < 2**31 and p = 1 (mod 2**14), in decreasing
 order.  The paper fixes neither the prime size nor the evaluation points (Sec. 5.1,
-step (a) "sufficiently many primes", step (b) "choose a set of points"); 31-bit primes
-with a 2**14-th root of unity let every prime carry an evaluation set of up to 16384
-points that is a coset of the roots of unity.
+steps (a) and (b) leave both open); 31-bit primes with a 2**14-th root of unity let every
+prime carry an evaluation set of up to 16384 points that is a coset of the roots of unity.
 """
 
 from __future__ import annotations
