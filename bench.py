@@ -627,9 +627,15 @@ def run_ours(args):
 
     batched = served = projection = None
     if rank == 0 and not args.no_extras:
-        batched = _bench_batched(bs, ctx)
-        served = _bench_served(bs)
-        projection = _bench_projection(bs, ctx, f, g, ctx.resultant(f, g))
+        # the extra measurements never cost the headline line: a failure is reported in it
+        def extra(fn):
+            try:
+                return fn()
+            except (Exception, SystemExit) as e:  # noqa: BLE001
+                return {"error": f"{type(e).__name__}: {e}"}
+        batched = extra(lambda: _bench_batched(bs, ctx))
+        served = extra(lambda: _bench_served(bs))
+        projection = extra(lambda: _bench_projection(bs, ctx, f, g, ctx.resultant(f, g)))
 
     cpu = None
     if want_cpu:
