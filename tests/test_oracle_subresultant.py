@@ -36,6 +36,44 @@ def test_hand_expanded_examples():
     assert S.psc_univariate(a, b)[1] == want
 
 
+def test_psc_from_roots():
+    # Sylvester's single sum (proved by D'Andrea, Hong, Krick and Szanto, 2007): for
+    # a = a_m prod (y - alpha_i) with distinct alpha_i and b = b_n prod (y - beta_j),
+    # sr_k = (-1)^(k(m-k)) a_m^(n-k) b_n^(m-k) sum over k-subsets A' of the alphas of
+    # R(alpha \ A', beta) / R(A', alpha \ A'), with R(U, V) = prod (u - v); k = 0 is the
+    # classical root product of the resultant.  No determinant is involved.
+    import itertools
+    from fractions import Fraction
+
+    def rprod(U, V):
+        out = 1
+        for u in U:
+            for v in V:
+                out *= u - v
+        return out
+
+    rng = random.Random(17)
+    for _ in range(150):
+        m, n = rng.randrange(1, 6), rng.randrange(1, 6)
+        alpha = rng.sample(range(-9, 10), m)
+        beta = [rng.randrange(-9, 10) for _ in range(n)]
+        am, bn = rng.choice([1, -2, 3]), rng.choice([1, 2, -3])
+        a, b = [am], [bn]
+        for r in alpha:
+            a = P.mul(a, [-r, 1])
+        for r in beta:
+            b = P.mul(b, [-r, 1])
+        sr = S.psc_univariate(a, b)
+        assert len(sr) == min(m, n)
+        for k in range(min(m, n)):
+            s = Fraction(0)
+            for sub in itertools.combinations(range(m), k):
+                A1 = [alpha[i] for i in sub]
+                A2 = [alpha[i] for i in range(m) if i not in sub]
+                s += Fraction(rprod(A2, beta), rprod(A1, A2))
+            assert sr[k] == (-1) ** (k * (m - k)) * am ** (n - k) * bn ** (m - k) * s, (m, n, k)
+
+
 def test_sr0_is_the_resultant():
     rng = random.Random(11)
     for _ in range(20):
