@@ -13,7 +13,13 @@
  *     step (b));
  *   - the square-free part of a polynomial in Z[x] and its full square-free
  *     factorisation by Yun's algorithm (Sec. 2.1, BiProject), and the gcd in Z[x], all
- *     by the modular route of Sec. 5.1 ("Computing gcds in Z[x]").
+ *     by the modular route of Sec. 5.1 ("Computing gcds in Z[x]");
+ *   - the principal subresultant coefficients of two bivariate polynomials, exact or
+ *     modulo one prime, and on them the fiber counts of Sec. 3.3 (the number N of curve
+ *     points over the critical values, its bounds N^- and N^+), Teissier's Q and the split
+ *     of R* by the multiplicity of Q at its roots;
+ *   - the content of a bivariate polynomial with respect to one variable and its
+ *     primitive part (Sec. 4: vertical lines).
  *
  * Integer encoding.  Every integer coefficient is a fixed number of little-endian
  * uint32 limbs in two's complement (limb 0 is the least significant; the sign is the
@@ -361,6 +367,26 @@ int bs_content(bs_ctx *ctx, const bs_bipoly *f, int var, bs_upoly *h, int cap_ro
  * Q: caller-owned output in the layout of bs_squarefree_part; Q->c == NULL is a size query
  * (it computes the sequence).  Errors as for bs_psc, BS_ERR_ZERO for f = 0. */
 int bs_teissier_q(bs_ctx *ctx, const bs_bipoly *f, int var, bs_upoly *Q, int32_t *d);
+
+/* The square-free part R* of a non-zero R in Z[x] split by the multiplicity of a non-zero
+ * Q at its roots (Sec. 3.3: Teissier's test weighs mult(R, alpha) against mult(Q, alpha) at
+ * the critical values alpha, Q as returned by bs_teissier_q): the primitive, pairwise
+ * coprime c_0, c_1, ..., c_t with positive leading coefficients and R* = c_0 c_1 ... c_t,
+ * where c_k(alpha) = 0 exactly for the roots alpha of R with mult(Q, alpha) = k; c_t is
+ * not constant unless t = 0, and a multiplicity below t that no root has gives c_k = 1.
+ * With Yun's factorisation Q = c q_1 q_2^2 ... q_s^s (bs_squarefree_factorization),
+ * c_k = gcd(R*, q_k) for k >= 1 and c_0 = R* / gcd(R*, Q*), Q* the square-free part of Q;
+ * the square-free parts, the factorisation, the gcds and the quotient run on the device by
+ * the modular route (four passes of launches).
+ * r, q: host buffers in the layout of bs_squarefree_part.
+ * out, fdeg, nfac: as for bs_squarefree_factorization, with c_0, ..., c_t packed one after
+ * the other, fdeg[k] = deg c_k (cap_factors entries available) and *nfac = t + 1.  With
+ * out->c == NULL the call only writes upper bounds (out->deg = deg R + deg Q, out->limbs,
+ * *nfac = deg Q + 1 as the factor capacity) and returns BS_OK.
+ * Errors: BS_ERR_ARG, BS_ERR_ZERO (R = 0 or Q = 0), BS_ERR_CAPACITY, BS_ERR_RANGE and
+ * BS_ERR_UNLUCKY as for bs_squarefree_factorization and bs_gcd_z. */
+int bs_root_multiplicity(bs_ctx *ctx, const bs_upoly *r, const bs_upoly *q, int cap_factors,
+                         int32_t *fdeg, int32_t *nfac, bs_upoly *out);
 
 /* Launch shapes of the batched stages (bs_autotune_batch). */
 typedef struct {

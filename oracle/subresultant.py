@@ -19,6 +19,10 @@ Test infrastructure only: plain, slow, exact.
 * Teissier's Q = res(f_x*, f_y*; y) with f_x*, f_y* the cofactors of h = gcd(f_x, f_y) in
   Z[x, y] (the primitive pseudo-remainder sequence), and the upper bound
   N^+ = deg R* n_y - deg R + deg gcd(R^inf mod p, Q mod p) (Sec. 3.3).
+* mult(Q, alpha) at the roots alpha of R (the quantity Teissier's test of Sec. 3.3 sets
+  against mult(R, alpha)): over Q, Q and its first k - 1 derivatives vanish at alpha
+  exactly when mult(Q, alpha) >= k, so G_1 = gcd(R*, Q), G_(k+1) = gcd(G_k, Q^(k)) holds
+  the roots of multiplicity at least k and c_k = G_k / G_(k+1) those of multiplicity k.
 """
 
 from __future__ import annotations
@@ -309,3 +313,30 @@ def fiber_upper_bound_modp(f, p):
         dQ = P.mod_p(P.derivative(dQ), p)
         T = G.gcd_modp(T, dQ, p)
     return P.deg(Rs) * n_y - P.deg(Rr) + total
+
+
+def multiplicity_split(r, q):
+    """[c_0, c_1, ..., c_t] with R* = c_0 c_1 ... c_t, c_k the primitive factor (positive
+    leading coefficient) vanishing exactly at the roots alpha of R with mult(Q, alpha) = k;
+    c_t is not constant unless t = 0.  R and Q must be non-zero."""
+    rs = G.squarefree_part(r)
+    q = P.trim(q)
+    if not q:
+        raise ValueError("Q = 0")
+    chain = [rs]                      # G_0 = R*, G_1, G_2, ...
+    dq = q
+    while P.deg(chain[-1]) > 0:
+        g = G.gcd_z(chain[-1], dq)
+        g = P.primitive_part(g) if P.deg(g) > 0 else [1]
+        if g[-1] < 0:
+            g = P.scale(g, -1)
+        chain.append(g)
+        if not dq:
+            break
+        dq = P.derivative(dq)
+    out = [P.exact_div_z(chain[k], chain[k + 1]) for k in range(len(chain) - 1)]
+    out = [P.primitive_part(c) if P.deg(c) > 0 else [1] for c in out]
+    out = [P.scale(c, -1) if c[-1] < 0 else c for c in out]
+    while len(out) > 1 and P.deg(out[-1]) <= 0:
+        out.pop()
+    return out or [[1]]

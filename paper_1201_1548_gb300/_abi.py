@@ -20,7 +20,7 @@ EXPORTED_SYMBOLS = [
     "bs_stage_times", "bs_resultant_device_noalloc", "bs_gcd_z", "bs_modgcd_batch",
     "bs_autotune_batch", "bs_set_tune", "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
     "bs_squarefree_factorization", "bs_squarefree_factorization_batch", "bs_psc",
-    "bs_psc_modp", "bs_fiber_count", "bs_content", "bs_teissier_q",
+    "bs_psc_modp", "bs_fiber_count", "bs_content", "bs_teissier_q", "bs_root_multiplicity",
 ]
 
 
@@ -138,6 +138,8 @@ def load_library():
                                 C.POINTER(C.c_int32), P, P, C.POINTER(C.c_uint32)]
     lib.bs_content.argtypes = [P, C.POINTER(_Bipoly), I, C.POINTER(_Upoly), I, P, C.POINTER(C.c_int32)]
     lib.bs_teissier_q.argtypes = [P, C.POINTER(_Bipoly), I, C.POINTER(_Upoly), C.POINTER(C.c_int32)]
+    lib.bs_root_multiplicity.argtypes = [P, C.POINTER(_Upoly), C.POINTER(_Upoly), I, P, P,
+                                         C.POINTER(_Upoly)]
     lib.bs_fiber_count.argtypes = [P, C.POINTER(_Bipoly), I, I, I, P, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int64), C.POINTER(C.c_uint32)]
     lib.bs_serve_start.argtypes = [P, I, I, C.c_size_t]
@@ -325,6 +327,31 @@ class Context:
         self._check(self.lib.bs_teissier_q(self.h, C.byref(fb), int(var), C.byref(q), C.byref(d)))
         return (limbs_to_ints(buf, q.deg + 1, q.limbs) if q.deg >= 0 else []), int(d.value)
 
+    def root_multiplicity(self, r, q):
+        """[c_0, c_1, ..., c_t]: the square-free part of the ascending integer list r split
+        by the multiplicity of q at its roots (c_k vanishes exactly where q has multiplicity
+        k), each primitive with a positive leading coefficient."""
+        ar, Lr = ints_to_limbs(r)
+        aq, Lq = ints_to_limbs(q)
+        rb = _Upoly(len(r) - 1, Lr, ar.ctypes.data)
+        qb = _Upoly(len(q) - 1, Lq, aq.ctypes.data)
+        out, nfac = _Upoly(0, 0, None), C.c_int32(0)
+        self._check(self.lib.bs_root_multiplicity(self.h, C.byref(rb), C.byref(qb), 0, None,
+                                                  C.addressof(nfac), C.byref(out)))
+        cap = max(int(nfac.value), 1)
+        fdeg = np.zeros(cap, dtype=np.int32)
+        buf = np.zeros((out.deg + 1) * out.limbs, dtype=np.uint32)
+        out = _Upoly(out.deg, out.limbs, buf.ctypes.data)
+        self._check(self.lib.bs_root_multiplicity(self.h, C.byref(rb), C.byref(qb), cap,
+                                                  fdeg.ctypes.data, C.addressof(nfac),
+                                                  C.byref(out)))
+        coefs = limbs_to_ints(buf, out.deg + 1, out.limbs)
+        facs, pos = [], 0
+        for d in fdeg[: int(nfac.value)]:
+            facs.append(coefs[pos: pos + int(d) + 1])
+            pos += int(d) + 1
+        return facs
+
     def fiber_count(self, f, var=1, mode=0):
         """(degs, N, p): deg R_1, deg R_2, ... of the decomposition of R* by fibers, the point
         count N (mode 0, exact), its lower bound N^- (mode 1) or upper bound N^+ (mode 2, no
@@ -441,14 +468,15 @@ class Context:
         return self.modgcd_batch([(0, a, b)])[0]
 
     def modgcd_batch(self, jobs):
-        """jobs: list of (kind, a, b); kind 0 gcd(a, b), kind 1 square-free part of a."""
+        """jobs: list of (kind, a, b); kind 0 gcd(a, b), kind 1 square-free part of a (b
+        unused), kind 2 the exact quotient a / b (b must divide a in Z[x])."""
         n = len(jobs)
         kinds = (C.c_int * n)(*[int(k) for k, _, _ in jobs])
         keep = []
         A = (_Upoly * n)()
         Bv = (_Upoly * n)()
         for j, (k, a, b) in enumerate(jobs):
-            for arr_list, poly in ((A, a), (Bv, b if k == 0 else [])):
+            for arr_list, poly in ((A, a), (Bv, b if k != 1 else [])):
                 arr, L = ints_to_limbs(poly)
                 keep.append(arr)
                 arr_list[j] = _Upoly(len(poly) - 1, L, arr.ctypes.data)

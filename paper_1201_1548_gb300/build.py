@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbsres.so")
 
-SOURCES = ["resultant_kernels.cu", "tables.cu", "launch.cu", "api.cu", "gcd.cu", "modgcd.cu", "probe.cu", "noalloc.cu", "serve.cu", "bigcrt.cu", "yun.cu", "psc.cu", "fiber.cu", "content.cu"]
+SOURCES = ["resultant_kernels.cu", "tables.cu", "launch.cu", "api.cu", "gcd.cu", "modgcd.cu", "probe.cu", "noalloc.cu", "serve.cu", "bigcrt.cu", "yun.cu", "psc.cu", "fiber.cu", "content.cu", "mult.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -13,34 +13,9 @@
 
 #include "ctx.cuh"
 #include "modpoly.cuh"
+#include "owned.cuh"
 
 namespace bs {
-
-struct OwnedPoly {
-  std::vector<uint32_t> c;
-  bs_upoly u{-1, 1, nullptr};
-};
-
-// bs_modgcd_batch with owned outputs: a size query, then the computation
-static int modgcd_owned(bs_ctx* ctx, const std::vector<int>& kind, const std::vector<bs_upoly>& a,
-                        const std::vector<bs_upoly>& b, std::vector<OwnedPoly>* out) {
-  const int n = (int)kind.size();
-  out->assign(n, OwnedPoly{});
-  std::vector<bs_upoly> o(n, bs_upoly{0, 0, nullptr});
-  int rc = bs_modgcd_batch(ctx, n, kind.data(), a.data(), b.data(), o.data());
-  if (rc) return rc;
-  for (int j = 0; j < n; ++j) {
-    OwnedPoly& p = (*out)[j];
-    p.c.assign((size_t)(std::max(o[j].deg, 0) + 1) * std::max(o[j].limbs, 1), 0u);
-    o[j].deg = std::max(o[j].deg, 0);
-    o[j].limbs = std::max(o[j].limbs, 1);
-    o[j].c = p.c.data();
-  }
-  rc = bs_modgcd_batch(ctx, n, kind.data(), a.data(), b.data(), o.data());
-  if (rc) return rc;
-  for (int j = 0; j < n; ++j) (*out)[j].u = o[j];
-  return BS_OK;
-}
 
 static int run_content(bs_ctx* ctx, const bs_bipoly* f, int var, bs_upoly* h, int cap_rows, bs_upoly* rows,
                        int32_t* nrows) {
@@ -91,10 +66,10 @@ static int run_content(bs_ctx* ctx, const bs_bipoly* f, int var, bs_upoly* h, in
   // gcd of the nonzero rows, a pairwise tree of batched gcds
   std::vector<bs_upoly> cur;
   for (int e : nz) cur.push_back(row[e]);
-  std::vector<OwnedPoly> keep;
+  std::vector<HostPoly> keep;
   int rc;
   if (cur.size() == 1) {  // one row: gcd(row, 0) normalises its sign
-    std::vector<OwnedPoly> o;
+    std::vector<HostPoly> o;
     rc = modgcd_owned(ctx, {0}, {cur[0]}, {bs_upoly{-1, 1, nullptr}}, &o);
     if (rc) return rc;
     keep = std::move(o);
@@ -108,7 +83,7 @@ static int run_content(bs_ctx* ctx, const bs_bipoly* f, int var, bs_upoly* h, in
       a.push_back(cur[i]);
       b.push_back(cur[i + 1]);
     }
-    std::vector<OwnedPoly> o;
+    std::vector<HostPoly> o;
     rc = modgcd_owned(ctx, kind, a, b, &o);
     if (rc) return rc;
     std::vector<bs_upoly> next;
@@ -129,7 +104,7 @@ static int run_content(bs_ctx* ctx, const bs_bipoly* f, int var, bs_upoly* h, in
     while (d >= 0 && limbs_zero(a[e].c + (size_t)d * L, L)) --d;
     a[e].deg = d;
   }
-  std::vector<OwnedPoly> q;
+  std::vector<HostPoly> q;
   rc = modgcd_owned(ctx, kind, a, b, &q);
   if (rc) return rc;
   for (int e = 0; e <= top; ++e) {

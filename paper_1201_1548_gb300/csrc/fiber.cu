@@ -23,6 +23,7 @@
 
 #include "ctx.cuh"
 #include "modpoly.cuh"
+#include "owned.cuh"
 
 namespace bs {
 
@@ -71,25 +72,6 @@ static int lead_degree(const bs_bipoly& f, int var, bool* constant_lc) {
   }
   *constant_lc = true;
   return -1;
-}
-
-// an integer polynomial as a host buffer
-struct HostPoly {
-  std::vector<uint32_t> c;
-  bs_upoly u{-1, 1, nullptr};
-};
-
-// call a bs_upoly-producing entry point twice: size query, then the computation
-template <class F>
-static int fetch(HostPoly* h, F&& call) {
-  h->u = bs_upoly{0, 0, nullptr};
-  int rc = call(&h->u);
-  if (rc) return rc;
-  h->c.assign((size_t)(std::max(h->u.deg, 0) + 1) * std::max(h->u.limbs, 1), 0u);
-  h->u.limbs = std::max(h->u.limbs, 1);
-  h->u.deg = std::max(h->u.deg, 0);
-  h->u.c = h->c.data();
-  return call(&h->u);
 }
 
 static uint32_t residue_of(const uint32_t* c, int L, uint32_t p) {

@@ -160,3 +160,69 @@ def test_fiber_upper_bound_dense(ctx):
         f = dense_curve(rng, 3 + t % 2, 10)
         _, ub, p = ctx.fiber_count(f, mode=2)
         assert ub == S.fiber_upper_bound_modp(f, p), t
+
+
+def _from_roots(lc, roots):
+    from oracle import poly as P
+    a = [lc]
+    for r in roots:
+        a = P.mul(a, [-r, 1])
+    return a
+
+
+def test_root_multiplicity_split_polynomials(ctx):
+    import random
+    from oracle import poly as P
+    rng = random.Random(67)
+    for t in range(12):
+        ra = rng.sample(range(-30, 31), rng.randrange(1, 9))
+        rroots = ra + [rng.choice(ra) for _ in range(rng.randrange(0, 3))]
+        qroots = [rng.choice(ra) if rng.random() < 0.6 else rng.randrange(-30, 31)
+                  for _ in range(rng.randrange(1, 12))]
+        r = _from_roots(rng.choice([1, -3, 7]), rroots)
+        q = P.mul(_from_roots(rng.choice([1, 2, -5]), qroots), [rng.randrange(1, 9), 0, 1])
+        assert ctx.root_multiplicity(r, q) == S.multiplicity_split(r, q), t
+
+
+def test_root_multiplicity_random_factors(ctx):
+    # dense factors with wide coefficients: R = u v w (square-free in general), Q = u^3 v z
+    from oracle import poly as P
+    from workloads import random_univariate
+    rng = _rng(68)
+    for t in range(4):
+        u, v, w, z = (random_univariate(rng, int(rng.integers(2, 7)), int(rng.integers(8, 70)))
+                      for _ in range(4))
+        r = P.mul(P.mul(u, v), w)
+        q = P.mul(P.mul(P.mul(P.mul(u, u), u), v), z)
+        got = ctx.root_multiplicity(r, q)
+        assert got == S.multiplicity_split(r, q), t
+        assert len(got) >= 4 and P.deg(got[3]) > 0, t       # the roots of u: multiplicity 3
+
+
+def test_root_multiplicity_of_teissier_q(ctx):
+    # the use of Sec. 3.3: R = res(f, f_y) and Teissier's Q of curves with singular points
+    from oracle import resultant as Rm
+    import random
+    rng = random.Random(69)
+    cases = [S.split_curve(b) for b in SPLIT[:3]]
+    for _ in range(2):
+        pc = [rng.randrange(-4, 5) or 1 for _ in range(rng.randrange(2, 4))]
+        kc = [rng.randrange(-4, 5) or 1 for _ in range(rng.randrange(2, 4))]
+        Pp, add, mul = _compose(pc, 1, 1)
+        Kk, _, _ = _compose(kc, 1, -1)
+        cases.append(_grid(add(mul(mul(Pp, Pp), Kk), [[rng.randrange(1, 9)]])))
+    for t, f in enumerate(cases):
+        Rr = Rm.res_y(f, S.d_dy(f))
+        Q, _ = S.teissier_q(f)
+        assert ctx.root_multiplicity(Rr, Q) == S.multiplicity_split(Rr, Q), t
+
+
+def test_root_multiplicity_edge_cases(ctx):
+    assert ctx.root_multiplicity([-6, 1, 1], [5]) == [[-6, 1, 1]]          # Q constant
+    assert ctx.root_multiplicity([7], [1, 2, 1]) == [[1]]                   # R constant
+    # R = 4 x^2 (R* = x), Q = x^3: the one root has multiplicity 3 in Q
+    assert ctx.root_multiplicity([0, 0, 4], [0, 0, 0, 1]) == [[1], [1], [1], [0, 1]]
+    for r, q in (([], [1, 1]), ([1, 1], []), ([0, 0], [1, 1])):
+        with pytest.raises(bs.BsError) as e:
+            ctx.root_multiplicity(r, q)
+        assert e.value.code == bs.BS_ERR_ZERO

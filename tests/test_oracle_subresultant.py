@@ -264,3 +264,62 @@ def test_fiber_bounds_bracket_N():
         ub = S.fiber_upper_bound_modp(f, p)
         assert lb <= N <= ub
         assert ub == N          # lines in general position: f_x*, f_y* meet only on C
+
+
+def _from_roots(lc, roots):
+    a = [lc]
+    for r in roots:
+        a = P.mul(a, [-r, 1])
+    return a
+
+
+def test_multiplicity_split_by_counting_roots():
+    # R and Q split over Z (plus an irreducible quadratic in Q): mult(Q, a) is the number
+    # of times a appears among Q's roots, so c_k is the product of x - a over R's distinct
+    # roots a that appear exactly k times
+    rng = random.Random(21)
+    for _ in range(60):
+        ra = rng.sample(range(-8, 9), rng.randrange(1, 6))
+        rroots = ra + [rng.choice(ra) for _ in range(rng.randrange(0, 3))]   # repeated roots
+        qroots = [rng.randrange(-8, 9) for _ in range(rng.randrange(0, 7))]
+        r = _from_roots(rng.choice([1, -3, 4]), rroots)
+        q = P.mul(_from_roots(rng.choice([1, 2, -5]), qroots), [rng.randrange(1, 5), 0, 1])
+        mult = {a: qroots.count(a) for a in ra}
+        t = max(mult.values())
+        want = [_from_roots(1, sorted(a for a in ra if mult[a] == k)) for k in range(t + 1)]
+        assert S.multiplicity_split(r, q) == want, (rroots, qroots)
+
+
+def test_multiplicity_split_against_sympy_factors():
+    # a third route: the irreducible factors of R over Q (sympy), each weighed by how many
+    # times it divides Q
+    sympy = pytest.importorskip("sympy")
+    x = sympy.symbols("x")
+    rng = random.Random(22)
+
+    def expr(c):
+        return sum(int(v) * x ** i for i, v in enumerate(c))
+
+    for _ in range(12):
+        u = _rand(rng, rng.randrange(1, 3), -6, 6)
+        v = _rand(rng, rng.randrange(1, 3), -6, 6)
+        w = _rand(rng, rng.randrange(1, 3), -6, 6)
+        r = P.mul(P.mul(u, v), w)
+        q = P.mul(P.mul(P.mul(u, u), v), _rand(rng, 2, -6, 6))
+        groups = {}
+        for fac, _ in sympy.factor_list(expr(r))[1]:
+            k, rest = 0, sympy.Poly(expr(q), x)
+            fp = sympy.Poly(fac, x)
+            while True:
+                qq, rem = sympy.div(rest, fp)
+                if not rem.is_zero:
+                    break
+                k, rest = k + 1, qq
+            groups.setdefault(k, []).append(fac)
+        t = max(groups)
+        want = []
+        for k in range(t + 1):
+            c = sympy.Poly(sympy.Mul(*groups.get(k, [])), x)
+            coeffs = [int(a) for a in reversed(c.all_coeffs())]
+            want.append(P.scale(coeffs, -1) if coeffs[-1] < 0 else coeffs)
+        assert S.multiplicity_split(r, q) == want
