@@ -193,39 +193,36 @@ __global__ void k_mg_gather(const MgJob* jobs, int n, Tables T, int second) {
   }
 }
 
-// ---- contents: one warp per job ---------------------------------------------------------
+// ---- contents: one block per job, its warps splitting the coefficients -----------------
 template <int K>
-__device__ void mg_content_job(const MgJob& J) {
+__device__ void mg_content_job(const MgJob& J, uint32_t* part) {
   if (J.info[3] != 0) return;
   if (J.kind == kMgDiv) {  // the quotient is the result as it is
-    for (int l = threadIdx.x & 31; l < J.Lc; l += 32) J.content[l] = J.cmul[l] = (l == 0) ? 1u : 0u;
+    for (int l = threadIdx.x; l < J.Lc; l += blockDim.x) J.content[l] = J.cmul[l] = (l == 0) ? 1u : 0u;
     return;
   }
   const int dh = J.info[0];
-  ContentAcc<K> h;
-  h.fold(J.crt[0].out, dh + 1, J.Lc);
-  h.store(J.content, J.Lc);
-  if (J.kind == kMgGcd) {
-    ContentAcc<K> m;
-    m.fold(J.A, J.da + 1, J.La);
-    if (!m.is_one()) m.fold(J.B, J.db + 1, J.Lb);
-    m.store(J.cmul, J.Lc);
+  block_content<K>(J.crt[0].out, dh + 1, J.Lc, nullptr, 0, 1, part, J.Lc, J.content, J.Lc);
+  if (J.kind == kMgGcd) {  // gcd(cont a, cont b) = cont gcd(a, b): it fits the output's limbs
+    const int Lp = std::max(std::max(J.La, J.Lb), J.Lc);
+    block_content<K>(J.A, J.da + 1, J.La, J.B, J.db + 1, J.Lb, part, Lp, J.cmul, J.Lc);
   } else {
-    for (int l = threadIdx.x & 31; l < J.Lc; l += 32) J.cmul[l] = (l == 0) ? 1u : 0u;
+    for (int l = threadIdx.x; l < J.Lc; l += blockDim.x) J.cmul[l] = (l == 0) ? 1u : 0u;
   }
 }
 
-__global__ void k_mg_content(const MgJob* jobs, int n, int K) {
-  const int warps = blockDim.x >> 5;
-  for (int ji = blockIdx.x * warps + (threadIdx.x >> 5); ji < n; ji += gridDim.x * warps) {
+// dynamic shared memory: (blockDim.x / 32) * max(Lc, La, Lb) words for the partial gcds
+__global__ void __launch_bounds__(256) k_mg_content(const MgJob* jobs, int n, int K) {
+  extern __shared__ uint32_t mg_part[];
+  for (int ji = blockIdx.x; ji < n; ji += gridDim.x) {
     if (K <= 1)
-      mg_content_job<1>(jobs[ji]);
+      mg_content_job<1>(jobs[ji], mg_part);
     else if (K <= 2)
-      mg_content_job<2>(jobs[ji]);
+      mg_content_job<2>(jobs[ji], mg_part);
     else if (K <= 4)
-      mg_content_job<4>(jobs[ji]);
+      mg_content_job<4>(jobs[ji], mg_part);
     else
-      mg_content_job<8>(jobs[ji]);
+      mg_content_job<8>(jobs[ji], mg_part);
   }
 }
 
@@ -534,7 +531,13 @@ int mg_launch(bs_ctx* ctx, MgBatch& B, const bs_upoly* a, const bs_upoly* b, cha
   };
   if (crt(wl1)) return ctx_fail(ctx, BS_ERR_RANGE, "too many primes for the reconstruction stage");
   const int K = (std::max(B.lmax - 1, B.in_limbs) + 31) / 32;  // <= 8: 256 limbs at most
-  k_mg_content<<<(m + 3) / 4, 128, 0, s>>>(dj, m, K);
+  {  // one block per job, one warp per 64 coefficients of the longest job (8 at most)
+    int maxc = 1;
+    for (int j : B.gen) maxc = std::max(maxc, std::max(B.da[j], B.db[j]) + 1);
+    const int W = std::min(8, std::max(1, (maxc + 63) / 64));
+    const size_t part_words = (size_t)W * std::max(B.lmax, B.in_limbs);
+    k_mg_content<<<m, W * 32, part_words * sizeof(uint32_t), s>>>(dj, m, K);
+  }
   k_mg_cinv<<<gblocks, 128, 0, s>>>(dj, m, Tv);
   k_mg_gather<<<gblocks, 256, 0, s>>>(dj, m, Tv, 1);
   if (crt(wl2)) return ctx_fail(ctx, BS_ERR_RANGE, "too many primes for the reconstruction stage");

@@ -389,12 +389,13 @@ struct ContentAcc {
 
   __device__ __forceinline__ bool is_one() const { return small && g64 == 1u; }
 
-  // fold the n coefficients c[i * L .. i * L + L - 1] into the gcd
-  __device__ void fold(const uint32_t* c, int n, int L) {
+  // fold the n coefficients c[i * step * L .. i * step * L + L - 1] into the gcd
+  __device__ void fold(const uint32_t* c, int n, int L, int step = 1) {
+    const int64_t stride = (int64_t)step * L;
     int i = 0;
     for (; i < n && !small; ++i) {  // warp-wide gcds until the gcd fits in 64 bits
       WBig<K> b;
-      wb_load_abs<K>(b, c + (int64_t)i * L, L);
+      wb_load_abs<K>(b, c + i * stride, L);
       if (wb_is_zero<K>(b)) continue;
       if (!started) {
         g = b;
@@ -425,7 +426,7 @@ struct ContentAcc {
       WBig<K> b[B4];
 #pragma unroll
       for (int j = 0; j < B4; ++j)
-        if (i + j < n) wb_load_abs<K>(b[j], c + (int64_t)(i + j) * L, L);
+        if (i + j < n) wb_load_abs<K>(b[j], c + (i + j) * stride, L);
       uint64_t r[B4];
 #pragma unroll
       for (int j = 0; j < B4; ++j) r[j] = (i + j < n) ? wb_mod64<K>(b[j], mp) : 0u;
@@ -452,5 +453,39 @@ struct ContentAcc {
     for (int l = 32 * K + lane; l < Lout; l += 32) out[l] = 0u;
   }
 };
+
+// The gcd of the n1 coefficients at c1 (L1 limbs each, two's complement) and the n2 at c2
+// (L2 limbs; n2 = 0 for none) by all warps of the block: warp w folds the coefficients
+// w, w + W, w + 2W, ... of each sequence (W warps), so the first gcd of two full-size
+// coefficients runs in every warp at once and the long tail of reductions modulo the (by
+// then 64-bit) gcd runs W warps wide.  The W partial gcds meet in shared memory (part:
+// W * Lp words, Lp >= max(L1, L2) so that a partial gcd, at most one coefficient's
+// magnitude, fits) and warp 0 folds them into out (Lout magnitude limbs, which must hold
+// the final gcd; 0 when every coefficient is zero).  Every thread of the block calls it;
+// it starts and ends with a barrier and returns, in every thread, whether the gcd is 1.
+template <int K>
+__device__ __noinline__ bool block_content(const uint32_t* c1, int n1, int L1, const uint32_t* c2, int n2, int L2,
+                                           uint32_t* part, int Lp, uint32_t* out, int Lout) {
+  __shared__ int s_one;
+  const int W = blockDim.x >> 5, w = threadIdx.x >> 5;
+  __syncthreads();  // part and s_one may still be read by an earlier call
+  {
+    ContentAcc<K> h;
+    const int m1 = n1 > w ? (n1 - w + W - 1) / W : 0;
+    h.fold(c1 + (int64_t)w * L1, m1, L1, W);
+    const int m2 = n2 > w ? (n2 - w + W - 1) / W : 0;
+    if (m2 > 0 && !h.is_one()) h.fold(c2 + (int64_t)w * L2, m2, L2, W);
+    h.store(part + (int64_t)w * Lp, Lp);
+  }
+  __syncthreads();
+  if (w == 0) {
+    ContentAcc<K> t;
+    t.fold(part, W, Lp);
+    t.store(out, Lout);
+    if (threadIdx.x == 0) s_one = t.is_one() ? 1 : 0;
+  }
+  __syncthreads();
+  return s_one != 0;
+}
 
 }  // namespace bs

@@ -259,22 +259,34 @@ __device__ void yun_content_factor(const YunJob& J, int f) {
   h.store(J.content + (int64_t)f * J.Lc, J.Lc);
 }
 
-__global__ void k_yun_content(const YunJob* jobs, int n, int K) {
-  const int warps = blockDim.x >> 5;
+// one warp per factor when the job has at least as many factors as the block has warps;
+// otherwise the factors one after the other, each by all warps (block_content)
+template <int K>
+__device__ void yun_content_job(const YunJob& J, uint32_t* part) {
+  const int s = J.info[2], warps = blockDim.x >> 5;
+  if (s >= warps) {
+    for (int f = threadIdx.x >> 5; f < s; f += warps) yun_content_factor<K>(J, f);
+    return;
+  }
+  for (int f = 0; f < s; ++f)
+    block_content<K>(J.crt[0].out + (int64_t)J.foff[f] * J.Lc, J.fdeg[f] + 1, J.Lc, nullptr, 0, 1, part, J.Lc,
+                     J.content + (int64_t)f * J.Lc, J.Lc);
+}
+
+// dynamic shared memory: (blockDim.x / 32) * Lc words for the partial gcds
+__global__ void __launch_bounds__(256) k_yun_content(const YunJob* jobs, int n, int K) {
+  extern __shared__ uint32_t yun_part[];
   for (int ji = blockIdx.x; ji < n; ji += gridDim.x) {
     const YunJob& J = jobs[ji];
     if (J.info[3] != 0) continue;
-    const int s = J.info[2];
-    for (int f = threadIdx.x >> 5; f < s; f += warps) {
-      if (K <= 1)
-        yun_content_factor<1>(J, f);
-      else if (K <= 2)
-        yun_content_factor<2>(J, f);
-      else if (K <= 4)
-        yun_content_factor<4>(J, f);
-      else
-        yun_content_factor<8>(J, f);
-    }
+    if (K <= 1)
+      yun_content_job<1>(J, yun_part);
+    else if (K <= 2)
+      yun_content_job<2>(J, yun_part);
+    else if (K <= 4)
+      yun_content_job<4>(J, yun_part);
+    else
+      yun_content_job<8>(J, yun_part);
   }
 }
 
@@ -495,7 +507,7 @@ static int yun_launch(bs_ctx* ctx, YunBatch& B, const bs_upoly* r, char* base, c
   };
   if (crt(wl1)) return ctx_fail(ctx, BS_ERR_RANGE, "too many primes for the reconstruction stage");
   const int K = (B.lmax - 1 + 31) / 32;  // <= 8: out_limbs <= 256
-  k_yun_content<<<gblocks, 256, 0, s>>>(dj, m, K);
+  k_yun_content<<<gblocks, 256, (size_t)8 * B.lmax * sizeof(uint32_t), s>>>(dj, m, K);
   k_yun_cinv<<<gblocks, 128, 0, s>>>(dj, m, Tv);
   k_yun_gather<<<gblocks, 256, 0, s>>>(dj, m, Tv, 1);
   if (crt(wl2)) return ctx_fail(ctx, BS_ERR_RANGE, "too many primes for the reconstruction stage");
