@@ -173,22 +173,23 @@ __global__ void k_mg_select(const MgJob* jobs, int n) {
 
 // ---- residues for a reconstruction: block per job ---------------------------------------
 // second = 0: images of H; second = 1: images of H times cinv
+// blockIdx.x strides over the jobs, blockIdx.y over a job's selected primes (rows)
 __global__ void k_mg_gather(const MgJob* jobs, int n, Tables T, int second) {
   for (int ji = blockIdx.x; ji < n; ji += gridDim.x) {
     const MgJob& J = jobs[ji];
     if (J.info[3] != 0) continue;
     const int dh = J.info[0];
-    const int64_t cnt = (int64_t)J.k_need * (dh + 1);
-    for (int64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
-      const int r = (int)(t / (dh + 1));
-      const int i = (int)(t - (int64_t)r * (dh + 1));
+    for (int r = blockIdx.y; r < J.k_need; r += gridDim.y) {
       const int q = J.sel[r];
-      uint32_t v = J.Qp[(int64_t)q * (J.cap + 1) + i];
+      const uint32_t* src = J.Qp + (int64_t)q * (J.cap + 1);
+      uint32_t* dst = J.rmod + (int64_t)r * (dh + 1);
       if (second) {  // standard form times Montgomery form gives standard form
         const PrimeConst pc = T.pc[q];
-        v = redc((uint64_t)v * J.cinv[r], pc.p, pc.pinv);
+        const uint32_t ci = J.cinv[r];
+        for (int i = threadIdx.x; i <= dh; i += blockDim.x) dst[i] = redc((uint64_t)src[i] * ci, pc.p, pc.pinv);
+      } else {
+        for (int i = threadIdx.x; i <= dh; i += blockDim.x) dst[i] = src[i];
       }
-      J.rmod[(int64_t)r * (dh + 1) + i] = v;
     }
   }
 }
@@ -514,7 +515,9 @@ int mg_launch(bs_ctx* ctx, MgBatch& B, const bs_upoly* a, const bs_upoly* b, cha
   k_mg_images<<<img_grid, B.threads, B.smem, s>>>(dj, wl_items, Tv);
   k_mg_select<<<(m + 127) / 128, 128, 0, s>>>(dj, m);
   const int gblocks = std::min(m, 4 * ctx->sms);
-  k_mg_gather<<<gblocks, 256, 0, s>>>(dj, m, Tv, 0);
+  // the gathers: a few jobs still fill the GPU by spreading their rows over blockIdx.y
+  const dim3 ggrid(gblocks, std::max(1, std::min(B.kmax, (4 * ctx->sms + gblocks - 1) / gblocks)));
+  k_mg_gather<<<ggrid, 256, 0, s>>>(dj, m, Tv, 0);
   const int crt_grid = (int)std::min<int64_t>(tiles, (int64_t)4 * ctx->sms);
   const size_t wsm = crt_warp_smem(B.kmax, B.lmax);
   auto crt = [&](const WorkList& wl) -> int {
@@ -539,7 +542,7 @@ int mg_launch(bs_ctx* ctx, MgBatch& B, const bs_upoly* a, const bs_upoly* b, cha
     k_mg_content<<<m, W * 32, part_words * sizeof(uint32_t), s>>>(dj, m, K);
   }
   k_mg_cinv<<<gblocks, 128, 0, s>>>(dj, m, Tv);
-  k_mg_gather<<<gblocks, 256, 0, s>>>(dj, m, Tv, 1);
+  k_mg_gather<<<ggrid, 256, 0, s>>>(dj, m, Tv, 1);
   if (crt(wl2)) return ctx_fail(ctx, BS_ERR_RANGE, "too many primes for the reconstruction stage");
   rc = ctx_cuda(ctx, cudaGetLastError(), "launch");
   if (rc) return rc;

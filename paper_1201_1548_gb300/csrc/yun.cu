@@ -229,24 +229,26 @@ __device__ __forceinline__ int factor_of(const int32_t* foff, int s, int i) {
 
 // ---- residues for a reconstruction: block per job ---------------------------------------
 // second = 0: images of the H_i; second = 1: images of H_i (s c_i)^-1
+// blockIdx.x strides over the jobs, blockIdx.y over a job's selected primes (rows)
 __global__ void k_yun_gather(const YunJob* jobs, int n, Tables T, int second) {
   for (int ji = blockIdx.x; ji < n; ji += gridDim.x) {
     const YunJob& J = jobs[ji];
     if (J.info[3] != 0) continue;
     const int cnt1 = J.info[0] + 1;
     const int s = J.info[2];
-    const int64_t cnt = (int64_t)J.k_need * cnt1;
-    for (int64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
-      const int r = (int)(t / cnt1);
-      const int i = (int)(t - (int64_t)r * cnt1);
+    for (int r = blockIdx.y; r < J.k_need; r += gridDim.y) {
       const int q = J.sel[r];
-      uint32_t v = J.Qp[(int64_t)q * J.cap + i];
+      const uint32_t* src = J.Qp + (int64_t)q * J.cap;
+      uint32_t* dst = J.rmod + (int64_t)r * cnt1;
       if (second) {  // standard form times Montgomery form gives standard form
         const PrimeConst pc = T.pc[q];
-        const int f = factor_of(J.foff, s, i);
-        v = redc((uint64_t)v * J.cinv[(int64_t)f * J.k_need + r], pc.p, pc.pinv);
+        for (int i = threadIdx.x; i < cnt1; i += blockDim.x) {
+          const int f = factor_of(J.foff, s, i);
+          dst[i] = redc((uint64_t)src[i] * J.cinv[(int64_t)f * J.k_need + r], pc.p, pc.pinv);
+        }
+      } else {
+        for (int i = threadIdx.x; i < cnt1; i += blockDim.x) dst[i] = src[i];
       }
-      J.rmod[(int64_t)r * cnt1 + i] = v;
     }
   }
 }
@@ -490,7 +492,9 @@ static int yun_launch(bs_ctx* ctx, YunBatch& B, const bs_upoly* r, char* base, c
   k_yun_images<<<img_grid, B.threads, B.smem, s>>>(dj, wl_items, Tv);
   k_yun_select<<<(m + 127) / 128, 128, 0, s>>>(dj, m);
   const int gblocks = std::min(m, 4 * ctx->sms);
-  k_yun_gather<<<gblocks, 256, 0, s>>>(dj, m, Tv, 0);
+  // the gathers: a few jobs still fill the GPU by spreading their rows over blockIdx.y
+  const dim3 ggrid(gblocks, std::max(1, std::min(B.kmax, (4 * ctx->sms + gblocks - 1) / gblocks)));
+  k_yun_gather<<<ggrid, 256, 0, s>>>(dj, m, Tv, 0);
   const int crt_grid = (int)std::min<int64_t>(toff[m], (int64_t)4 * ctx->sms);
   const size_t wsm = crt_warp_smem(B.kmax, B.lmax);
   auto crt = [&](const WorkList& wl) -> int {
@@ -509,7 +513,7 @@ static int yun_launch(bs_ctx* ctx, YunBatch& B, const bs_upoly* r, char* base, c
   const int K = (B.lmax - 1 + 31) / 32;  // <= 8: out_limbs <= 256
   k_yun_content<<<gblocks, 256, (size_t)8 * B.lmax * sizeof(uint32_t), s>>>(dj, m, K);
   k_yun_cinv<<<gblocks, 128, 0, s>>>(dj, m, Tv);
-  k_yun_gather<<<gblocks, 256, 0, s>>>(dj, m, Tv, 1);
+  k_yun_gather<<<ggrid, 256, 0, s>>>(dj, m, Tv, 1);
   if (crt(wl2)) return ctx_fail(ctx, BS_ERR_RANGE, "too many primes for the reconstruction stage");
   rc = ctx_cuda(ctx, cudaGetLastError(), "launch");
   if (rc) return rc;
