@@ -130,3 +130,22 @@ def test_resultant_bounds_cover_plans():
         assert lib.bs_resultant_bounds(C.byref(fb), C.byref(gb), 1, C.byref(d), C.byref(L)) == 0
         p = bs.bs_plan(f, g, 1)
         assert d.value >= p["D"] and L.value >= p["out_limbs"]
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    # every compute entry point needs a context, and a context needs a CUDA device: on a
+    # machine without one the library reports a CUDA error instead of computing on the host
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(bs.BsError) as e:
+        bs.Context(0)
+    assert e.value.code == bs.BS_ERR_CUDA
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    from paper_1201_1548_gb300 import _abi
+    monkeypatch.setattr(_abi, "_LIB", None)
+    monkeypatch.setattr(_abi, "_LIB_PATH", str(tmp_path / "libbsres.so"))
+    with pytest.raises(bs.BsError):
+        _abi.load_library()
