@@ -171,7 +171,7 @@ __global__ void k_mg_select(const MgJob* jobs, int n) {
   }
 }
 
-// ---- residues for a reconstruction: block per job ---------------------------------------
+// ---- residues for a reconstruction: blocks over jobs and their selected primes ----------
 // second = 0: images of H; second = 1: images of H times cinv
 // blockIdx.x strides over the jobs, blockIdx.y over a job's selected primes (rows)
 __global__ void k_mg_gather(const MgJob* jobs, int n, Tables T, int second) {

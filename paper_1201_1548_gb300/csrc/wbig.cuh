@@ -1,11 +1,12 @@
 // Warp-wide big integers and the content (gcd of the coefficients) of an integer
-// polynomial, computed by one warp.
+// polynomial, computed by one warp or by the warps of a block splitting the coefficients.
 //
 // A non-negative integer of up to 32 K limbs is spread over the lanes: lane l, slot s
 // holds limb 32 s + l.  Comparisons, subtraction and shifts resolve carries across lanes
-// with ballots.  The gcd is Stein's binary algorithm; once the running gcd fits in 64
-// bits every further coefficient is reduced modulo it by the whole warp and the gcd
-// finishes in 64-bit arithmetic.
+// with ballots.  The gcd of two full-size numbers takes Lehmer steps on their leading 31
+// bits (Knuth's Algorithm L), with a binary (Stein) step when a round makes no progress;
+// once the running gcd fits in 64 bits every further coefficient is reduced modulo it by
+// the whole warp and the gcd finishes in 64-bit arithmetic.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -13,7 +13,8 @@
 // Every factor image is scaled to H_i = lc(R) monic(r_i) = (lc(R) / lc(r_i)) r_i, an
 // integer polynomial with ||H_i||_inf <= 2^deg(r_i) ||R||_2 (Mignotte's bound for a factor
 // of R).  All factors of a job are concatenated and lifted in one reconstruction; the
-// content c_i of each H_i is computed by one warp, and a second reconstruction of the
+// content c_i of each H_i is computed on the device (one warp per factor, or the block's
+// warps together on each factor when a job has few factors), and a second reconstruction of the
 // images H_i (s c_i)^-1, s the sign of lc(R), yields the primitive r_i with positive
 // leading coefficients.
 #include <cuda_runtime.h>
@@ -227,7 +228,7 @@ __device__ __forceinline__ int factor_of(const int32_t* foff, int s, int i) {
   return lo;
 }
 
-// ---- residues for a reconstruction: block per job ---------------------------------------
+// ---- residues for a reconstruction: blocks over jobs and their selected primes ----------
 // second = 0: images of the H_i; second = 1: images of H_i (s c_i)^-1
 // blockIdx.x strides over the jobs, blockIdx.y over a job's selected primes (rows)
 __global__ void k_yun_gather(const YunJob* jobs, int n, Tables T, int second) {
@@ -253,7 +254,7 @@ __global__ void k_yun_gather(const YunJob* jobs, int n, Tables T, int second) {
   }
 }
 
-// ---- contents: block per job, one warp per factor ---------------------------------------
+// ---- contents: block per job, one warp per factor or all warps on each factor -----------
 template <int K>
 __device__ void yun_content_factor(const YunJob& J, int f) {
   ContentAcc<K> h;
