@@ -119,7 +119,9 @@ int bs_last_stats(const bs_ctx *ctx, bs_stats *out);
  * ------------------------------------------------------------------------------ */
 
 /* The plan of res(f, g; var) (host only, no context or GPU needed).  Degrees are the
- * actual degrees found in the data; e is the eliminated variable, o the other one. */
+ * actual degrees found in the data; e is the eliminated variable, o the other one.
+ * Errors: BS_ERR_ARG for a null pointer, var other than 0 or 1, a negative grid extent,
+ * limbs outside 1..64 or a null coefficient array. */
 typedef struct {
     int32_t trivial;      /* 0 general; 1 the result is 0; 2 the result is 1            */
     int32_t m_e, n_e;     /* degrees of f and g in the eliminated variable              */

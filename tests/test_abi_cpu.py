@@ -149,3 +149,26 @@ def test_missing_library_raises(monkeypatch, tmp_path):
     monkeypatch.setattr(_abi, "_LIB_PATH", str(tmp_path / "libbsres.so"))
     with pytest.raises(bs.BsError):
         _abi.load_library()
+
+
+def test_planner_rejects_malformed_inputs():
+    import ctypes as C
+    from paper_1201_1548_gb300._abi import _Bipoly, _PlanInfo
+    lib = bs.load_library()
+    buf = np.zeros(2 * 2 * 65, dtype=np.uint32)
+    buf[0] = 1
+
+    def plan(f, g, var=1):
+        info = _PlanInfo()
+        return lib.bs_plan(C.byref(f) if f is not None else None, C.byref(g), var, C.byref(info))
+
+    ok = _Bipoly(1, 1, 1, buf.ctypes.data)
+    assert plan(ok, ok) == bs.BS_OK
+    assert plan(_Bipoly(1, 1, 64, buf.ctypes.data), ok) == bs.BS_OK       # the widest coefficients
+    for bad in (_Bipoly(1, 1, 0, buf.ctypes.data), _Bipoly(1, 1, 65, buf.ctypes.data),
+                _Bipoly(-1, 1, 1, buf.ctypes.data), _Bipoly(1, -1, 1, buf.ctypes.data),
+                _Bipoly(1, 1, 1, None)):
+        assert plan(bad, ok) == bs.BS_ERR_ARG
+        assert plan(ok, bad) == bs.BS_ERR_ARG
+    assert plan(None, ok) == bs.BS_ERR_ARG
+    assert plan(ok, ok, 2) == bs.BS_ERR_ARG
