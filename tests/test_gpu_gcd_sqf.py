@@ -225,3 +225,16 @@ def test_modgcd_batch_matches_single_calls(ctx):
         want = G.gcd_z(a, b) if k == 0 else G.squarefree_part(a)
         assert g == want
         assert g == (ctx.gcd_z(a, b) if k == 0 else ctx.squarefree_part(a))
+
+
+def test_gcd_z_partial_content_wider_than_the_result(ctx):
+    # the inputs' contents are folded by several warps (one per 64 coefficients): with
+    # a = 2^300 (x^200 + x) and b = 3 x^2 + 3, one warp sees a's coefficient 2^300 and no
+    # coefficient of b, so its partial gcd is far wider than the one-limb result
+    a = [0] * 201
+    a[1] = a[200] = 1 << 300
+    b = [3, 0, 3]
+    assert ctx.gcd_z(a, b) == G.gcd_z(a, b) == [1]
+    a2 = [6 * x for x in a]
+    b2 = [4 * x for x in P.mul(b, [1, 0, 0, 1])]         # b (x^3 + 1): shares x + 1 with a
+    assert ctx.gcd_z(a2, b2) == G.gcd_z(a2, b2)
