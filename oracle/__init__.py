@@ -14,7 +14,11 @@ follows the definitions of the paper directly:
   theorem in Sec. 5.1), gcd in Z[x], Yun's square-free factorisation (Sec. 2.1) and the
   square-free part;
 * ``numtheory``  -- Miller-Rabin, the table of transform-friendly 31-bit primes,
-  primitive roots.
+  primitive roots;
+* ``subresultant`` -- principal subresultant coefficients (Sec. 3.3), exact and modulo
+  a prime, the fiber counts N, N^- and N^+, the bivariate gcd and Teissier's Q, and the
+  split of R* by the multiplicity of Q at its roots; ``gcd`` also holds the content of
+  a bivariate polynomial with respect to one variable (Sec. 4).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import anything from here.  The product path (``paper_1201_1548_gb300``) never
