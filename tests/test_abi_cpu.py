@@ -172,3 +172,15 @@ def test_planner_rejects_malformed_inputs():
         assert plan(ok, bad) == bs.BS_ERR_ARG
     assert plan(None, ok) == bs.BS_ERR_ARG
     assert plan(ok, ok, 2) == bs.BS_ERR_ARG
+
+
+def test_smoke_needs_the_gpu():
+    # the smoke check compares the CUDA path with the oracle; without a GPU it must fail,
+    # not pass on some other path
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import __graft_entry__ as entry
+    with pytest.raises(bs.BsError) as e:
+        entry.smoke()
+    assert e.value.code == bs.BS_ERR_CUDA
