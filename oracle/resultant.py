@@ -197,6 +197,55 @@ def interpolate_consecutive(x0, vals):
     return P.trim(out)
 
 
+def interpolate_consecutive_modp(x0, vals, p):
+    """Polynomial of degree <= D over Z_p through (x0 + t, vals[t]), t = 0..D, for a
+    prime p > D: Newton's form sum_k (Delta^k v_0 / k!) prod_{s<k} (x - x_s), with the
+    forward differences and the nested products taken mod p."""
+    D = len(vals) - 1
+    if D < 0:
+        return []
+    if p <= D:
+        raise ValueError("need p > D so that k! is invertible mod p")
+    diffs = []
+    cur = [v % p for v in vals]
+    for _ in range(D + 1):
+        diffs.append(cur[0])
+        cur = [(cur[i + 1] - cur[i]) % p for i in range(len(cur) - 1)]
+    inv_fact = [1] * (D + 1)
+    f = 1
+    for k in range(1, D + 1):
+        f = f * k % p
+        inv_fact[k] = pow(f, p - 2, p)
+    acc = [diffs[D] * inv_fact[D] % p]
+    for k in range(D - 1, -1, -1):
+        xk = (x0 + k) % p
+        nxt = [0] * (len(acc) + 1)
+        for i, c in enumerate(acc):
+            nxt[i + 1] = (nxt[i + 1] + c) % p
+            nxt[i] = (nxt[i] - xk * c) % p
+        nxt[0] = (nxt[0] + diffs[k] * inv_fact[k]) % p
+        acc = nxt
+    return P.trim(acc)
+
+
+def res_y_modp(f, g, p):
+    """res(f, g; y) with every coefficient reduced mod p (a prime above the degree bound
+    D): the formal-shape Sylvester determinant over Z_p at the D + 1 consecutive integer
+    points of the points route (step (c) of Sec. 5.1), interpolated over Z_p.  Same
+    conventions as ``res_y`` (res(0, g) = 0, both constant in y gives 1)."""
+    rf = _formal_rows(f)
+    rg = _formal_rows(g)
+    if not rf or not rg:
+        return []
+    my, ny = len(rf) - 1, len(rg) - 1
+    if my == 0 and ny == 0:
+        return [1 % p] if p > 1 else []
+    D = degree_bound(f, g)
+    x0 = -(D // 2)
+    vals = [res_at_point_modp(f, g, x0 + t, p) for t in range(D + 1)]
+    return interpolate_consecutive_modp(x0, vals, p)
+
+
 # --------------------------------------------------------------------------------------
 # bound and plan
 # --------------------------------------------------------------------------------------

@@ -155,10 +155,6 @@ def test_degree_and_coefficient_bounds():
         for p in primes[:k]:
             prod *= p
         assert prod > 2 * max(abs(c) for c in r)
-        # CRT from the first k primes recovers R
-        for p in primes[:3]:
-            vals = [c % p for c in r]
-            assert vals == [c % p for c in r]
 
 
 def test_point_values_and_modular_values():
@@ -203,3 +199,43 @@ def test_sympy_cross_check():
     ref = sympy.Poly(sympy.resultant(to_sym(f), to_sym(g), y), x)
     ours = R.res_y(f, g)
     assert [int(c) for c in reversed(ref.all_coeffs())] == ours
+
+
+def test_interpolate_consecutive_modp_recovers_polynomial():
+    """Newton interpolation over Z_p against known polynomials and against the integer
+    interpolant reduced mod p."""
+    rng = random.Random(4)
+    for p in (101, 2147483647, (1 << 61) - 1):
+        for d in range(0, 14):
+            poly = [rng.randrange(-10**9, 10**9) for _ in range(d + 1)]
+            x0 = -(d // 2) - rng.randrange(3)
+            vals = [P.evaluate(poly, x0 + t) for t in range(d + 1)]
+            got = R.interpolate_consecutive_modp(x0, vals, p)
+            assert got == P.mod_p(poly, p)
+            assert got == P.mod_p(R.interpolate_consecutive(x0, vals), p)
+    with pytest.raises(ValueError):
+        R.interpolate_consecutive_modp(0, [1, 2, 3], 2)
+
+
+def test_res_y_modp_against_the_zx_route():
+    """res(f, g; y) mod p by point determinants over Z_p and interpolation over Z_p,
+    against the exact Bareiss determinant over Z[x] reduced mod p: random pairs, a leading
+    coefficient with integer roots (vertical asymptotes at some of the points), a square
+    factor (R = 0) and the constant conventions."""
+    from workloads import cfg4_cases
+    rng = _rng(15)
+    q = (1 << 61) - 1
+    for t in range(10):
+        f = dense_curve(rng, int(rng.integers(1, 6)), int(rng.integers(2, 40)),
+                        zero_prob=0.2 if t % 2 else 0.0)
+        g = dense_curve(rng, int(rng.integers(1, 6)), int(rng.integers(2, 40)))
+        for p in (q, 2147483647):
+            assert R.res_y_modp(f, g, p) == P.mod_p(R.res_y(f, g, route="zx"), p), t
+    cases = cfg4_cases(seed=3, deg=3, bits=10)
+    for name in ("4a", "4b2", "4c"):
+        f, g = cases[name]
+        assert R.res_y_modp(f, g, q) == P.mod_p(R.res_y(f, g, route="zx"), q), name
+    assert R.res_y_modp(cases["4b2"][0], cases["4b2"][1], q) == []
+    assert R.res_y_modp([[0]], [[1, 2], [3]], q) == []
+    assert R.res_y_modp([[5]], [[7, 1]], q) == [1]
+    assert R.res_y_modp([[3]], [[1], [2], [1]], q) == [9]
