@@ -28,6 +28,7 @@ Test infrastructure only: plain, slow, exact.
 from __future__ import annotations
 
 from fractions import Fraction
+from functools import partial
 
 from . import gcd as G
 from . import poly as P
@@ -84,6 +85,30 @@ def subresultant_poly(a, b, i):
     return P.trim(out)
 
 
+def subresultant_y(f, g, d, map=map):
+    """The d-th subresultant polynomial of f and g with respect to y as [s_0, ..., s_d], s_j
+    the coefficient of y^j, an ascending list in Z[x] (formal degrees in y from the actual
+    top rows, 0 <= d < min(m_y, n_y)).  Each s_j is a minor of the Sylvester matrix, so its
+    degree is at most the resultant's bound D; the points route evaluates the univariate
+    subresultant polynomial exactly at D + 1 consecutive integers and interpolates."""
+    rf, rg = y_rows(f), y_rows(g)
+    q = min(len(rf), len(rg)) - 1
+    if not 0 <= d < q:
+        raise ValueError("subresultant index out of range")
+    D = degree_bound(f, g)
+    x0 = -(D // 2)
+    xs = list(range(x0, x0 + D + 1))
+    vals = list(map(partial(_sres_at_point, rf, rg, d), xs))
+    return [interpolate_consecutive(x0, [v[j] if j < len(v) else 0 for v in vals])
+            for j in range(d + 1)]
+
+
+def _sres_at_point(rf, rg, d, x):
+    a = [P.evaluate(row, x) for row in rf]
+    b = [P.evaluate(row, x) for row in rg]
+    return subresultant_poly(a, b, d)
+
+
 def psc_univariate(a, b):
     """[sr_0, ..., sr_(q-1)], q = min(m, n), over Z (formal degrees)."""
     q = min(len(a), len(b)) - 1
@@ -97,9 +122,18 @@ def psc_univariate_modp(a, b, p):
     return [det_modp(psc_matrix(a, b, i), p) for i in range(max(q, 0))]
 
 
-def psc_y(f, g, route=None):
+def _psc_at_point(rf, rg, i, x):
+    """sr_i(f(x, y), g(x, y)) exactly, formal degrees from the rows rf, rg."""
+    a = [P.evaluate(row, x) for row in rf]
+    b = [P.evaluate(row, x) for row in rg]
+    return det_bareiss(psc_matrix(a, b, i), IntRing)
+
+
+def psc_y(f, g, route=None, map=map):
     """[sr_0(x), ..., sr_(q-1)(x)] of f and g with respect to y, q = min(m_y, n_y), each an
-    ascending list in Z[x] (formal degrees in y from the actual top rows)."""
+    ascending list in Z[x] (formal degrees in y from the actual top rows).  ``map`` applies
+    the point determinants of the points route (a process pool's map spreads them over
+    cores; the arithmetic is the same)."""
     rf, rg = y_rows(f), y_rows(g)
     if not rf or not rg:
         return []
@@ -115,11 +149,7 @@ def psc_y(f, g, route=None):
         xs = list(range(x0, x0 + D + 1))
         out = []
         for i in range(q):
-            vals = []
-            for x in xs:
-                a = [P.evaluate(row, x) for row in rf]
-                b = [P.evaluate(row, x) for row in rg]
-                vals.append(det_bareiss(psc_matrix(a, b, i), IntRing))
+            vals = list(map(partial(_psc_at_point, rf, rg, i), xs))
             out.append(interpolate_consecutive(x0, vals))
         return out
     raise ValueError(route)
@@ -244,12 +274,14 @@ def _pprem(A, B):
 def bigcd_y(A, B):
     """gcd of A and B in Z[x][y] by the primitive pseudo-remainder sequence: the gcd of the
     contents (in Z[x]) times the primitive part of the last nonzero remainder, with a
-    positive leading coefficient."""
+    positive leading coefficient (the highest power of x in the top row); gcd(0, B) is B
+    with that sign, gcd(0, 0) = 0 (no rows)."""
     A, B = _rows(A), _rows(B)
-    if not A:
-        return B
-    if not B:
-        return A
+    if not A or not B:  # gcd(0, B) = B with a positive leading coefficient
+        g = B if not A else A
+        if g and g[-1][-1] < 0:
+            g = _scale_rows(g, [-1])
+        return g
     ca, cb = _content_rows(A), _content_rows(B)
     c = G.gcd_z(ca, cb)
     A, B = _div_rows(A, ca), _div_rows(B, cb)

@@ -323,3 +323,42 @@ def test_multiplicity_split_against_sympy_factors():
             coeffs = [int(a) for a in reversed(c.all_coeffs())]
             want.append(P.scale(coeffs, -1) if coeffs[-1] < 0 else coeffs)
         assert S.multiplicity_split(r, q) == want
+
+
+def test_bivariate_subresultant_polynomial():
+    """S_d of two curves: S_0 is the resultant (Sylvester route), the top coefficient of S_d
+    is sr_d (the psc route), and for a planted common factor C of degree k in y the
+    S_j below k vanish and pp(S_k) = pp(C) up to sign."""
+    rng = np.random.Generator(np.random.PCG64(21))
+    for t in range(4):
+        f = dense_curve(rng, 3 + t % 2, 8)
+        g = dense_curve(rng, 2 + t % 3, 8)
+        q = min(len(R.y_rows(f)), len(R.y_rows(g))) - 1
+        assert S.subresultant_y(f, g, 0) == [R.res_y(f, g, route="zx")]
+        sr = S.psc_y(f, g)
+        for d in range(q):
+            sd = S.subresultant_y(f, g, d)
+            assert len(sd) == d + 1 and sd[d] == sr[d], (t, d)
+    _, add, mul = _compose([1], 1, 1)
+    for t in range(3):
+        C = dense_curve(rng, 1 + t % 2, 5)
+        U = dense_curve(rng, 2, 5)
+        V = dense_curve(rng, 2, 5)
+        A, B = mul(C, U), mul(C, V)
+        k = len(R.y_rows(C)) - 1
+        for j in range(k):
+            assert all(not P.trim(s) for s in S.subresultant_y(A, B, j)), (t, j)
+        Sk = S.subresultant_y(A, B, k)
+        ppS = S._div_rows(Sk, S._content_rows(Sk))
+        ppC = S._div_rows(R.y_rows(C), S._content_rows(R.y_rows(C)))
+        assert ppS == ppC or ppS == [P.scale(r, -1) for r in ppC], t
+    with pytest.raises(ValueError):
+        S.subresultant_y([[1], [2], [3]], [[1], [1]], 1)
+
+
+def test_bivariate_gcd_conventions():
+    A = [[1, 2], [3, 0], [-5, 1]]
+    rows = R.y_rows(A)
+    assert S.bigcd_y([[0]], A) == S.bigcd_y(A, [[0]]) == rows
+    assert S.bigcd_y([[0]], [[-c for c in r] for r in A]) == rows
+    assert S.bigcd_y([[0]], [[0]]) == []
