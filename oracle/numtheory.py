@@ -95,13 +95,33 @@ def root_of_unity(p: int, n: int) -> int:
     return pow(primitive_root(p), (p - 1) // n, p)
 
 
-def coset_points(p: int, n: int):
-    """The evaluation set g * w**t, t = 0..n-1, with g the smallest primitive root and
-    w = g**((p-1)/n).  It avoids 0 and every n-th root of unity (in particular +-1)."""
+COSET_EXPONENT = 0x9E3779B9    # odd; the representative is a power of g with this exponent
+COSET_MAX_LOG = 14            # transform sizes up to 2^14 (the primes are 1 mod 2^14)
+
+
+def coset_representative(p: int) -> int:
+    """c = g**e for the first e of E mod (p-1), E mod (p-1) + 2, ... with c**(2**14) != 1
+    (g the smallest primitive root, E = COSET_EXPONENT): c lies outside the subgroup of
+    every transform size.  It is not a small integer, unlike g (often 3), which would make
+    x = g a point of every evaluation set."""
     g = primitive_root(p)
+    e = COSET_EXPONENT % (p - 1)
+    while True:
+        c = pow(g, e, p)
+        if pow(c, 1 << COSET_MAX_LOG, p) != 1:
+            return c
+        e = (e + 2) % (p - 1)
+
+
+def coset_points(p: int, n: int):
+    """The evaluation set c * w**t, t = 0..n-1, with c = coset_representative(p) and
+    w = g**((p-1)/n) for the smallest primitive root g.  It avoids 0 and every n-th root of
+    unity (in particular +-1), since c**n != 1."""
+    g = primitive_root(p)
+    c = coset_representative(p)
     w = pow(g, (p - 1) // n, p)
     pts = []
-    x = g
+    x = c
     for _ in range(n):
         pts.append(x)
         x = x * w % p

@@ -84,3 +84,23 @@ def test_root_of_unity_and_coset():
         assert len(set(pts)) == 64
         assert all(pow(x, 64, p) != 1 for x in pts)
         assert 1 not in pts and p - 1 not in pts and 0 not in pts
+
+
+def test_coset_avoids_small_integers():
+    """The evaluation cosets c <w> of the first 300 table primes contain no integer of
+    [-16, 16] for the transform sizes 2^8, 2^10 and 2^13 (so curves with vertical
+    asymptotes at small integers reject no prime by a coset hit), and c lies outside the
+    subgroup of order 2^14.  The smallest primitive root would not do: it is 3 for about
+    half of these primes, so x = 3 would be a point of their every evaluation set."""
+    primes = nt.prime_table(300)
+    for p in primes:
+        c = nt.coset_representative(p)
+        assert pow(c, 1 << 14, p) != 1
+        ci = pow(c, p - 2, p)
+        for n in (1 << 8, 1 << 10, 1 << 13):
+            for x in range(-16, 17):
+                if x:
+                    assert pow(x * ci % p, n, p) != 1, (p, n, x)
+        pts = nt.coset_points(p, 256)
+        assert pts[0] == c and pts[1] == c * nt.root_of_unity(p, 256) % p
+    assert sum(nt.primitive_root(p) == 3 for p in primes) > 100
