@@ -29,6 +29,7 @@ absolute value.  Symmetric residues then need prod(p) > 2B.
 
 from __future__ import annotations
 
+from functools import partial
 from math import factorial
 
 from . import poly as P
@@ -109,8 +110,11 @@ def _formal_rows(f):
     return rows
 
 
-def res_y(f, g, route=None):
-    """res(f, g; y) in Z[x] (ascending coefficients; [] is the zero polynomial)."""
+def res_y(f, g, route=None, map=map):
+    """res(f, g; y) in Z[x] (ascending coefficients; [] is the zero polynomial).
+
+    ``map`` applies the point determinants of the points route (the built-in by default;
+    a process pool's ``map`` spreads them over cores without changing any arithmetic)."""
     rf = _formal_rows(f)
     rg = _formal_rows(g)
     if not rf or not rg:
@@ -127,19 +131,19 @@ def res_y(f, g, route=None):
         D = degree_bound(f, g)
         x0 = -(D // 2)
         xs = list(range(x0, x0 + D + 1))
-        vals = [res_at_point(f, g, x) for x in xs]
+        vals = list(map(partial(res_at_point, f, g), xs))
         return interpolate_consecutive(x0, vals)
     raise ValueError(route)
 
 
-def res_x(f, g, route=None):
+def res_x(f, g, route=None, map=map):
     """res(f, g; x) in Z[y]."""
-    return res_y(transpose(f), transpose(g), route=route)
+    return res_y(transpose(f), transpose(g), route=route, map=map)
 
 
-def resultant(f, g, var=1, route=None):
+def resultant(f, g, var=1, route=None, map=map):
     """var = 1 eliminates y (result in Z[x]); var = 0 eliminates x (result in Z[y])."""
-    return res_y(f, g, route) if var == 1 else res_x(f, g, route)
+    return res_y(f, g, route, map) if var == 1 else res_x(f, g, route, map)
 
 
 def specialise(f, x0):
@@ -228,7 +232,7 @@ def interpolate_consecutive_modp(x0, vals, p):
     return P.trim(acc)
 
 
-def res_y_modp(f, g, p):
+def res_y_modp(f, g, p, map=map):
     """res(f, g; y) with every coefficient reduced mod p (a prime above the degree bound
     D): the formal-shape Sylvester determinant over Z_p at the D + 1 consecutive integer
     points of the points route (step (c) of Sec. 5.1), interpolated over Z_p.  Same
@@ -242,8 +246,12 @@ def res_y_modp(f, g, p):
         return [1 % p] if p > 1 else []
     D = degree_bound(f, g)
     x0 = -(D // 2)
-    vals = [res_at_point_modp(f, g, x0 + t, p) for t in range(D + 1)]
+    vals = list(map(partial(_res_at_point_modp_args, f, g, p), range(x0, x0 + D + 1)))
     return interpolate_consecutive_modp(x0, vals, p)
+
+
+def _res_at_point_modp_args(f, g, p, x0):
+    return res_at_point_modp(f, g, x0, p)
 
 
 # --------------------------------------------------------------------------------------
