@@ -74,8 +74,11 @@ def test_cfg2_sampled_points(ctx):
     for x0 in (0, 1, -1, 3):
         assert P.evaluate(r, x0) == R.res_at_point(f, g, x0), x0
     rng = random.Random(3)
-    for p in nt.prime_table(3):
-        for _ in range(2):
+    # primes outside the library's table (2^31 - 1 is not 1 mod 2^14), so a wrong
+    # reconstruction cannot agree with them by construction
+    for p in (2147483647, (1 << 61) - 1):
+        assert p not in nt.prime_table(200)
+        for _ in range(3):
             a = rng.randrange(p)
             assert P.evaluate(r, a) % p == R.res_at_point_modp(f, g, a, p)
 
@@ -140,6 +143,51 @@ def test_point_rejection_on_coset(ctx):
     assert ctx.last_stats()["primes_rejected"] >= 1
 
 
+def test_unlucky_job_fails_cleanly_and_context_stays_usable(ctx):
+    """A leading coefficient vanishing at a point of the first three primes' evaluation
+    sets (their coset representatives are roots of lc_y f) rejects three primes, one more
+    than the host plan's two spares: the call reports BS_ERR_UNLUCKY (the reconstruction
+    reads no unset selection slot), and so does the device-planned entry point unless its
+    own spare count covers them (then its result is exact); later calls on the context
+    are exact."""
+    import paper_1201_1548_gb300 as bs
+    torch = pytest.importorskip("torch")
+    rng = _rng(31)
+    f = dense_curve(rng, 5, 12)
+    lc = [1]
+    for p in nt.prime_table(3):
+        lc = P.mul(lc, [-nt.coset_representative(p), 1])    # (x - c_0)(x - c_1)(x - c_2)
+    width = max(len(lc), len(f[0]))
+    f = [row + [0] * (width - len(row)) for row in f]
+    f[5] = lc + [0] * (width - len(lc))
+    g = d_dy(f)
+    plan = bs.bs_plan(f, g)
+    assert plan["k_total"] - plan["k_need"] == 2
+    with pytest.raises(bs.BsError) as e:
+        ctx.resultant(f, g)
+    assert e.value.code == bs.BS_ERR_UNLUCKY
+    af, dxf, dyf, Lf = bs.bipoly_to_limbs(f)
+    ag, dxg, dyg, Lg = bs.bipoly_to_limbs(g)
+    df = torch.from_numpy(af.view(np.int32).copy()).cuda()
+    dg = torch.from_numpy(ag.view(np.int32).copy()).cuda()
+    dcap, lcap = ctx.resultant_bounds((dxf, dyf, Lf), (dxg, dyg, Lg))
+    out = torch.zeros((dcap + 1) * lcap, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    ctx.resultant_device(df.data_ptr(), (dxf, dyf, Lf), dg.data_ptr(), (dxg, dyg, Lg),
+                         out.data_ptr(), (dcap, lcap))
+    try:
+        ctx.device_status()
+    except bs.BsError as e:
+        assert e.code == bs.BS_ERR_UNLUCKY
+    else:
+        vals = bs.limbs_to_ints(out.cpu().numpy().view(np.uint32), dcap + 1, lcap)
+        while vals and vals[-1] == 0:
+            vals.pop()
+        assert vals == R.res_y(f, g)
+    f1, g1 = cfg1_pair(2)
+    assert ctx.resultant(f1, g1) == R.res_y(f1, g1)
+
+
 def test_batch_matches_single_and_oracle(ctx):
     pairs = cfg3_batch(seed=21, count=48, deg_lo=2, deg_hi=7, bits_lo=8, bits_hi=64)
     got = ctx.resultant_batch(pairs)
@@ -160,7 +208,7 @@ def test_large_transforms_sampled(ctx, tdeg, bits):
     assert P.deg(r) <= R.degree_bound(f, g)
     for x0 in (0, 1, -2):
         assert P.evaluate(r, x0) == R.res_at_point(f, g, x0)
-    p = nt.prime_table(1)[0]
+    p = 2147483647  # outside the library's table
     assert P.evaluate(r, 12345) % p == R.res_at_point_modp(f, g, 12345, p)
 
 
@@ -227,8 +275,10 @@ def test_largest_served_size(ctx):
 
 
 @pytest.mark.parametrize("shape", [
-    dict(eval_warps=2, eval_blocks_per_sm=4, uni_threads=(64,) * 6, crt_tile=2, crt_blocks_per_sm=2),
-    dict(eval_warps=4, eval_blocks_per_sm=16, uni_threads=(256,) * 6, crt_tile=4, crt_blocks_per_sm=8),
+    dict(eval_warps=2, eval_blocks_per_sm=4, uni_threads=(64,) * 6, crt_tile=2, crt_blocks_per_sm=2,
+         eval_independent=0),
+    dict(eval_warps=4, eval_blocks_per_sm=16, uni_threads=(256,) * 6, crt_tile=4, crt_blocks_per_sm=8,
+         eval_independent=0),
     dict(eval_warps=1, eval_blocks_per_sm=1, uni_threads=(64, 128, 256, 64, 128, 256), crt_tile=1,
          crt_blocks_per_sm=1),
 ])
@@ -253,6 +303,7 @@ def test_autotune_batch(ctx):
     try:
         assert info["trials"] >= 3
         assert info["eval_warps"] in (2, 4, 8) and info["crt_tile"] in (2, 4, 8)
+        assert info["eval_independent"] in (0, 1)
         assert all(t in (64, 128, 256) for t in info["uni_threads"])
         assert 0 < info["ms_tuned"] <= 1.1 * info["ms_default"]
         assert ctx.resultant_batch(pairs) == ref
