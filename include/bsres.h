@@ -163,10 +163,11 @@ int bs_resultant_device(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int
                         bs_upoly *out);
 
 /* res(f, g; var) with device-resident buffers, for callers that cannot allocate device
- * memory while they run: code executing inside a CUDA stream capture (where cudaMalloc
- * would synchronise or be refused), programs whose device memory is owned by another
- * allocator or framework, and latency-critical loops that must not pay for an
- * allocation.  The paper has no counterpart; this is a service of the library.
+ * memory while they run: programs whose device memory is owned by another allocator or
+ * framework (a caching allocator, a fixed memory budget handed out by the host
+ * application), and latency-critical loops that must not pay for an allocation and the
+ * synchronisation cudaMalloc implies.  The paper has no counterpart; this is a service
+ * of the library.
  *
  * Arguments, layout, capacities and the asynchronous behaviour are those of
  * bs_resultant_device.  The call performs no cudaMalloc or cudaFree: all of its scratch
@@ -176,7 +177,8 @@ int bs_resultant_device(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int
  * bs_resultant_bounds) exceeds 32 MiB is rejected with BS_ERR_RANGE; for example the
  * degree-32 discriminant with 32-bit coefficients does not fit, a degree-12 one does.
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture.  Every call
+ * cudaGetSymbolAddress and keeps it for the life of the process (resetting the device
+ * afterwards is not supported); make that first call before any stream capture.  Every call
  * shares the one array and leaves its contents behind (the call clears what must start
  * at zero), so calls whose GPU work overlaps -- on different streams or contexts of the
  * same device -- race and corrupt each other's results.  The call does not grow the
@@ -359,15 +361,47 @@ int bs_fiber_count(bs_ctx *ctx, const bs_bipoly *f, int var, int mode, int cap, 
 int bs_content(bs_ctx *ctx, const bs_bipoly *f, int var, bs_upoly *h, int cap_rows, bs_upoly *rows,
                int32_t *nrows);
 
-/* Teissier's Q = res(f_x*, f_y*; y) of Sec. 3.3, where f_x* = f_x / h, f_y* = f_y / h and
- * h = gcd(f_x, f_y) in Z[x, y] (for var = 0 the roles of x and y are exchanged), up to a
- * nonzero constant factor.  With lc(f) constant in the eliminated variable (required:
- * BS_ERR_ARG otherwise), h has a constant leading coefficient and the first principal
- * subresultant coefficient of f_x and f_y that is not identically zero, sr_d, is a
- * constant multiple of Q with d = deg h (the cofactor property of subresultants); Q is
- * returned as that sr_d (the constant 1 when every sr_i vanishes), *d = d.
+/* The d-th subresultant polynomial S_d(f, g) = sum_j s_j y^j with respect to the eliminated
+ * variable (var as in bs_resultant), 0 <= d < min(m, n) for the actual degrees m, n of f
+ * and g in that variable (Sec. 3.3: the Sres_i matrix with n - d shifted rows of f, m - d
+ * rows of g and the polynomials in its last column; s_d = sr_d).  The coefficients s_j are
+ * minors of the Sylvester matrix, so the resultant's plan, primes, points, rejection rule
+ * and bounds serve them; each (prime, point) image stops the division-free elimination of
+ * the psc stage when the shorter polynomial first reaches degree d.
+ * out: caller-owned array of cap host polynomials; out[j] receives s_j in the layout of
+ * bs_resultant (deg -1 for zero), *n = d + 1.  With out == NULL or out[0].c == NULL a size
+ * query (*n and upper bounds in out[j]).  The call waits for the device.
+ * Errors: BS_ERR_ARG (d out of range, bad arguments), BS_ERR_CAPACITY (cap < d + 1 or an
+ * output too small), BS_ERR_RANGE, BS_ERR_UNLUCKY as for bs_psc. */
+int bs_subresultant(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var, int d, int cap,
+                    int32_t *n, bs_upoly *out);
+
+/* gcd(f, g) in Z[x, y] (Sec. 3.3 takes h = gcd(f_x, f_y)), by the eliminated variable var:
+ * gcd(cont f, cont g) * pp(S_d(f, g)), where cont is the gcd in Z[x] of the coefficients
+ * with respect to the eliminated variable, d the index of the first principal subresultant
+ * coefficient that is not identically zero (d = the degree of the gcd in that variable),
+ * and pp divides by the content; when every sr_i vanishes the polynomial of smaller degree
+ * replaces S_d.  The result has a positive leading coefficient (the highest power of the
+ * other variable in its top row).  gcd(0, g) = +-g with that sign; gcd(0, 0) has no rows.
+ * The psc sequence, S_d, the contents, the exact quotients and the product by the
+ * content's gcd all run on the device.
+ * rows: caller-owned array of cap_rows host polynomials receiving the coefficients h_j of
+ * the powers of the eliminated variable (layout of bs_squarefree_part), *nrows = deg + 1.
+ * With rows == NULL or rows[0].c == NULL a size query (it runs the computation and writes
+ * the exact sizes).  Errors: BS_ERR_ARG, BS_ERR_CAPACITY, BS_ERR_RANGE, BS_ERR_UNLUCKY. */
+int bs_gcd_bivariate(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var, int cap_rows,
+                     bs_upoly *rows, int32_t *nrows);
+
+/* Teissier's Q = res(f_x*, f_y*; y) of Sec. 3.3 exactly, where f_x* = f_x / h, f_y* = f_y / h
+ * and h = gcd(f_x, f_y) as bs_gcd_bivariate returns it (for var = 0 the roles of x and y are
+ * exchanged), and *d = deg_y h.  With m, n the y-degrees of f_x and f_y, the cofactor
+ * property of subresultants gives sr_d(f_x, f_y) = lc_y(h)^(m + n - 2d) Q, so Q is one exact
+ * quotient in Z[x] of the psc sr_d by a power of lc_y(h); when every sr_i vanishes (or one
+ * derivative is free of y) one cofactor is free of y and Q is its power.  No condition on
+ * lc_y(f); f_x = 0 gives Q = 0 (deg -1).
  * Q: caller-owned output in the layout of bs_squarefree_part; Q->c == NULL is a size query
- * (it computes the sequence).  Errors as for bs_psc, BS_ERR_ZERO for f = 0. */
+ * (it runs the computation).  Errors as for bs_gcd_bivariate, BS_ERR_ZERO for f = 0,
+ * BS_ERR_RANGE for coefficients of f of 64 limbs (the derivatives need one more). */
 int bs_teissier_q(bs_ctx *ctx, const bs_bipoly *f, int var, bs_upoly *Q, int32_t *d);
 
 /* The square-free part R* of a non-zero R in Z[x] split by the multiplicity of a non-zero
@@ -401,23 +435,27 @@ typedef struct {
   float ms_default;            /* device time of the batch's stages with the default shapes */
   float ms_tuned;              /* ... with the chosen shapes (CUDA events, best of two runs) */
   int32_t trials;              /* shape combinations measured */
+  int32_t eval_independent;    /* 1: evaluation by independent warps (one row each, the prime's
+                                  tables read through L1; eval_warps unused), 0: blocks of
+                                  eval_warps rows of one prime with the tables staged */
 } bs_tune_info;
 
 /* Autotune the launch shapes for batches like this one: plans and uploads the batch, then
  * runs its stages on the context's stream once per candidate shape (coordinate descent:
- * evaluation warps per block and grid, univariate threads per block for each degree
- * class present, reconstruction tile and grid), keeping for each stage the shape with the
- * least device time.  The chosen shapes stay on the context and apply to its later
- * bs_resultant_batch and bs_resultant calls (not to the device-planned entry points);
- * *info (may be NULL) receives them.  Results are not returned; the call waits for the
- * device.  Errors as bs_resultant_batch. */
+ * evaluation warps per block and grid, the evaluation variant, univariate threads per
+ * block for each degree class present, reconstruction tile and grid), keeping for each
+ * stage the shape with the least device time.  The chosen shapes stay on the context and
+ * apply to its later bs_resultant_batch and bs_resultant calls; of them only the
+ * evaluation variant also applies to the device-planned entry points.  *info (may be
+ * NULL) receives them.  Results are not returned; the call waits for the device.  Errors
+ * as bs_resultant_batch. */
 int bs_autotune_batch(bs_ctx *ctx, int n, const bs_bipoly *f, const bs_bipoly *g, int var,
                       bs_tune_info *info);
 
-/* Set the batched launch shapes explicitly (t == NULL restores the defaults: 8 warps and
- * 8 blocks per SM for evaluation, 128 threads per univariate block, 8 coefficients and 4
- * blocks per SM for reconstruction).  The timing fields of *t are ignored.  BS_ERR_ARG for
- * a shape outside the ranges of bs_tune_info. */
+/* Set the batched launch shapes explicitly (t == NULL restores the defaults: evaluation
+ * by independent warps with 4 blocks per SM, 128 threads per univariate block, 8
+ * coefficients and 4 blocks per SM for reconstruction).  The timing fields of *t are
+ * ignored.  BS_ERR_ARG for a shape outside the ranges of bs_tune_info. */
 int bs_set_tune(bs_ctx *ctx, const bs_tune_info *t);
 
 /* ---------------------------------------------------------------------------------
@@ -427,8 +465,14 @@ int bs_set_tune(bs_ctx *ctx, const bs_tune_info *t);
  * stream, and one device arena of `arena_bytes` (0: half the free device memory, capped
  * by the context's budget).  bs_submit() copies a job's operands and queues it.  A free
  * worker forms a batch from the queued jobs of the head job's type (resultants in y,
- * resultants in x, or gcd / square-free jobs), first come first served and at most
- * `max_batch` jobs, and admits it once the arena can hold it; it then runs the batch
+ * resultants in x, or gcd / square-free jobs) and work class (large: a resultant whose
+ * plan counts more than 2e9 multiply-reduce operations in its univariate stage, about a
+ * millisecond of the GPU; small otherwise), first come first served and at most
+ * `max_batch` jobs; with two or more slots the last worker takes small jobs only, on a
+ * stream of the highest priority, and the persistent grids of a large batch are sized for
+ * three quarters of the SMs, so small jobs neither queue behind large ones nor wait for
+ * a large kernel to free the SMs.  The batch is admitted once the arena can hold it; the
+ * worker then runs the batch
  * (one graph launch for resultants, one pass of launches for gcds), posts the results
  * and frees the arena space.  Workers run concurrently, so batches admitted while
  * others are on the GPU overlap with them.  Every intermediate (residues, images,

@@ -8,7 +8,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libbsres.so")
+# BSRES_DEBUG=1 selects the build whose kernels bounds-check their accesses
+_LIB_PATH = os.path.join(_HERE, "libbsres_debug.so" if os.environ.get("BSRES_DEBUG") == "1"
+                         else "libbsres.so")
 _LIB = None
 
 # every symbol that include/bsres.h declares
@@ -21,6 +23,7 @@ EXPORTED_SYMBOLS = [
     "bs_autotune_batch", "bs_set_tune", "bs_serve_start", "bs_serve_stop", "bs_submit", "bs_poll", "bs_wait", "bs_serve_stats",
     "bs_squarefree_factorization", "bs_squarefree_factorization_batch", "bs_psc",
     "bs_psc_modp", "bs_fiber_count", "bs_content", "bs_teissier_q", "bs_root_multiplicity",
+    "bs_subresultant", "bs_gcd_bivariate",
 ]
 
 
@@ -28,7 +31,7 @@ class _TuneInfo(C.Structure):
     _fields_ = [("eval_warps", C.c_int32), ("eval_blocks_per_sm", C.c_int32),
                 ("uni_threads", C.c_int32 * 6), ("crt_tile", C.c_int32),
                 ("crt_blocks_per_sm", C.c_int32), ("ms_default", C.c_float),
-                ("ms_tuned", C.c_float), ("trials", C.c_int32)]
+                ("ms_tuned", C.c_float), ("trials", C.c_int32), ("eval_independent", C.c_int32)]
 
 
 class BsError(RuntimeError):
@@ -138,6 +141,10 @@ def load_library():
                                 C.POINTER(C.c_int32), P, P, C.POINTER(C.c_uint32)]
     lib.bs_content.argtypes = [P, C.POINTER(_Bipoly), I, C.POINTER(_Upoly), I, P, C.POINTER(C.c_int32)]
     lib.bs_teissier_q.argtypes = [P, C.POINTER(_Bipoly), I, C.POINTER(_Upoly), C.POINTER(C.c_int32)]
+    lib.bs_subresultant.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, I, I,
+                                    C.POINTER(C.c_int32), P]
+    lib.bs_gcd_bivariate.argtypes = [P, C.POINTER(_Bipoly), C.POINTER(_Bipoly), I, I, P,
+                                     C.POINTER(C.c_int32)]
     lib.bs_root_multiplicity.argtypes = [P, C.POINTER(_Upoly), C.POINTER(_Upoly), I, P, P,
                                          C.POINTER(_Upoly)]
     lib.bs_fiber_count.argtypes = [P, C.POINTER(_Bipoly), I, I, I, P, C.POINTER(C.c_int32),
@@ -273,6 +280,48 @@ class Context:
         return [limbs_to_ints(bufs[i], outs[i].deg + 1, outs[i].limbs) if outs[i].deg >= 0 else []
                 for i in range(n)]
 
+    def _rows_call(self, call, n):
+        """The two-call pattern of an entry point writing n caller-owned rows: a size query,
+        then the computation; returns the rows as lists of Python ints."""
+        if n == 0:
+            return []
+        outs = (_Upoly * n)()
+        for i in range(n):
+            outs[i] = _Upoly(0, 0, None)
+        self._check(call(n, C.cast(outs, C.c_void_p)))
+        bufs = []
+        for i in range(n):
+            buf = np.zeros((max(outs[i].deg, 0) + 1) * outs[i].limbs, dtype=np.uint32)
+            bufs.append(buf)
+            outs[i] = _Upoly(max(outs[i].deg, 0), outs[i].limbs, buf.ctypes.data)
+        self._check(call(n, C.cast(outs, C.c_void_p)))
+        return [limbs_to_ints(bufs[i], outs[i].deg + 1, outs[i].limbs) if outs[i].deg >= 0 else []
+                for i in range(n)]
+
+    def subresultant(self, f, g, d, var=1):
+        """[s_0, ..., s_d]: the d-th subresultant polynomial of f and g with respect to y
+        (var=1) or x (var=0), s_j the coefficient of the j-th power (lists of Python ints)."""
+        af, dxf, dyf, Lf = bipoly_to_limbs(f)
+        ag, dxg, dyg, Lg = bipoly_to_limbs(g)
+        fb, gb = _bip(af, dxf, dyf, Lf), _bip(ag, dxg, dyg, Lg)
+        n = C.c_int32(0)
+        self._check(self.lib.bs_subresultant(self.h, C.byref(fb), C.byref(gb), int(var), int(d), 0,
+                                             C.byref(n), None))
+        return self._rows_call(lambda cap, outs: self.lib.bs_subresultant(
+            self.h, C.byref(fb), C.byref(gb), int(var), int(d), cap, C.byref(n), outs), n.value)
+
+    def gcd_bivariate(self, f, g, var=1):
+        """gcd(f, g) in Z[x, y] as rows by powers of y (var=1) or x (var=0), each a list of
+        Python ints in the other variable ([] for gcd(0, 0))."""
+        af, dxf, dyf, Lf = bipoly_to_limbs(f)
+        ag, dxg, dyg, Lg = bipoly_to_limbs(g)
+        fb, gb = _bip(af, dxf, dyf, Lf), _bip(ag, dxg, dyg, Lg)
+        n = C.c_int32(0)
+        self._check(self.lib.bs_gcd_bivariate(self.h, C.byref(fb), C.byref(gb), int(var), 0, None,
+                                              C.byref(n)))
+        return self._rows_call(lambda cap, outs: self.lib.bs_gcd_bivariate(
+            self.h, C.byref(fb), C.byref(gb), int(var), cap, outs, C.byref(n)), n.value)
+
     def psc_modp(self, f, g, var=1):
         """(p, [sr_0 mod p, ...]) for the first accepted table prime p (ascending residues)."""
         af, dxf, dyf, Lf = bipoly_to_limbs(f)
@@ -316,8 +365,8 @@ class Context:
         return conv(h, hb), [conv(rows[i], bufs[i]) for i in range(nr.value)]
 
     def teissier_q(self, f, var=1):
-        """(Q, d): Teissier's Q up to a nonzero constant (the d-th principal subresultant
-        coefficient of f_x and f_y, d = deg gcd(f_x, f_y))."""
+        """(Q, d): Teissier's Q = res(f_x / h, f_y / h; y) exactly, h = gcd(f_x, f_y) in
+        Z[x, y] and d = deg_y h (x and y exchanged for var=0)."""
         af, dxf, dyf, Lf = bipoly_to_limbs(f)
         fb = _bip(af, dxf, dyf, Lf)
         q, d = _Upoly(0, 0, None), C.c_int32(0)
@@ -611,13 +660,14 @@ class Context:
         out["uni_threads"] = list(info.uni_threads)
         return out
 
-    def set_tune(self, eval_warps=8, eval_blocks_per_sm=8, uni_threads=(128,) * 6, crt_tile=8,
-                 crt_blocks_per_sm=4):
+    def set_tune(self, eval_warps=8, eval_blocks_per_sm=4, uni_threads=(128,) * 6, crt_tile=8,
+                 crt_blocks_per_sm=4, eval_independent=1):
         t = _TuneInfo()
         t.eval_warps, t.eval_blocks_per_sm = eval_warps, eval_blocks_per_sm
         for c in range(6):
             t.uni_threads[c] = uni_threads[c]
         t.crt_tile, t.crt_blocks_per_sm = crt_tile, crt_blocks_per_sm
+        t.eval_independent = eval_independent
         self._check(self.lib.bs_set_tune(self.h, C.byref(t)))
 
     def squarefree_part(self, r):

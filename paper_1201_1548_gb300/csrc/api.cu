@@ -25,6 +25,12 @@ int ctx_fail(bs_ctx* ctx, int code, const std::string& msg) {
   return code;
 }
 
+std::string device_failure_detail(const int32_t* st) {
+  std::string m = "device stage reported a failure";
+  if (st[2]) m += " (debug bounds check failed at site " + std::to_string(st[2]) + ")";
+  return m;
+}
+
 int ctx_cuda(bs_ctx* ctx, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return 0;
   return ctx_fail(ctx, BS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -191,7 +197,7 @@ static int check_bipoly(bs_ctx* ctx, const bs_bipoly* p, const char* name) {
 static Grid grid_of(const bs_bipoly* p) { return Grid{p->c, p->deg_x, p->deg_y, p->limbs}; }
 
 // upper bounds from extents and limb counts only
-static int meta_bounds(const bs_bipoly* f, const bs_bipoly* g, int var, MetaBounds* mb) {
+int bs::meta_bounds(const bs_bipoly* f, const bs_bipoly* g, int var, MetaBounds* mb) {
   const int fe = var ? f->deg_y : f->deg_x, fo = var ? f->deg_x : f->deg_y;
   const int ge = var ? g->deg_y : g->deg_x, go = var ? g->deg_x : g->deg_y;
   const int64_t d1 = (int64_t)(f->deg_x + f->deg_y) * (g->deg_x + g->deg_y);
@@ -474,7 +480,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
       if (P.logN <= kWarpLogNMax) {
         const int ec = eval_class_of(P.logN);
         eids[ec][efill[ec]] = i;
-        const int ew = ctx->tune.eval_warps;
+        const int ew = ctx->tune.eval_independent ? 1 : ctx->tune.eval_warps;  // rows per item
         eoffs[ec][efill[ec] + 1] = eoffs[ec][efill[ec]] + (int64_t)P.k_total * ((J.rows + ew - 1) / ew);
         ++efill[ec];
       } else {
@@ -563,6 +569,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
   L.logN_max = B.needLog;
   L.eval_warps = ctx->tune.eval_warps;
   L.eval_blocks_per_sm = ctx->tune.eval_blocks_per_sm;
+  L.eval_independent = ctx->tune.eval_independent != 0;
   L.crt_tile = crt_tile;
   L.crt_blocks_per_sm = ctx->tune.crt_blocks_per_sm;
   for (int c = 0; c < kNumUniClasses; ++c) L.uni_threads[c] = ctx->tune.uni_threads[c];
@@ -588,7 +595,7 @@ int batch_finish(bs_ctx* ctx, const HostBatch& B, const char* hd, bs_upoly* out)
   ctx->stats.mulmods_alg = B.mulmods;
   ctx->stats.max_points = B.maxpts;
   ctx->stats.max_primes = B.maxprimes;
-  if (st[0]) return ctx_fail(ctx, st[0], "device stage reported a failure");
+  if (st[0]) return ctx_fail(ctx, st[0], device_failure_detail(st));
   // results are independent: large batches are formatted on several host threads
   std::vector<int> err(B.n, 0);
   parallel_for(B.n, 256, [&](int i) {
@@ -711,22 +718,27 @@ extern "C" int bs_autotune_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const b
   }
   const float ms_default = st[0] + st[1] + st[2] + st[3];
   Tune best = dflt;
-  // evaluation: rows per block and grid cap
+  // evaluation: the variant (independent warps: grid cap; staged blocks: rows per block
+  // and grid cap)
   {
     float bt = st[0];
-    for (int w : {2, 4, 8})
-      for (int b : {4, 8, 16}) {
-        if (w == dflt.eval_warps && b == dflt.eval_blocks_per_sm) continue;
-        ctx->tune = best;
-        ctx->tune.eval_warps = w;
-        ctx->tune.eval_blocks_per_sm = b;
-        if ((rc = run(st))) break;
-        if (st[0] < bt) {
-          bt = st[0];
-          best.eval_warps = w;
-          best.eval_blocks_per_sm = b;
+    for (int v : {1, 0})
+      for (int w : {2, 4, 8})
+        for (int b : {4, 8, 16}) {
+          if (v == 1 && w != dflt.eval_warps) continue;  // rows per block unused there
+          if (v == dflt.eval_independent && w == dflt.eval_warps && b == dflt.eval_blocks_per_sm) continue;
+          ctx->tune = best;
+          ctx->tune.eval_independent = v;
+          ctx->tune.eval_warps = w;
+          ctx->tune.eval_blocks_per_sm = b;
+          if ((rc = run(st))) break;
+          if (st[0] < bt) {
+            bt = st[0];
+            best.eval_independent = v;
+            best.eval_warps = w;
+            best.eval_blocks_per_sm = b;
+          }
         }
-      }
   }
   // univariate resultants: threads per block, one degree class at a time
   for (int c = 0; c < kNumUniClasses && !rc; ++c) {
@@ -782,6 +794,7 @@ extern "C" int bs_autotune_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const b
     for (int c = 0; c < kNumUniClasses; ++c) info->uni_threads[c] = best.uni_threads[c];
     info->crt_tile = best.crt_tile;
     info->crt_blocks_per_sm = best.crt_blocks_per_sm;
+    info->eval_independent = best.eval_independent;
     info->ms_default = ms_default;
     info->ms_tuned = ms_tuned;
     info->trials = trials;
@@ -799,7 +812,8 @@ extern "C" int bs_set_tune(bs_ctx* ctx, const bs_tune_info* t) {
   if (t->eval_warps < 1 || t->eval_warps > kEvalThreads / 32 || t->eval_blocks_per_sm < 1 ||
       t->eval_blocks_per_sm > 64 || (t->crt_tile != 1 && t->crt_tile != 2 && t->crt_tile != 4 &&
                                      t->crt_tile != 8) ||
-      t->crt_blocks_per_sm < 1 || t->crt_blocks_per_sm > 64)
+      t->crt_blocks_per_sm < 1 || t->crt_blocks_per_sm > 64 ||
+      (t->eval_independent != 0 && t->eval_independent != 1))
     return ctx_fail(ctx, BS_ERR_ARG, "launch shape out of range");
   for (int c = 0; c < kNumUniClasses; ++c) {
     if (t->uni_threads[c] != 64 && t->uni_threads[c] != 128 && t->uni_threads[c] != 256)
@@ -810,6 +824,7 @@ extern "C" int bs_set_tune(bs_ctx* ctx, const bs_tune_info* t) {
   u.eval_blocks_per_sm = t->eval_blocks_per_sm;
   u.crt_tile = t->crt_tile;
   u.crt_blocks_per_sm = t->crt_blocks_per_sm;
+  u.eval_independent = t->eval_independent;
   ctx->tune = u;
   return BS_OK;
 }
@@ -912,7 +927,7 @@ extern "C" int bs_device_status(bs_ctx* ctx) {
     return ctx_fail(ctx, BS_ERR_CUDA, "status read failed");
   cudaMemsetAsync(ctx->d_status, 0, sizeof(st), ctx->stream);
   ctx->stats.primes_rejected = st[1];
-  if (st[0]) return ctx_fail(ctx, st[0], "device stage reported a failure");
+  if (st[0]) return ctx_fail(ctx, st[0], device_failure_detail(st));
   return BS_OK;
 }
 

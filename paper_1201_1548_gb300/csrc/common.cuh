@@ -27,8 +27,8 @@ struct PrimeConst {
   uint32_t pinv;   // p^-1 mod 2^32
   uint32_t one_m;  // 2^32 mod p   (Montgomery form of 1)
   uint32_t r2;     // 2^64 mod p
-  uint32_t g;      // smallest primitive root (standard form)
-  uint32_t g_m;    // its Montgomery form
+  uint32_t g;      // smallest primitive root (standard form): omega = g^((p-1)/N)
+  uint32_t c_m;    // coset representative c (Montgomery form): the points are c omega^t
   uint32_t half;   // (p - 1) / 2
   uint32_t pad;
 };
@@ -42,8 +42,8 @@ struct Tables {
   // transform tables for the first Tt primes, row length NT
   const uint32_t* tw;    // [Tt][NT/2] omega^i, omega of order NT (Montgomery)
   const uint32_t* itw;   // [Tt][NT/2] omega^-i (Montgomery)
-  const uint32_t* cp;    // [Tt][NT] g^i (Montgomery)
-  const uint32_t* icp;   // [Tt][NT] g^-i (standard form)
+  const uint32_t* cp;    // [Tt][NT] c^i, c the coset representative (Montgomery)
+  const uint32_t* icp;   // [Tt][NT] c^-i (standard form)
   const uint32_t* ninv;  // [Tt][kLogNMax + 1] 2^-s (Montgomery form)
   // packed twiddles [Tt][NT]: twp[len + j] = omega_{2 len}^j, itwp[len + j] = omega_{2 len}^-j
   // (len = 1, 2, ..., NT/2; j < len; entry 0 is 1), Montgomery form
@@ -130,6 +130,45 @@ __device__ __forceinline__ int find_item(const int64_t* off, int n, int64_t item
 
 __device__ __forceinline__ void set_status(int32_t* st, int32_t code) {
   if (st) atomicCAS(st, 0, code);
+}
+
+// Debug bounds checks, compiled in with -DBS_DEBUG_CHECKS (the library built by
+// build(debug=True)): a failed check records kErrInternal in the call's status word and
+// the site number (kDbg*) in its third word, and the guarded access is skipped, so a bad
+// index is reported to the host instead of faulting.  Without the flag every check is
+// the constant true and costs nothing.
+enum DebugSite : int32_t {
+  kDbgEvalIn = 11, kDbgEvalOut = 12, kDbgEvalTab = 13, kDbgEvalPf = 14,
+  kDbgUniIn = 21, kDbgUniOut = 22, kDbgUniStat = 23, kDbgUniPrime = 24,
+  kDbgInttIn = 31, kDbgInttOut = 32, kDbgInttSel = 33, kDbgInttTab = 34,
+  kDbgCrtIn = 41, kDbgCrtSel = 42, kDbgCrtOut = 43, kDbgCrtWs = 44, kDbgCrtGinv = 45,
+  kDbgCrtPp = 46,
+};
+#ifdef BS_DEBUG_CHECKS
+__device__ __forceinline__ bool dbg_ok(bool cond, int32_t* st, int32_t site) {
+  if (!cond && st) {
+    atomicCAS(st, 0, kErrInternal);
+    atomicCAS(st + 2, 0, site);
+  }
+  return cond;
+}
+#else
+__device__ __forceinline__ constexpr bool dbg_ok(bool, int32_t*, int32_t) { return true; }
+#endif
+// elements of a job's buffers, from its plan (a device-planned job's capacities are at
+// least these)
+__device__ __forceinline__ int64_t job_ev_words(const Job* J) {
+  return (int64_t)J->plan.k_total * J->rows * J->plan.N;
+}
+__device__ __forceinline__ int64_t job_vals_words(const Job* J) { return (int64_t)J->plan.k_total * J->plan.N; }
+__device__ __forceinline__ int64_t job_rmod_words(const Job* J) {
+  return (int64_t)J->plan.k_need * (J->plan.D + 1);
+}
+__device__ __forceinline__ int64_t job_out_words(const Job* J) {
+  return (int64_t)(J->cap_deg + 1) * J->cap_limbs;
+}
+__device__ __forceinline__ int64_t grid_words(const Grid& g) {
+  return (int64_t)(g.dx + 1) * (g.dy + 1) * g.L;
 }
 
 }  // namespace bs

@@ -14,10 +14,12 @@ namespace bs {
 // for a batch (the device-planned single job always uses the defaults)
 struct Tune {
   int eval_warps = 8;           // rows (one warp each) per evaluation block, 1..8
-  int eval_blocks_per_sm = 8;   // cap of the persistent evaluation grid
+  int eval_blocks_per_sm = 4;   // cap of the persistent evaluation grid
   int uni_threads[kNumUniClasses] = {128, 128, 128, 128, 128, 128};  // 64, 128 or 256
   int crt_tile = 8;             // coefficients (one warp each) per reconstruction block, 1..8
   int crt_blocks_per_sm = 4;    // cap of the persistent reconstruction grid
+  int eval_independent = 1;     // 1: independent-warp evaluation (k_eval_iw), rows per item 1;
+                                // 0: blocks of eval_warps rows of one prime (k_eval_w)
 };
 constexpr int kUniThreadChoices[3] = {64, 128, 256};
 }  // namespace bs
@@ -76,6 +78,10 @@ struct MetaBounds {
   int32_t D, logN, rows, len, k_total, k_need, out_limbs;
 };
 
+// upper bounds of a resultant job from the grids' extents and limb counts only (the sizes
+// of the device-planned entry points' workspace); BS_ERR_RANGE beyond the supported sizes
+int meta_bounds(const bs_bipoly* f, const bs_bipoly* g, int var, MetaBounds* mb);
+
 struct StageLaunch {
   const Job* jobs;
   WorkList eval, intt, intt_w, crt;
@@ -90,6 +96,7 @@ struct StageLaunch {
   int64_t eval_items, intt_items, intt_w_items, crt_items;
   int64_t evw_items[kNumEvalClasses], evw_any_items;
   int eval_warps = 8, eval_blocks_per_sm = 8, crt_tile = kCrtTile, crt_blocks_per_sm = 4;
+  bool eval_independent = false;  // k_eval_iw (work lists count single rows)
   bool pdl = false;  // programmatic dependent launch between the stage kernels
   int uni_threads[kNumUniClasses] = {kUniTile, kUniTile, kUniTile, kUniTile, kUniTile, kUniTile};
   int64_t uni_items[kNumUniClasses];
@@ -109,6 +116,8 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
 }  // namespace bs
 
 int ctx_fail(bs_ctx* ctx, int code, const std::string& msg);
+// the host message of a device status word [status, rejected, debug site, -]
+std::string device_failure_detail(const int32_t* st);
 int ctx_cuda(bs_ctx* ctx, cudaError_t e, const char* what);
 int ensure_workspace(bs_ctx* ctx, size_t bytes);
 void ctx_release_extra(bs_ctx* ctx);

@@ -85,55 +85,6 @@ static uint32_t residue_of(const uint32_t* c, int L, uint32_t p) {
   return (uint32_t)r;
 }
 
-// the exact psc sequence of (a, b) as owned host polynomials
-static int psc_owned(bs_ctx* ctx, const bs_bipoly* a, const bs_bipoly* b, int var, std::vector<HostPoly>* out) {
-  int32_t q = 0;
-  int rc = bs_psc(ctx, a, b, var, 0, &q, nullptr);
-  if (rc) return rc;
-  out->assign(q, HostPoly{});
-  if (q == 0) return BS_OK;
-  std::vector<bs_upoly> sr(q, bs_upoly{0, 0, nullptr});
-  rc = bs_psc(ctx, a, b, var, q, &q, sr.data());
-  if (rc) return rc;
-  for (int i = 0; i < q; ++i) {
-    (*out)[i].c.assign((size_t)(std::max(sr[i].deg, 0) + 1) * sr[i].limbs, 0u);
-    sr[i].c = (*out)[i].c.data();
-  }
-  rc = bs_psc(ctx, a, b, var, q, &q, sr.data());
-  if (rc) return rc;
-  for (int i = 0; i < q; ++i) {
-    (*out)[i].u = sr[i];
-    (*out)[i].u.c = (*out)[i].c.data();
-  }
-  return BS_OK;
-}
-
-// Teissier's Q up to a nonzero constant: with lc(f) constant in the eliminated variable,
-// h = gcd(f_x, f_y) has a constant leading coefficient, and at every point the first
-// principal subresultant coefficient of f_x and f_y that is not identically zero, sr_d
-// with d = deg h, is that constant's power times res(f_x / h, f_y / h) (the cofactor
-// property of subresultants); so Q is sr_d as a polynomial (1 when all sr_i vanish).
-static int teissier(bs_ctx* ctx, const bs_bipoly* f, int var, HostPoly* Q, int* d_out) {
-  std::vector<uint32_t> xbuf, ybuf;
-  bs_bipoly fx, fy;
-  grid_derivative(*f, 1 - var, &xbuf, &fx);
-  grid_derivative(*f, var, &ybuf, &fy);
-  std::vector<HostPoly> sr;
-  int rc = psc_owned(ctx, &fx, &fy, var, &sr);
-  if (rc) return rc;
-  int d = 0;
-  while (d < (int)sr.size() && sr[d].u.deg < 0) ++d;
-  *d_out = d;
-  if (d < (int)sr.size()) {
-    *Q = std::move(sr[d]);
-    Q->u.c = Q->c.data();
-  } else {
-    Q->c.assign(1, 1u);
-    Q->u = bs_upoly{0, 1, Q->c.data()};
-  }
-  return BS_OK;
-}
-
 static int run_fiber(bs_ctx* ctx, const bs_bipoly* f, int var, int mode, int cap, int32_t* degs, int32_t* s_out,
                      int64_t* N_out, uint32_t* p_out) {
   if (!f || f->deg_x < 0 || f->deg_y < 0 || f->limbs < 1 || !f->c)
@@ -305,26 +256,4 @@ extern "C" int bs_fiber_count(bs_ctx* ctx, const bs_bipoly* f, int var, int mode
     return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
   if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
   return run_fiber(ctx, f, var, mode, cap, degs, s, N, p);
-}
-
-extern "C" int bs_teissier_q(bs_ctx* ctx, const bs_bipoly* f, int var, bs_upoly* Q, int32_t* d) {
-  if (!ctx) return BS_ERR_ARG;
-  if (!f || !Q || !d || (var != 0 && var != 1)) return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
-  if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
-  if (f->deg_x < 0 || f->deg_y < 0 || f->limbs < 1 || !f->c) return ctx_fail(ctx, BS_ERR_ARG, "bad bivariate polynomial");
-  if (f->limbs >= kMaxLimbs) return ctx_fail(ctx, BS_ERR_RANGE, "the derivatives need more than 64 limbs");
-  bool clc = true;
-  if (lead_degree(*f, var, &clc) < 0) return ctx_fail(ctx, BS_ERR_ZERO, "the zero polynomial");
-  if (!clc) return ctx_fail(ctx, BS_ERR_ARG, "the leading coefficient is not constant (vertical asymptote)");
-  HostPoly q;
-  int dd = 0;
-  int rc = teissier(ctx, f, var, &q, &dd);
-  if (rc) return rc;
-  *d = dd;
-  if (!Q->c) {  // size query
-    Q->deg = q.u.deg;
-    Q->limbs = q.u.limbs;
-    return BS_OK;
-  }
-  return put_result(ctx, q.u.c, q.u.limbs, q.u.deg, Q);
 }

@@ -57,11 +57,21 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   int g;
   const PfHint pf{L.kt_max, 1 << L.logN_max, L.kmax};
   for (int c = 0; c < kNumEvalClasses; ++c) {
-    g = grid_for(L.evw_items[c], (int64_t)sms * L.eval_blocks_per_sm);
-    if (g) launch_eval_w(c, g, L.eval_warps, s, L.jobs, L.evw[c], Tv, pf);
+    if (L.eval_independent) {  // items are rows, eight warps per block
+      g = grid_for((L.evw_items[c] + 7) / 8, (int64_t)sms * L.eval_blocks_per_sm);
+      if (g) launch_eval_iw(c, g, s, L.jobs, L.evw[c], Tv, pf);
+    } else {
+      g = grid_for(L.evw_items[c], (int64_t)sms * L.eval_blocks_per_sm);
+      if (g) launch_eval_w(c, g, L.eval_warps, s, L.jobs, L.evw[c], Tv, pf);
+    }
   }
-  g = grid_for(L.evw_any_items, (int64_t)sms * 8);
-  if (g) launch_eval_w(-1, g, kEvalThreads / 32, s, L.jobs, L.evw_any, Tv, pf);
+  if (L.eval_independent) {
+    g = grid_for((L.evw_any_items + 7) / 8, (int64_t)sms * 4);
+    if (g) launch_eval_iw(-1, g, s, L.jobs, L.evw_any, Tv, pf);
+  } else {
+    g = grid_for(L.evw_any_items, (int64_t)sms * 8);
+    if (g) launch_eval_w(-1, g, kEvalThreads / 32, s, L.jobs, L.evw_any, Tv, pf);
+  }
   // persistent blocks of C = N / 1024 warps, about 16 warps per SM; a device plan sizes
   // this launch from the extents and usually leaves it empty, so there it stays small
   const int ecw = std::max(2, L.maxN >> 10);
@@ -167,7 +177,8 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   mark(ctx, 0, s);
   // the plan kernel receives the job by value, zeroes its prime flags and stores the
   // planned job for the stage kernels
-  launch_plan_single(s, J, dj, offs, Tv);
+  const bool indep = ctx->tune.eval_independent != 0;
+  launch_plan_single(s, J, dj, offs, Tv, indep ? 1 : kEvalThreads / 32);
   StageLaunch L;
   L.jobs = dj;
   const bool wsize = mb.logN <= kWarpLogNMax;  // the actual size is at most the bound
@@ -186,7 +197,8 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   L.crt = WorkList{nullptr, offs + kOffCrt, 1};
   // the transform size is known on the device only: one kernel dispatches per job
   L.evw_any = WorkList{nullptr, offs + kOffEvalW, 1};
-  L.evw_any_items = (int64_t)mb.k_total * ((mb.rows + 7) / 8);
+  L.eval_independent = indep;
+  L.evw_any_items = indep ? (int64_t)mb.k_total * mb.rows : (int64_t)mb.k_total * ((mb.rows + 7) / 8);
   L.eval_items = wsize ? 0 : (int64_t)mb.k_total * mb.rows;
   // a single job has few primes: one block per prime (no second, possibly empty launch)
   L.intt_w_items = 0;

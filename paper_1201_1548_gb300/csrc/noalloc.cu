@@ -24,7 +24,8 @@ std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
 
 // device address of the static scratch array on the current device (set-up on the first
-// call per device; the caller has made ctx->device current)
+// call per device; the caller has made ctx->device current).  The address is kept for the
+// life of the process: a device reset that rebuilds the primary context is not supported.
 int scratch_address(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return kErrArg;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -61,31 +62,10 @@ extern "C" int bs_resultant_device_noalloc(bs_ctx* ctx, const bs_bipoly* f, cons
   if (rc) return ctx_fail(ctx, rc, "problem exceeds the supported range");
   if (out->deg < dcap || out->limbs < lcap)
     return ctx_fail(ctx, BS_ERR_CAPACITY, "output capacity below bs_resultant_bounds()");
+  // the workspace bounds of the allocating device entry point, from the same function
   MetaBounds mb;
-  {
-    const int fe = var ? f->deg_y : f->deg_x, ge = var ? g->deg_y : g->deg_x;
-    // the same quantities bs_resultant_bounds derived, recomputed for the layout
-    const HostPrimes& H = host_primes();
-    auto Sbound = [&](int rows, int cols, int L) {
-      UF c = uf_make(1, 32 * L - 1, false);
-      UF l1 = uf_mul(uf_make((uint64_t)cols, 0, false), c);
-      return uf_mul(uf_make((uint64_t)rows, 0, false), uf_mul(l1, l1));
-    };
-    const int fo = var ? f->deg_x : f->deg_y, go = var ? g->deg_x : g->deg_y;
-    Plan P = finish_plan(Sbound(fe + 1, fo + 1, f->limbs), fe, f->deg_x + f->deg_y, fo,
-                         32 * f->limbs, Sbound(ge + 1, go + 1, g->limbs), ge,
-                         g->deg_x + g->deg_y, go, 32 * g->limbs, H.lg_prefix.data(),
-                         (int)H.p.size());
-    if (P.status) return ctx_fail(ctx, P.status, "problem exceeds the supported range");
-    mb.D = dcap;
-    mb.logN = 0;
-    while ((1 << mb.logN) < dcap + 1) ++mb.logN;
-    mb.rows = (fe + 1) + (ge + 1);
-    mb.len = (fe > ge ? fe : ge) + 1;
-    mb.k_total = P.k_total > 1 ? P.k_total : 1;
-    mb.k_need = P.k_need > 1 ? P.k_need : 1;
-    mb.out_limbs = P.out_limbs;
-  }
+  rc = meta_bounds(f, g, var, &mb);
+  if (rc) return ctx_fail(ctx, rc, "problem exceeds the supported range");
   const int cls = uni_class_of(mb.len);
   if (cls < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree in the eliminated variable above 64");
   // this call never grows the context's tables
@@ -108,7 +88,14 @@ extern "C" int bs_resultant_device_noalloc(bs_ctx* ctx, const bs_bipoly* f, cons
                         " bytes of scratch; the static scratch array holds 33554432 bytes");
   void* scratch = nullptr;
   rc = scratch_address(ctx->device, &scratch);
-  if (rc) return ctx_fail(ctx, rc, "cudaGetSymbolAddress of the static scratch failed");
+  if (rc) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      return ctx_fail(ctx, rc, "the first call on a device looks up the static scratch; make it "
+                               "before the stream capture begins");
+    cudaGetLastError();
+    return ctx_fail(ctx, rc, "cudaGetSymbolAddress of the static scratch failed");
+  }
   char* base = (char*)scratch;
   Job J;
   std::memset(&J, 0, sizeof(J));

@@ -59,6 +59,50 @@ __global__ void __launch_bounds__(kUniMaxThreads) k_psc(const Job* jobs, WorkLis
   }
 }
 
+// ---- the subresultant stage: S_d(A, B) at one (prime, point) per thread ------------------
+// The job's value slices j = 0..d receive the coefficient of y^j.  A point where a
+// leading coefficient vanishes rejects its prime (the rule of the resultant).
+template <int L>
+__global__ void __launch_bounds__(kUniMaxThreads) k_sres(const Job* jobs, WorkList wl, Tables T, int d) {
+  const int64_t total = wl.off[wl.n];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int ji = find_item(wl.off, wl.n, g);
+    const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
+    const int logN = J->plan.logN;
+    const int64_t inst = g - wl.off[ji];
+    const int N = 1 << logN;
+    const int q = (int)(inst >> logN);
+    const int t = (int)(inst & (N - 1));
+    const int me = J->plan.me, ne = J->plan.ne;
+    const PrimeConst pc = T.pc[q];
+    const Mod M{pc.p, pc.pinv};
+    const uint32_t* bf = J->ev + (int64_t)q * J->rows * N + t;
+    const uint32_t* bg = bf + (int64_t)(me + 1) * N;
+    uint32_t A[Arr<L>::N], B[Arr<L>::N];
+#pragma unroll
+    for (int s = 0; s < Arr<L>::N; ++s) {
+      A[s] = (s <= me) ? __ldg(bf + (int64_t)(me - s) * N) : 0u;
+      B[s] = (s <= ne) ? __ldg(bg + (int64_t)(ne - s) * N) : 0u;
+    }
+    if (A[0] == 0 || B[0] == 0) J->pstat[q] = 1;  // unlucky: a leading coefficient vanishes
+    if (!sres_seq<L>(A, me + 1, B, ne + 1, d, M, pc.one_m, J->vals + inst, J->psc_stride))
+      set_status(J->status, kErrInternal);
+  }
+}
+
+static void launch_sres(int cls, int grid, int threads, cudaStream_t s, const Job* jobs, WorkList wl,
+                        Tables T, int d) {
+  switch (cls) {
+    case 0: k_sres<8><<<grid, threads, 0, s>>>(jobs, wl, T, d); break;
+    case 1: k_sres<16><<<grid, threads, 0, s>>>(jobs, wl, T, d); break;
+    case 2: k_sres<24><<<grid, threads, 0, s>>>(jobs, wl, T, d); break;
+    case 3: k_sres<33><<<grid, threads, 0, s>>>(jobs, wl, T, d); break;
+    case 4: k_sres<48><<<grid, threads, 0, s>>>(jobs, wl, T, d); break;
+    default: k_sres<65><<<grid, threads, 0, s>>>(jobs, wl, T, d); break;
+  }
+}
+
 static void launch_psc(int cls, int grid, int threads, cudaStream_t s, const Job* jobs, WorkList wl,
                        Tables T) {
   switch (cls) {
@@ -75,7 +119,8 @@ static void launch_psc(int cls, int grid, int threads, cudaStream_t s, const Job
 struct PscPlan {
   Plan P;
   bool modp = false;  // one good prime, residues only (no reconstruction)
-  int q = 0, rows = 0;
+  int sres_d = -1;    // >= 0: the coefficients of S_d instead of the psc sequence
+  int q = 0, rows = 0;  // q: output polynomials (sr_0..sr_(q-1), or the d + 1 of S_d)
   size_t o_jobs = 0, o_ev_off = 0, o_psc_off = 0, o_ids = 0, o_intt_off = 0, o_crt_off = 0;
   size_t o_status = 0, o_pstat = 0, o_in = 0, up_bytes = 0;
   size_t o_ev = 0, o_vals = 0, o_rmod = 0, o_sel = 0;
@@ -89,9 +134,11 @@ static int check_grid(bs_ctx* ctx, const bs_bipoly* p) {
   return 0;
 }
 
-static int psc_plan(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, bool modp, PscPlan* pp) {
+static int psc_plan(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, bool modp, PscPlan* pp,
+                    int sres_d = -1) {
   PscPlan& S = *pp;
   S.modp = modp;
+  S.sres_d = sres_d;
   const HostPrimes& H = host_primes();
   const Grid gf{f->c, f->deg_x, f->deg_y, f->limbs}, gg{g->c, g->deg_x, g->deg_y, g->limbs};
   S.P = plan_host(gf, gg, var, H.lg_prefix.data(), (int)H.p.size(), H.p.data());
@@ -104,6 +151,10 @@ static int psc_plan(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var
   if (S.q <= 0) {
     S.q = 0;
     return 0;
+  }
+  if (sres_d >= 0) {  // S_d is defined for d below the smaller degree
+    if (sres_d >= S.q) return ctx_fail(ctx, BS_ERR_ARG, "subresultant index out of range");
+    S.q = sres_d + 1;
   }
   const Plan& P = S.P;
   if (uni_class_of(std::max(P.me, P.ne) + 1) < 0)
@@ -223,7 +274,11 @@ static int psc_launch(bs_ctx* ctx, const PscPlan& S, const bs_bipoly* f, const b
     const int cls = uni_class_of(std::max(P.me, P.ne) + 1);
     const int th = 128;
     const int grid = (int)std::min<int64_t>((po[1] + th - 1) / th, (int64_t)sms * std::max(1, ctx->occ[cls][1]));
-    launch_psc(cls, grid, th, s, dj, WorkList{nullptr, (const int64_t*)(base + S.o_psc_off), 1}, Tv);
+    const WorkList wl_p{nullptr, (const int64_t*)(base + S.o_psc_off), 1};
+    if (S.sres_d >= 0)
+      launch_sres(cls, grid, th, s, dj, wl_p, Tv, S.sres_d);
+    else
+      launch_psc(cls, grid, th, s, dj, wl_p, Tv);
   }
   const WorkList wl_i{(const int32_t*)(base + S.o_ids), (const int64_t*)(base + S.o_intt_off), q};
   if (P.logN <= kWarpInttLogNMax)
@@ -260,7 +315,7 @@ static int psc_launch(bs_ctx* ctx, const PscPlan& S, const bs_bipoly* f, const b
 static int psc_finish(bs_ctx* ctx, const PscPlan& S, const char* hd, bs_upoly* out) {
   const Plan& P = S.P;
   const int32_t* st = (const int32_t*)(hd + (S.o_status_dn - S.dn_start));
-  if (st[0]) return ctx_fail(ctx, st[0], "device stage reported a failure");
+  if (st[0]) return ctx_fail(ctx, st[0], device_failure_detail(st));
   for (int i = 0; i < S.q; ++i) {
     const uint32_t* src = (const uint32_t*)(hd + (S.o_out - S.dn_start)) + (size_t)i * (P.D + 1) * P.out_limbs;
     int deg = P.D;
@@ -278,17 +333,20 @@ static int psc_finish(bs_ctx* ctx, const PscPlan& S, const char* hd, bs_upoly* o
 }
 
 static int run_psc(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, int cap_q, int32_t* q_out,
-                   bs_upoly* out) {
+                   bs_upoly* out, int sres_d = -1) {
   if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
   int rc = check_grid(ctx, f);
   if (!rc) rc = check_grid(ctx, g);
   if (rc) return rc;
   cudaSetDevice(ctx->device);
   PscPlan S;
-  rc = psc_plan(ctx, f, g, var, false, &S);
+  rc = psc_plan(ctx, f, g, var, false, &S, sres_d);
   if (rc) return rc;
   *q_out = S.q;
-  if (S.q == 0) return BS_OK;
+  if (S.q == 0) {
+    if (sres_d >= 0) return ctx_fail(ctx, BS_ERR_ARG, "subresultant index out of range");
+    return BS_OK;
+  }
   if (!out || !out[0].c) {  // size query
     for (int i = 0; out && i < std::min(cap_q, S.q); ++i) {
       out[i].deg = S.P.D;
@@ -342,7 +400,7 @@ static int run_psc_modp(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int
   if (rc) return rc;
   const char* hd = (const char*)ctx->h_down;
   const int32_t* st = (const int32_t*)(hd + (S.o_status_dn - S.dn_start));
-  if (st[0]) return ctx_fail(ctx, st[0], "device stage reported a failure");
+  if (st[0]) return ctx_fail(ctx, st[0], device_failure_detail(st));
   const int32_t* sel = (const int32_t*)(hd + (S.o_sel - S.dn_start));
   *p_out = host_primes().p[sel[0]];
   const int D = S.P.D;
@@ -366,6 +424,14 @@ extern "C" int bs_psc_modp(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, 
   if (!ctx) return BS_ERR_ARG;
   if (!f || !g || !q || !dmax || !p || (var != 0 && var != 1)) return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
   return run_psc_modp(ctx, f, g, var, q, dmax, deg, coef, p);
+}
+
+extern "C" int bs_subresultant(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, int d,
+                               int cap, int32_t* n, bs_upoly* out) {
+  if (!ctx) return BS_ERR_ARG;
+  if (!f || !g || !n || (var != 0 && var != 1) || d < 0 || cap < 0)
+    return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
+  return run_psc(ctx, f, g, var, cap, n, out, d);
 }
 
 extern "C" int bs_psc(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var, int cap_q, int32_t* q,

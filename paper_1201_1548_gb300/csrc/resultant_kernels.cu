@@ -51,12 +51,14 @@ struct PfRange {
   size_t bytes;
 };
 
-__device__ void prefetch_late_tables(const Tables& T, int kt, int N, int kn, int rank, int ranks) {
+__device__ void prefetch_late_tables(const Tables& T, int kt, int N, int kn, int rank, int ranks,
+                                     int32_t* st) {
   kt = min(kt, T.Tt);
   kn = min(kn, T.Tg);
   const int K = min(kn, T.WK);
   int64_t mwords = 0;  // the M_k block of k = K
   if (K >= 1) mwords = (int64_t)K * ws_len(K);
+  if (!dbg_ok(K < 1 || T.ws_moff[K] + mwords <= T.ws_m_words, st, kDbgEvalPf)) return;
   const PfRange R[6] = {
       {T.itwp, sizeof(uint32_t) * (size_t)kt * T.NT},
       {T.icp, sizeof(uint32_t) * (size_t)kt * T.NT},
@@ -284,7 +286,8 @@ __device__ int prime_count_warp(const int64_t* lg_prefix, int T, int64_t need) {
   }
 }
 
-__global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, int64_t* offs, Tables T) {
+__global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, int64_t* offs, Tables T,
+                                                              int eval_group) {
   constexpr int kRows = kPlanThreads / 16;  // row slots per half
   __shared__ UF sh_uf[2][kRows];
   __shared__ int sh_int[2][kSlotInts * kRows];
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
     // intt, smem intt, crt tiles
     const bool wsize = P.logN <= kWarpLogNMax;
     for (int s = 0; s < kNumOffs; s += 2) offs[s] = 0;
-    offs[kOffEvalW + 1] = (run && wsize) ? (int64_t)P.k_total * ((J.rows + 7) / 8) : 0;
+    offs[kOffEvalW + 1] = (run && wsize) ? (int64_t)P.k_total * ((J.rows + eval_group - 1) / eval_group) : 0;
     offs[kOffEvalS + 1] = (run && !wsize) ? (int64_t)P.k_total * J.rows : 0;
     offs[kOffUni + 1] = run ? ((int64_t)P.k_total << P.logN) : 0;  // instances
     offs[kOffInttW + 1] = 0;  // a single job interpolates one block per prime
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(kEvalBigMaxWarps * 32) k_eval(const Job* jobs,
         uint32_t acc = 0;
         for (int o = pt; o <= eo; o += N) {
           const uint32_t x = residue_m(coef_ptr(G, var, e, o), G.L, pw, mpw, M.p, M.pinv);
-          const uint32_t s = (o < T.NT) ? __ldg(cp + o) : mpow(pc.g_m, (uint32_t)o, pc.one_m, M);
+          const uint32_t s = (o < T.NT) ? __ldg(cp + o) : mpow(pc.c_m, (uint32_t)o, pc.one_m, M);
           acc = madd(acc, mmul(x, s, M), M.p);
         }
         v[r] = acc;
@@ -466,7 +469,8 @@ __global__ void __launch_bounds__(kEvalBigMaxWarps * 32) k_eval(const Job* jobs,
 // Residues of row e of f (or g) times g^o, folded modulo N, in layout A: register r of
 // lane l holds element 32 r + l.  Only the first NZ registers can be nonzero when the
 // row has at most 32 NZ coefficients (and N > that count).
-template <int R>
+// NZ: registers of layout A that can hold a coefficient (the others are set to zero)
+template <int R, int NZ = R>
 __device__ __forceinline__ void eval_load_row(uint32_t (&v)[R], const Job* J, int q, int row,
                                               const Tables& T, uint32_t* sw, const uint32_t* s_cp,
                                               const PrimeConst& pc, const Mod& M, int N) {
@@ -481,18 +485,21 @@ __device__ __forceinline__ void eval_load_row(uint32_t (&v)[R], const Job* J, in
   const int eo = ext_o(G, var);
   // residues times g^o, folded modulo N, staged in this warp's shared slice (rolled loop)
   const int top = min(eo + 1, N);
+  const int64_t gw = grid_words(G);
   for (int t = lane; t < top; t += 32) {
     uint32_t acc = 0;
     for (int o = t; o <= eo; o += N) {
-      const uint32_t x = residue_m(coef_ptr(G, var, e, o), G.L, pw, mpw, M.p, M.pinv);
-      const uint32_t s = (o < N) ? s_cp[o] : mpow(pc.g_m, (uint32_t)o, pc.one_m, M);
+      const uint32_t* cp = coef_ptr(G, var, e, o);
+      if (!dbg_ok(cp >= G.c && cp + G.L <= G.c + gw, J->status, kDbgEvalIn)) continue;
+      const uint32_t x = residue_m(cp, G.L, pw, mpw, M.p, M.pinv);
+      const uint32_t s = (o < N) ? s_cp[o] : mpow(pc.c_m, (uint32_t)o, pc.one_m, M);
       acc = madd(acc, mmul(x, s, M), M.p);
     }
     sw[t] = acc;
   }
   __syncwarp();
 #pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = (32 * r + lane < top) ? sw[32 * r + lane] : 0u;
+  for (int r = 0; r < R; ++r) v[r] = (r < NZ && 32 * r + lane < top) ? sw[32 * r + lane] : 0u;
   __syncwarp();  // the transposes reuse sw
 }
 
@@ -504,14 +511,16 @@ __device__ __forceinline__ void eval_row_nz(const Job* J, int q, int row, const 
   constexpr uint32_t MASK = (NZ >= 32) ? 0xffffffffu : ((1u << NZ) - 1u);
   const int lane = threadIdx.x & 31;
   uint32_t v[R];
-  eval_load_row<R>(v, J, q, row, T, sw, s_cp, pc, M, N);
+  eval_load_row<R, (NZ < R ? NZ : R)>(v, J, q, row, T, sw, s_cp, pc, M, N);
   if constexpr (R == 32)
     warp_dif_1024_pk<MASK>(v, sw, s_tw, M);
   else
     warp_dif_pk<R, MASK>(v, s_tw, M, pc.one_m);
   uint32_t* dst = J->ev + ((int64_t)q * J->rows + row) * N;
+  if (dbg_ok(((int64_t)q * J->rows + row + 1) * N <= job_ev_words(J), J->status, kDbgEvalOut)) {
 #pragma unroll
-  for (int r = 0; r < R; ++r) dst[32 * r + lane] = v[r];
+    for (int r = 0; r < R; ++r) dst[32 * r + lane] = v[r];
+  }
   __syncwarp();
 }
 
@@ -527,7 +536,8 @@ __device__ __forceinline__ void eval_row_small(const Job* J, int q, int row, con
     warp_dif_short(v[0], N, s_tw, M, pc.one_m);
   else
     warp_dif_pk<1, 1u>(v, s_tw, M, pc.one_m);
-  if (lane < N) J->ev[((int64_t)q * J->rows + row) * N + lane] = v[0];
+  if (lane < N && dbg_ok(((int64_t)q * J->rows + row + 1) * N <= job_ev_words(J), J->status, kDbgEvalOut))
+    J->ev[((int64_t)q * J->rows + row) * N + lane] = v[0];
   __syncwarp();
 }
 
@@ -541,12 +551,12 @@ __device__ __forceinline__ void eval_row_class(const Job* J, int q, int row, con
   if constexpr (R == 1) {
     eval_row_small(J, q, row, T, sw, s_tw, s_cp, pc, M, J->plan.N);
   } else {
-    // how many registers of layout A the row's coefficients reach
+    // how many registers of layout A the row's coefficients reach: rows of up to 64
+    // coefficients share one pruned variant (a second one for rows of up to 32 would save
+    // a few butterflies but doubles the code the warps of a block fetch)
     const bool isf = row <= J->plan.me;
     const int eo = ext_o(isf ? J->f : J->g, J->var);
-    if (R >= 4 && eo < 32)
-      eval_row_nz<R, 1>(J, q, row, T, sw, s_tw, s_cp, pc, M);
-    else if (R >= 4 && eo < 64)
+    if (R >= 4 && eo < 64)
       eval_row_nz<R, 2>(J, q, row, T, sw, s_tw, s_cp, pc, M);
     else
       eval_row_nz<R, 32>(J, q, row, T, sw, s_tw, s_cp, pc, M);
@@ -577,7 +587,8 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_w(const Job* jobs, Wor
       N = P0.N;
       kn = P0.k_need;
     }
-    prefetch_late_tables(T, kt, N, kn, blockIdx.x, min((int)gridDim.x, kPfIssuers));
+    prefetch_late_tables(T, kt, N, kn, blockIdx.x, min((int)gridDim.x, kPfIssuers),
+                         jobs[wl.ids ? wl.ids[0] : 0].status);
   }
   int cur_q = -1, cur_N = -1;
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
@@ -595,7 +606,8 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_w(const Job* jobs, Wor
       __syncthreads();
       const uint32_t* twq = T.twp + (int64_t)q * T.NT;
       const uint32_t* cpq = T.cp + (int64_t)q * T.NT;
-      for (int t = threadIdx.x; t < N; t += blockDim.x) {
+      const bool tab_ok = dbg_ok(q < T.Tt && N <= T.NT && N <= NS, J->status, kDbgEvalTab);
+      for (int t = threadIdx.x; t < N && tab_ok; t += blockDim.x) {
         s_tw[t] = __ldg(twq + t);
         s_cp[t] = __ldg(cpq + t);
       }
@@ -623,12 +635,94 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_w(const Job* jobs, Wor
   pdl_trigger();
 }
 
+// The same evaluation with independent warps: the work list counts single rows, each
+// warp takes any (job, prime, row) item, and the prime's packed twiddles and coset powers
+// are read through the L1 cache instead of being staged per block, so no block waits at
+// a barrier for a change of prime and no warp idles at the end of a prime's rows.
+template <int R>
+__global__ void __launch_bounds__(kEvalThreads, 4) k_eval_iw(const Job* jobs, WorkList wl,
+                                                             Tables T, PfHint pf) {
+  pdl_wait();
+  constexpr int NS = R == 0 ? (1 << kWarpLogNMax) : 32 * R;  // largest transform size
+  __shared__ uint32_t s_stage[kEvalThreads / 32][(R == 32 || R == 0) ? 33 * 32 : NS];
+  const int warp = threadIdx.x >> 5;
+  uint32_t* sw = s_stage[warp];
+  const int nw = blockDim.x >> 5;
+  const int64_t total = wl.off[wl.n];
+  if (threadIdx.x == 0 && blockIdx.x < kPfIssuers && total > 0) {
+    int kt = pf.kt, N = pf.N, kn = pf.kn;
+    if (kt < 0) {
+      const Plan& P0 = jobs[wl.ids ? wl.ids[0] : 0].plan;
+      kt = P0.k_total;
+      N = P0.N;
+      kn = P0.k_need;
+    }
+    prefetch_late_tables(T, kt, N, kn, blockIdx.x, min((int)gridDim.x, kPfIssuers),
+                         jobs[wl.ids ? wl.ids[0] : 0].status);
+  }
+  for (int64_t item = (int64_t)blockIdx.x * nw + warp; item < total; item += (int64_t)gridDim.x * nw) {
+    const int ji = find_item(wl.off, wl.n, item);
+    const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
+    const int64_t local = item - wl.off[ji];
+    const int rows = J->rows;
+    const int q = (int)(local / rows);
+    const int row = (int)(local - (int64_t)q * rows);
+    const int N = J->plan.N;
+    if (!dbg_ok(q < T.Tt && N <= T.NT && N <= NS, J->status, kDbgEvalTab)) continue;
+    const uint32_t* tw = T.twp + (int64_t)q * T.NT;
+    const uint32_t* cp = T.cp + (int64_t)q * T.NT;
+    const PrimeConst pc = T.pc[q];
+    const Mod M{pc.p, pc.pinv};
+    if constexpr (R > 0) {
+      eval_row_class<R>(J, q, row, T, sw, tw, cp, pc, M);
+    } else {
+      switch (J->plan.logN) {
+        case 0: case 1: case 2: case 3: case 4: case 5:
+          eval_row_class<1>(J, q, row, T, sw, tw, cp, pc, M); break;
+        case 6: eval_row_class<2>(J, q, row, T, sw, tw, cp, pc, M); break;
+        case 7: eval_row_class<4>(J, q, row, T, sw, tw, cp, pc, M); break;
+        case 8: eval_row_class<8>(J, q, row, T, sw, tw, cp, pc, M); break;
+        case 9: eval_row_class<16>(J, q, row, T, sw, tw, cp, pc, M); break;
+        default: eval_row_class<32>(J, q, row, T, sw, tw, cp, pc, M); break;
+      }
+    }
+  }
+  pdl_trigger();
+}
+
 // ------------------------------------------------------------------------------------
 // (c): univariate resultants, one per thread
 // ------------------------------------------------------------------------------------
 // Work list offsets count (prime, point) instances; thread i of the grid-stride sweep
 // takes instance i of the flat index space and finds its job by binary search, so any
 // block size works and no thread idles at the end of a job.
+template <int L, class AT>
+__device__ __forceinline__ void unires_instance(const Job* J, int64_t inst, const Tables& T, AT& A, AT& B) {
+  const int logN = J->plan.logN;
+  const int N = 1 << logN;
+  const int q = (int)(inst >> logN);
+  const int t = (int)(inst & (N - 1));
+  const int me = J->plan.me, ne = J->plan.ne;
+  const int rows = J->rows;
+  if (!dbg_ok(q < T.T && q < J->plan.k_total, J->status, kDbgUniPrime)) return;
+  const PrimeConst pc = T.pc[q];
+  const Mod M{pc.p, pc.pinv};
+  const int64_t b0 = (int64_t)q * rows * N + t;
+  const uint32_t* bf = J->ev + b0;
+  const uint32_t* bg = bf + (int64_t)(me + 1) * N;
+  if (!dbg_ok(b0 + (int64_t)(rows - 1) * N < job_ev_words(J), J->status, kDbgUniIn)) return;
+#pragma unroll
+  for (int s = 0; s < Arr<L>::N; ++s) {
+    A[s] = (s <= me) ? __ldg(bf + (int64_t)(me - s) * N) : 0u;
+    B[s] = (s <= ne) ? __ldg(bg + (int64_t)(ne - s) * N) : 0u;
+  }
+  if (A[0] == 0 || B[0] == 0) J->pstat[q] = 1;  // unlucky: a leading coefficient vanishes
+  uint32_t den;
+  uint32_t num = unires_numden<L>(A, me + 1, B, ne + 1, M, pc.one_m, &den);
+  if (dbg_ok(inst < job_vals_words(J), J->status, kDbgUniOut))
+    J->vals[inst] = mmul(num, minv(den, pc.one_m, M), M);
+}
+
 template <int L>
 __global__ void __launch_bounds__(kUniMaxThreads) k_unires(const Job* jobs, WorkList wl, Tables T) {
   pdl_wait();
@@ -636,28 +730,31 @@ __global__ void __launch_bounds__(kUniMaxThreads) k_unires(const Job* jobs, Work
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     const int ji = find_item(wl.off, wl.n, g);
-    const Job* J = jobs + (wl.ids ? wl.ids[ji] : ji);
-    const int logN = J->plan.logN;
-    const int64_t inst = g - wl.off[ji];
-    const int N = 1 << logN;
-    const int q = (int)(inst >> logN);
-    const int t = (int)(inst & (N - 1));
-    const int me = J->plan.me, ne = J->plan.ne;
-    const int rows = J->rows;
-    const PrimeConst pc = T.pc[q];
-    const Mod M{pc.p, pc.pinv};
-    const uint32_t* bf = J->ev + (int64_t)q * rows * N + t;
-    const uint32_t* bg = bf + (int64_t)(me + 1) * N;
     uint32_t A[Arr<L>::N], B[Arr<L>::N];
-#pragma unroll
-    for (int s = 0; s < Arr<L>::N; ++s) {
-      A[s] = (s <= me) ? __ldg(bf + (int64_t)(me - s) * N) : 0u;
-      B[s] = (s <= ne) ? __ldg(bg + (int64_t)(ne - s) * N) : 0u;
-    }
-    if (A[0] == 0 || B[0] == 0) J->pstat[q] = 1;  // unlucky: a leading coefficient vanishes
-    uint32_t den;
-    uint32_t num = unires_numden<L>(A, me + 1, B, ne + 1, M, pc.one_m, &den);
-    J->vals[inst] = mmul(num, minv(den, pc.one_m, M), M);
+    unires_instance<L>(jobs + (wl.ids ? wl.ids[ji] : ji), g - wl.off[ji], T, A, B);
+  }
+  pdl_trigger();
+}
+
+// The same with the polynomials' high entries in shared memory (SplitArr): blocks of
+// kSplitThreads threads, SplitK<L>::K register entries per polynomial, sized so that
+// SplitK<L>::blocks blocks fit on an SM.  For the degree-32 class this gives 18 warps per
+// SM instead of 16, enough to hold the 81 x 1024 images of a degree-32 discriminant in
+// one pass over the SMs.
+template <int L>
+__global__ void __maxnreg__(SplitK<L>::regs) k_unires_split(const Job* jobs, WorkList wl,
+                                                                                  Tables T) {
+  extern __shared__ uint32_t sm_split[];
+  constexpr int K = SplitK<L>::K, H = Arr<L>::N - K;
+  pdl_wait();
+  const int64_t total = wl.off[wl.n];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int ji = find_item(wl.off, wl.n, g);
+    SplitArr<L, K, kSplitThreads> A, B;
+    A.s = sm_split + threadIdx.x;
+    B.s = sm_split + H * kSplitThreads + threadIdx.x;
+    unires_instance<L>(jobs + (wl.ids ? wl.ids[ji] : ji), g - wl.off[ji], T, A, B);
   }
   pdl_trigger();
 }
@@ -693,7 +790,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
       const uint32_t* src = J->vals + ((int64_t)q << logN);
       const uint32_t* itq = T.itwp + (int64_t)q * T.NT;
       const uint32_t* icq = T.icp + (int64_t)q * T.NT;
-      for (int t = threadIdx.x; t < N; t += blockDim.x) {
+      const bool in_ok = dbg_ok(((int64_t)(q + 1) << logN) <= job_vals_words(J), J->status, kDbgInttIn) &&
+                         dbg_ok(q < T.Tt && N <= T.NT, J->status, kDbgInttTab);
+      for (int t = threadIdx.x; t < N && in_ok; t += blockDim.x) {
         sm[t] = src[t];
         sit[t] = __ldg(itq + t);
         sic[t] = __ldg(icq + t);
@@ -709,9 +808,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
     }
     __syncthreads();
     const int r = s_rank;
-    if (q == 0 && threadIdx.x == 0) {
-      if (s_good < k_need) set_status(J->status, kErrUnlucky);
-      if (J->rejected) atomicAdd(J->rejected, k_total - s_good);
+    if (q == 0) {
+      if (s_good < k_need) {
+        // too few good primes: the job fails.  The selection slots no good prime fills get
+        // a valid index and the job is marked, so that the reconstruction writes zeros
+        // for it instead of reading unset slots.
+        for (int j = s_good + (int)threadIdx.x; j < k_need; j += blockDim.x) J->sel[j] = 0;
+        if (threadIdx.x == 0) {
+          set_status(J->status, kErrUnlucky);
+          const_cast<Job*>(J)->plan.status = kErrUnlucky;
+        }
+      }
+      if (threadIdx.x == 0 && J->rejected) atomicAdd(J->rejected, k_total - s_good);
     }
     const bool good = J->pstat[q] == 0;
     __syncthreads();
@@ -722,16 +830,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
     dit_intt(sm, logN, sit, M);
     const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
     uint32_t* dst = J->rmod + (int64_t)r * (D + 1);
+    const bool out_ok = dbg_ok((int64_t)(r + 1) * (D + 1) <= job_rmod_words(J), J->status, kDbgInttOut);
     bool bad = false;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       const uint32_t v = mmul(mmul(sm[i], sic[i], M), ni, M);
-      if (i <= D)
-        dst[i] = v;
-      else if (v != 0)
+      if (i <= D) {
+        if (out_ok) dst[i] = v;
+      } else if (v != 0) {
         bad = true;
+      }
     }
     if (bad) set_status(J->status, kErrInternal);
-    if (threadIdx.x == 0) J->sel[r] = q;
+    if (threadIdx.x == 0 && dbg_ok(r < k_need, J->status, kDbgInttSel)) J->sel[r] = q;
     __syncthreads();
   }
   pdl_trigger();
@@ -752,6 +862,9 @@ __device__ __forceinline__ void intt_prime_warp(const Job* J, int q, int r, cons
   const PrimeConst pc = T.pc[q];
   const Mod M{pc.p, pc.pinv};
   const uint32_t* src = J->vals + ((int64_t)q << logN);
+  if (!dbg_ok(((int64_t)(q + 1) << logN) <= job_vals_words(J), J->status, kDbgInttIn) ||
+      !dbg_ok(q < T.Tt && N <= T.NT && N <= 32 * R, J->status, kDbgInttTab))
+    return;
   // the prime's packed inverse twiddles, staged in this warp's shared slice (all loads in
   // flight at once instead of one L2 round trip per butterfly)
   const uint32_t* Pg = T.itwp + (int64_t)q * T.NT;
@@ -769,19 +882,21 @@ __device__ __forceinline__ void intt_prime_warp(const Job* J, int q, int r, cons
   const uint32_t* icp = T.icp + (int64_t)q * T.NT;
   const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
   uint32_t* dst = J->rmod + (int64_t)r * (D + 1);
+  const bool out_ok = dbg_ok((int64_t)(r + 1) * (D + 1) <= job_rmod_words(J), J->status, kDbgInttOut);
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < R; ++k) {
     const int i = 32 * k + lane;
     if (i >= N) continue;
     const uint32_t x = mmul(mmul(v[k], icp[i], M), ni, M);
-    if (i <= D)
-      dst[i] = x;
-    else if (x != 0)
+    if (i <= D) {
+      if (out_ok) dst[i] = x;
+    } else if (x != 0) {
       bad = true;
+    }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(J->status, kErrInternal);
-  if (lane == 0) J->sel[r] = q;
+  if (lane == 0 && dbg_ok(r < J->plan.k_need, J->status, kDbgInttSel)) J->sel[r] = q;
   __syncwarp();  // Pi and sw are reused by the warp's next prime
 }
 
@@ -812,10 +927,14 @@ __global__ void __launch_bounds__(kInttWarps * 32) k_intt_w(const Job* jobs, Wor
         const int j = j0 + lane;
         good += __popc(__ballot_sync(0xffffffffu, j < k_total && J->pstat[j] == 0));
       }
-      if (lane == 0) {
-        if (good < k_need) set_status(J->status, kErrUnlucky);
-        if (J->rejected) atomicAdd(J->rejected, k_total - good);
+      if (good < k_need) {  // as in k_intt: a failed job with valid slots
+        for (int j = good + lane; j < k_need; j += 32) J->sel[j] = 0;
+        if (lane == 0) {
+          set_status(J->status, kErrUnlucky);
+          const_cast<Job*>(J)->plan.status = kErrUnlucky;
+        }
       }
+      if (lane == 0 && J->rejected) atomicAdd(J->rejected, k_total - good);
     }
     if (J->pstat[q] != 0 || r >= k_need) continue;  // uniform across the warp
     switch (J->plan.logN) {
@@ -1329,19 +1448,25 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
     const int nvalid = min(ncoef, D + 1 - i0);
     const int nl = min(min(P.out_limbs, lmax), T.LPP);
     for (int j = threadIdx.x; j < k; j += nthr) {
-      const int s = J->sel[j];
+      int s = J->sel[j];
+      if (!dbg_ok(s >= 0 && s < T.Tg && s < J->plan.k_total, J->status, kDbgCrtSel) || s < 0 || s >= T.Tg)
+        s = 0;  // never read outside the tables, whatever the slot holds
       const PrimeConst pc = T.pc[s];
       pq[j] = pc.p;
       pinvq[j] = pc.pinv;
       selq[j] = (uint32_t)s;
     }
+    const bool x_ok = dbg_ok((int64_t)(k - 1) * (D + 1) + i0 + nvalid <= job_rmod_words(J), J->status, kDbgCrtIn);
 #pragma unroll 4
     for (int t = threadIdx.x; t < k * kCrtTile; t += nthr) {  // columns >= tile stay unused
       const int j = t / kCrtTile, c = t - j * kCrtTile;
-      X[t] = (c < nvalid) ? J->rmod[(int64_t)j * (D + 1) + i0 + c] : 0u;
+      X[t] = (c < nvalid && x_ok) ? J->rmod[(int64_t)j * (D + 1) + i0 + c] : 0u;
     }
     const int L = ws_len(k);
-    if (k <= T.WK) {
+    if (k <= T.WK &&
+        dbg_ok(T.ws_moff[k] + (int64_t)k * L <= T.ws_m_words && k <= T.Tg && L <= kmax + 4 &&
+                   (int64_t)k * L <= (int64_t)kmax * kmax + (int64_t)kmax * lmax,
+               J->status, kDbgCrtWs)) {
       // weighted-sum tables, staged with the residues (they depend on k only; the Garner
       // path below overwrites them when the selected primes are not the first k):
       // M_k is k rows of L limbs, contiguous: one flat copy with many loads in flight
@@ -1362,6 +1487,7 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
     // weighted-sum path for table-ordered jobs with tabulated k; Garner otherwise
     const bool ws = table_order && k <= T.WK;
     if (!ws) {
+      dbg_ok(k <= kmax && nl <= lmax && nl <= T.LPP && k <= Tg, J->status, kDbgCrtGinv);
       for (int a = warp; a < k; a += nthr / 32) {
         const int64_t rowa = (int64_t)selq[a] * Tg;
 #pragma unroll 4
@@ -1374,6 +1500,7 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
     }
     __syncthreads();
     for (int c = warp; c < ncoef; c += nthr / 32) {
+      if (!dbg_ok(i0 + c <= J->cap_deg && J->cap_limbs <= lmax, J->status, kDbgCrtOut)) continue;
       if (c >= nvalid) {  // above the degree bound
         uint32_t* out = J->out + (int64_t)(i0 + c) * cap;
         for (int l = lane; l < cap; l += 32) out[l] = 0u;
@@ -1478,6 +1605,7 @@ template __global__ void k_unires<24>(const Job*, WorkList, Tables);
 template __global__ void k_unires<33>(const Job*, WorkList, Tables);
 template __global__ void k_unires<48>(const Job*, WorkList, Tables);
 template __global__ void k_unires<65>(const Job*, WorkList, Tables);
+template __global__ void k_unires_split<33>(const Job*, WorkList, Tables);
 
 // ------------------------------------------------------------------------------------
 // launchers (kernels are launched from the translation unit that defines them)
@@ -1498,6 +1626,20 @@ int uni_occupancy(int cls, int threads) {
     case 4: return occ1<48>(threads);
     default: return occ1<65>(threads);
   }
+}
+
+size_t uni_split_smem() {
+  return sizeof(uint32_t) * 2 * (size_t)(Arr<33>::N - SplitK<33>::K) * kSplitThreads;
+}
+
+int uni_split_occupancy() {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_unires_split<33>, kSplitThreads, uni_split_smem());
+  return b > 0 ? b : 1;
+}
+
+void launch_uni_split(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
+  launch_k(k_unires_split<33>, grid, kSplitThreads, uni_split_smem(), s, jobs, wl, T);
 }
 
 void launch_uni(int cls, int grid, int threads, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
@@ -1528,6 +1670,19 @@ void launch_eval(int grid, int warps, cudaStream_t s, const Job* jobs, WorkList 
   const size_t smem = sizeof(uint32_t) * ((size_t)1024 * warps + 1024 + (size_t)warps * 33 * 32);
   launch_k(k_eval, grid, warps * 32, smem, s, jobs, wl, T);
 }
+void launch_eval_iw(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T, PfHint pf) {
+  const int th = kEvalThreads;
+  switch (cls) {
+    case -1: launch_k(k_eval_iw<0>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 0: launch_k(k_eval_iw<1>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 1: launch_k(k_eval_iw<2>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 2: launch_k(k_eval_iw<4>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 3: launch_k(k_eval_iw<8>, grid, th, 0, s, jobs, wl, T, pf); break;
+    case 4: launch_k(k_eval_iw<16>, grid, th, 0, s, jobs, wl, T, pf); break;
+    default: launch_k(k_eval_iw<32>, grid, th, 0, s, jobs, wl, T, pf); break;
+  }
+}
+
 void launch_eval_w(int cls, int grid, int warps, cudaStream_t s, const Job* jobs, WorkList wl,
                    Tables T, PfHint pf) {
   const int th = warps * 32;
@@ -1551,8 +1706,8 @@ void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* j
                 Tables T, int kmax, int lmax, int staged, int skip_big) {
   launch_k(k_crt, grid, threads, smem, s, jobs, wl, T, kmax, lmax, staged, skip_big);
 }
-void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T) {
-  k_plan_single<<<1, kPlanThreads, 0, s>>>(J, dst, offs, T);
+void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T, int eval_group) {
+  k_plan_single<<<1, kPlanThreads, 0, s>>>(J, dst, offs, T, eval_group);
 }
 int set_dyn_smem_limit(const void* func, int optin) {
   cudaFuncAttributes a;

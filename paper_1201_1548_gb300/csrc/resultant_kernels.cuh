@@ -46,9 +46,13 @@ constexpr int kPfIssuers = 128;   // blocks that issue one prefetch chunk each
 // warps: rows per block (1 .. kEvalThreads / 32); the work list counts groups of that many rows
 void launch_eval_w(int cls, int grid, int warps, cudaStream_t s, const Job* jobs, WorkList wl,
                    Tables T, PfHint pf);
+// independent-warp evaluation: the work list counts single rows (eval_rows_per_item = 1)
+void launch_eval_iw(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T, PfHint pf);
 void launch_crt(int grid, int threads, size_t smem, cudaStream_t s, const Job* jobs, WorkList wl,
                 Tables T, int kmax, int lmax, int staged, int skip_big = 0);
-void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T);
+// eval_group: rows per item of the warp-evaluation work list (8 for k_eval_w blocks of
+// eight warps, 1 for the independent-warp kernel)
+void launch_plan_single(cudaStream_t s, const Job& J, Job* dst, int64_t* offs, Tables T, int eval_group);
 int set_stage_smem_limits(int optin);
 // launches of the stage kernels from the calling thread use programmatic dependent launch
 // while on (each stage kernel waits for its predecessor before reading its results)
@@ -65,6 +69,23 @@ constexpr int kBigCarryWarps = 8;    // coefficients per carry block
 inline int big_ws_len(int k) { return (31 * k + 31) / 32 + 1; }
 void launch_bigcrt(int g_tab, int g_gemm, int g_carry, cudaStream_t s, const Job* jobs, WorkList tab,
                    WorkList gemm, WorkList carry, Tables T);
+
+// the univariate stage with the polynomials' high entries in shared memory (classes that
+// SplitK lists): threads per block, and per class the register entries of a polynomial and
+// the registers per thread the kernel is compiled for
+constexpr int kSplitThreads = 64;
+template <int L>
+struct SplitK {
+  static constexpr int K = 0, regs = 255;
+};
+template <>
+struct SplitK<33> {
+  static constexpr int K = 28, regs = 112;  // 9 blocks of 64 threads per SM
+};
+constexpr int kSplitClass = 3;  // the class (length 33) that has the split kernel
+int uni_split_occupancy();
+size_t uni_split_smem();
+void launch_uni_split(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
 
 // degree classes of the univariate stage: max(m_e, n_e) + 1 <= class length
 constexpr int kUniClasses[] = {8, 16, 24, 33, 48, 65};

@@ -2,15 +2,25 @@
 //
 // Jobs are submitted from any host thread and queued with copies of their inputs.  A
 // fixed number of slot threads, each with its own CUDA stream and executable graph,
-// take work from the queue: a slot forms a batch from the queued jobs of one type (first
-// come first served, up to a job limit), reserves device memory for it in the server's
-// arena (admission: the batch waits while the arena cannot hold it), launches it, waits
-// for its stream, posts the results and frees the memory.  Slots run concurrently, so a
-// batch admitted while others are on the GPU overlaps with them.  All slots share the
-// context's prime tables; a slot that needs larger tables waits until no batch is in
-// flight before growing them.
+// take work from the queue: a slot forms a batch from the queued jobs of one type and
+// one work class (first come first served, up to a job limit), reserves device memory
+// for it in the server's arena (admission: the batch waits while the arena cannot hold
+// it), launches it, waits for its stream, posts the results and frees the memory.  Slots
+// run concurrently, so a batch admitted while others are on the GPU overlaps with them.
+// All slots share the context's prime tables; a slot that needs larger tables waits
+// until no batch is in flight before growing them.
+//
+// Work classes keep small jobs from waiting behind large ones: a job is large when its
+// plan counts more than kLargeWork multiply-reduce operations (for a resultant: the
+// univariate eliminations of all its (prime, point) images), and a batch never mixes
+// classes, since every job of a batch finishes when the batch does.  With two or more
+// slots the last slot takes small jobs only, on a stream of the highest priority, so a
+// small job finds a slot even while the others run large batches; and the persistent
+// grids of a large batch are sized for kLargeShare of the SMs, so that the blocks of
+// small batches find room on every SM instead of waiting for a large kernel to end.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -96,6 +106,7 @@ struct Ticket {
   bs_upoly a{}, b{};
   std::vector<uint32_t> ac, bc;
   size_t bytes = 0;  // device bytes of the job as a batch of one (admission estimate)
+  int large = 0;     // work class (1: more than kLargeWork operations)
   int state = 0;     // 0 queued, 1 running, 2 done
   int status = 0;
   int deg = -1, limbs = 1;
@@ -128,6 +139,14 @@ namespace bs {
 
 static int job_type(const Ticket& t) { return t.kind == BS_JOB_RESULTANT ? (t.var ? 1 : 0) : 2; }
 
+// jobs of one batch: the same type and the same work class
+static int batch_class(const Ticket& t) { return job_type(t) * 2 + t.large; }
+
+// work of a large job: about a millisecond of the GPU's multiply pipe
+constexpr double kLargeWork = 2e9;
+// share of the SMs the persistent grids of a large batch are sized for
+constexpr double kLargeShare = 0.75;
+
 // device bytes reserved for a batch: the jobs' bytes as batches of one bound the batch's
 // layout (a batch shares its headers); the slack covers alignment
 constexpr size_t kBatchSlack = 64 * 1024;
@@ -139,7 +158,7 @@ static size_t jobs_bytes(const std::vector<Ticket*>& jobs) {
 }
 
 // the slot context: own stream, status word and graph; the parent's tables
-static int make_slot(bs_ctx* parent, bs_ctx** out) {
+static int make_slot(bs_ctx* parent, bool high_priority, bs_ctx** out) {
   bs_ctx* c = new bs_ctx();
   c->device = parent->device;
   c->sms = parent->sms;
@@ -150,7 +169,10 @@ static int make_slot(bs_ctx* parent, bs_ctx** out) {
   for (int i = 0; i < kNumUniClasses; ++i)
     for (int t = 0; t < 3; ++t) c->occ[i][t] = parent->occ[i][t];
   c->tune = parent->tune;
-  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  int lo = 0, hi = 0;  // numerically lower is higher priority
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (cudaStreamCreateWithPriority(&c->own_stream, cudaStreamNonBlocking, high_priority ? hi : lo) !=
+      cudaSuccess) {
     delete c;
     return BS_ERR_CUDA;
   }
@@ -170,6 +192,8 @@ static int make_slot(bs_ctx* parent, bs_ctx** out) {
 static void run_batch(bs_server* S, bs_ctx* c, std::vector<Ticket*>& jobs, char* dev) {
   const int n = (int)jobs.size();
   const int type = job_type(*jobs[0]);
+  // a large batch leaves room on every SM for the blocks of small ones
+  c->sms = jobs[0]->large ? std::max(1, (int)(S->parent->sms * kLargeShare)) : S->parent->sms;
   int rc = 0;
   std::vector<bs_upoly> outs(n);
   auto fail_all = [&](int code) {
@@ -269,16 +293,21 @@ static void slot_main(bs_server* S, int slot) {
     std::vector<uint64_t> ids;
     std::vector<Ticket*> jobs;
     size_t off = 0, bytes = 0;
+    const bool small_only = S->slots.size() >= 2 && slot == (int)S->slots.size() - 1;
     for (;;) {
       if (S->stop && S->queue.empty()) return;
-      if (!S->queue.empty()) {
-        Ticket& head = S->tickets[S->queue.front()];
-        const int type = job_type(head);
+      // the head: the oldest queued job (the oldest small one for the small-job slot)
+      size_t h = 0;
+      if (small_only)
+        while (h < S->queue.size() && S->tickets[S->queue[h]].large) ++h;
+      if (h < S->queue.size()) {
+        Ticket& head = S->tickets[S->queue[h]];
+        const int type = batch_class(head);
         size_t sum = kBatchSlack;
         std::vector<size_t> pos;
-        for (size_t q = 0; q < S->queue.size() && (int)pos.size() < S->max_batch; ++q) {
+        for (size_t q = h; q < S->queue.size() && (int)pos.size() < S->max_batch; ++q) {
           Ticket& t = S->tickets[S->queue[q]];
-          if (job_type(t) != type) continue;
+          if (batch_class(t) != type) continue;
           if (!pos.empty() && sum + t.bytes > S->arena.largest_free()) break;
           sum += t.bytes;
           pos.push_back(q);
@@ -348,7 +377,7 @@ extern "C" int bs_serve_start(bs_ctx* ctx, int slots, int max_batch, size_t aren
   S->arena.reset(arena_bytes);
   for (int i = 0; i < slots; ++i) {
     bs_ctx* c = nullptr;
-    if (make_slot(ctx, &c) != 0) {
+    if (make_slot(ctx, slots >= 2 && i == slots - 1, &c) != 0) {
       for (bs_ctx* d : S->slots) bs_free(d);
       cudaFree(S->arena_base);
       delete S;
@@ -402,10 +431,11 @@ extern "C" int bs_submit(bs_ctx* ctx, const bs_job* job, uint64_t* ticket) {
       st.assign(p.c, p.c + (size_t)(p.deg_x + 1) * (p.deg_y + 1) * p.limbs);
       (w ? t.g : t.f) = bs_bipoly{p.deg_x, p.deg_y, p.limbs, st.data()};
     }
-    HostBatch B;  // plan as a batch of one: validation and the admission estimate
+    HostBatch B;  // plan as a batch of one: validation, admission estimate, work class
     const int rc = batch_plan(ctx, 1, &t.f, &t.g, t.var, &B);
     if (rc) return rc;
     t.bytes = B.total;
+    t.large = (double)B.mulmods > kLargeWork;
   } else if (job->kind == BS_JOB_GCD || job->kind == BS_JOB_SQFREE) {
     if (copy_upoly(&job->a, &t.a, &t.ac)) return ctx_fail(ctx, BS_ERR_ARG, "bad operand a");
     if (job->kind == BS_JOB_GCD) {
@@ -432,7 +462,7 @@ extern "C" int bs_submit(bs_ctx* ctx, const bs_job* job, uint64_t* ticket) {
   S->queue.push_back(id);
   ++S->submitted;
   *ticket = id;
-  S->cv_work.notify_one();
+  S->cv_work.notify_all();  // the small-job slot must not absorb the wake-up of a large job
   return BS_OK;
 }
 

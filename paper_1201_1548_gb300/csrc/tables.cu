@@ -48,6 +48,22 @@ static bool is_prime_u32(uint32_t n) {
   return true;
 }
 
+// The representative c of each prime's evaluation coset c <omega>: c = g^e for the first e
+// of E mod (p - 1), E mod (p - 1) + 2, ... (E = 0x9E3779B9, odd, so every e is odd) with
+// c^(2^kLogNMax) != 1, i.e. c outside the subgroup of every transform size.  The smallest
+// primitive root g itself would be a poor choice: it is a small integer (3 for many table
+// primes), so x = g would be an evaluation point of every transform and a vertical
+// asymptote there would reject the prime.
+static uint32_t coset_rep(uint32_t p, uint32_t g) {
+  const uint64_t pm1 = p - 1;
+  uint64_t e = 0x9E3779B9ull % pm1;
+  for (;;) {
+    const uint32_t c = host_powmod(g, e, p);
+    if (host_powmod(c, 1ull << kLogNMax, p) != 1u) return c;
+    e = (e + 2) % pm1;
+  }
+}
+
 static uint32_t primitive_root(uint32_t p) {
   std::vector<uint32_t> fs;
   uint32_t n = p - 1;
@@ -93,7 +109,7 @@ const HostPrimes& host_primes() {
       c.one_m = (uint32_t)((1ull << 32) % p);
       c.r2 = (uint32_t)(((uint64_t)c.one_m << 32) % p);
       c.g = primitive_root(p);
-      c.g_m = host_to_mont(c.g, p);
+      c.c_m = host_to_mont(coset_rep(p, c.g), p);
       c.half = (p - 1) / 2;
       c.pad = 0;
       H.pc[i] = c;
@@ -131,8 +147,8 @@ __global__ void k_init_transform(const PrimeConst* pc, const uint32_t* omega_m,
       // omega^-i = omega^(NT - i)
       itw[(int64_t)q * (NT / 2) + i] = i ? mpow(w, (uint32_t)(NT - i), c.one_m, M) : c.one_m;
     }
-    cp[idx] = mpow(c.g_m, (uint32_t)i, c.one_m, M);
-    // standard form of g^-i: REDC of its Montgomery form
+    cp[idx] = mpow(c.c_m, (uint32_t)i, c.one_m, M);
+    // standard form of c^-i: REDC of its Montgomery form
     icp[idx] = redc((uint64_t)mpow(ginv_m[q], (uint32_t)i, c.one_m, M), c.p, c.pinv);
     if (i <= kLogNMax) {
       // 2^-i in Montgomery form: (2^-1)^i with 2^-1 = (p + 1) / 2
@@ -324,8 +340,9 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   for (int q = 0; q < newT; ++q) {
     const uint32_t p = H.p[q];
     const uint32_t g = H.pc[q].g;
+    const uint32_t cr = redc((uint64_t)H.pc[q].c_m, p, H.pc[q].pinv);  // c in standard form
     om[q] = host_to_mont(host_powmod(g, (p - 1) / newNT, p), p);
-    gim[q] = host_to_mont(host_powmod(g, p - 2, p), p);
+    gim[q] = host_to_mont(host_powmod(cr, p - 2, p), p);
   }
   rc |= cu_fail(cudaMemcpyAsync(omega, om.data(), sizeof(uint32_t) * newT, cudaMemcpyHostToDevice, s));
   rc |= cu_fail(cudaMemcpyAsync(gi, gim.data(), sizeof(uint32_t) * newT, cudaMemcpyHostToDevice, s));

@@ -34,10 +34,23 @@ struct Arr {
   static constexpr int N = LL + 2;            // storage (two zeros of headroom)
 };
 
+// A register array of Arr<L>::N entries whose entries from K on live in a column of
+// shared memory (entry u >= K at s[(u - K) * S], S the threads of the block): a thread
+// holds fewer registers, so more threads fit on an SM.  Every index the elimination uses
+// is a compile-time constant after unrolling, so the choice between register and shared
+// memory is resolved at compile time and the register part stays in registers.  The high
+// entries are touched only while a polynomial is longer than K - 2, in the first passes.
+template <int L, int K, int S>
+struct SplitArr {
+  uint32_t r[K];
+  uint32_t* s;
+  __device__ __forceinline__ uint32_t& operator[](int u) { return u < K ? r[u] : s[(u - K) * S]; }
+  __device__ __forceinline__ uint32_t operator[](int u) const { return u < K ? r[u] : s[(u - K) * S]; }
+};
+
 // P[u] = c2 P[u+2] + nc1 Q[u+2] + nc0 Q[u+1] for u < lp
-template <int L>
-__device__ __forceinline__ void fused_pass(uint32_t (&P)[Arr<L>::N], int lp,
-                                           const uint32_t (&Q)[Arr<L>::N], uint32_t c2,
+template <int L, class AP, class AQ>
+__device__ __forceinline__ void fused_pass(AP& P, int lp, const AQ& Q, uint32_t c2,
                                            uint32_t nc1, uint32_t nc0, uint32_t p, uint32_t pinv) {
 #pragma unroll
   for (int u0 = 0; u0 < Arr<L>::LL; u0 += 4) {
@@ -51,9 +64,8 @@ __device__ __forceinline__ void fused_pass(uint32_t (&P)[Arr<L>::N], int lp,
 }
 
 // P[u] = b0 P[u+1] + na0 Q[u+1] for u < lp
-template <int L>
-__device__ __forceinline__ void single_pass(uint32_t (&P)[Arr<L>::N], int lp,
-                                            const uint32_t (&Q)[Arr<L>::N], uint32_t b0,
+template <int L, class AP, class AQ>
+__device__ __forceinline__ void single_pass(AP& P, int lp, const AQ& Q, uint32_t b0,
                                             uint32_t na0, uint32_t p, uint32_t pinv) {
 #pragma unroll
   for (int u0 = 0; u0 < Arr<L>::LL; u0 += 4) {
@@ -66,8 +78,8 @@ __device__ __forceinline__ void single_pass(uint32_t (&P)[Arr<L>::N], int lp,
   }
 }
 
-template <int L>
-__device__ __forceinline__ void shift_pass(uint32_t (&P)[Arr<L>::N], int lp) {
+template <int L, class AP>
+__device__ __forceinline__ void shift_pass(AP& P, int lp) {
 #pragma unroll
   for (int u0 = 0; u0 < Arr<L>::LL; u0 += 4) {
     if (u0 >= lp) break;
@@ -78,9 +90,8 @@ __device__ __forceinline__ void shift_pass(uint32_t (&P)[Arr<L>::N], int lp) {
 
 // Returns num (Montgomery form, sign applied) and stores den so that the resultant is
 // num / den.  A and B hold la and lb coefficients (la, lb >= 1), zero beyond.
-template <int L>
-__device__ __forceinline__ uint32_t unires_numden(uint32_t (&A)[Arr<L>::N], int la,
-                                                  uint32_t (&B)[Arr<L>::N], int lb, const Mod M,
+template <int L, class AT>
+__device__ __forceinline__ uint32_t unires_numden(AT& A, int la, AT& B, int lb, const Mod M,
                                                   uint32_t one_m, uint32_t* den_out) {
   const uint32_t p = M.p, pinv = M.pinv;
   uint32_t num = one_m, den = one_m, pre = one_m;

@@ -116,31 +116,109 @@ def _grid(rows):
     return [list(r) + [0] * (w - len(r)) for r in rows]
 
 
-def test_teissier_q_with_a_common_factor(ctx):
-    # f = P(x+y)^2 K(x-y) + c: f_x and f_y share P(x+y), d = deg P
-    from oracle import poly as P
+def _teissier_family(rng, deg_p, deg_k):
+    """f = P(x+y)^2 K(x-y) + c with deg P = deg_p, deg K = deg_k (total degree
+    2 deg_p + deg_k): f_x and f_y share the factor P(x+y), so d = deg_p."""
+    pc = [rng.randrange(-4, 5) for _ in range(deg_p)] + [rng.choice([1, 2, -3])]
+    kc = [rng.randrange(-4, 5) for _ in range(deg_k)] + [rng.choice([1, -1, 2])]
+    Pp, add, mul = _compose(pc, 1, 1)
+    Kk, _, _ = _compose(kc, 1, -1)
+    return _grid(add(mul(mul(Pp, Pp), Kk), [[rng.randrange(1, 9)]]))
+
+
+@pytest.mark.parametrize("deg_p,deg_k", [(1, 2), (2, 2), (3, 2), (3, 3), (4, 1)])
+def test_teissier_q_exact_with_a_common_factor(ctx, deg_p, deg_k):
+    """Q = res(f_x / h, f_y / h; y) and h = gcd(f_x, f_y) exactly (not up to a constant)
+    on the family P(x+y)^2 K(x-y) + c up to total degree 10."""
     import random
-    rng = random.Random(64)
-    for t in range(4):
-        pc = [rng.randrange(-4, 5) or 1 for _ in range(rng.randrange(2, 4))]
-        kc = [rng.randrange(-4, 5) or 1 for _ in range(rng.randrange(2, 4))]
-        Pp, add, mul = _compose(pc, 1, 1)
-        Kk, _, _ = _compose(kc, 1, -1)
-        f = _grid(add(mul(mul(Pp, Pp), Kk), [[rng.randrange(1, 9)]]))
-        Q, d = ctx.teissier_q(f)
-        want, wd = S.teissier_q(f)
-        assert d == wd == len(pc) - 1, t
-        assert P.primitive_part(Q) == P.primitive_part(want), t
+    rng = random.Random(640 + 10 * deg_p + deg_k)
+    f = _teissier_family(rng, deg_p, deg_k)
+    want, wd = S.teissier_q(f)
+    Q, d = ctx.teissier_q(f)
+    assert d == wd >= deg_p                                # P(x+y) divides f_x and f_y
+    assert Q == want
+    fx, fy = S.d_dx(f), S.d_dy(f)
+    assert ctx.gcd_bivariate(fx, fy) == S.bigcd_y(fx, fy)
 
 
-def test_teissier_q_dense_curves(ctx):
+def test_teissier_q_exact_dense_curves(ctx):
+    """Dense curves of total degree 8 and 9, one with a vertical asymptote (a non-constant
+    leading coefficient in y).  There res(f_x, f_y; y) != 0, so f_x and f_y have no common
+    factor of positive degree in y, h is the gcd of their contents and
+    Q = res(f_x / h, f_y / h; y) (the oracle's primitive remainder sequence is too slow at
+    this degree; these are the same definitions by the resultant's zero criterion)."""
+    from oracle import gcd as G
     from oracle import poly as P
     rng = _rng(65)
-    for t in range(4):
-        f = dense_curve(rng, 3 + t % 2, 10)
-        Q, d = ctx.teissier_q(f)
-        want, wd = S.teissier_q(f)
-        assert d == wd == 0 and P.primitive_part(Q) == P.primitive_part(want), t
+    for t in range(3):
+        f = dense_curve(rng, 8 + t % 2, 10)
+        if t == 2:
+            f[-1] = [0, 3] + [0] * (len(f[-1]) - 2)       # lc_y f = 3 x
+        fx, fy = S.d_dx(f), S.d_dy(f)
+        assert R.res_y(fx, fy)                             # no common factor in y
+        h = G.gcd_z(G.content_rows(R.y_rows(fx)), G.content_rows(R.y_rows(fy)))
+        want = R.res_y([P.exact_div_z(r, h) for r in R.y_rows(fx)],
+                       [P.exact_div_z(r, h) for r in R.y_rows(fy)])
+        assert ctx.teissier_q(f) == (want, 0), t
+        assert ctx.gcd_bivariate(fx, fy) == [h], t
+
+
+def test_teissier_q_in_x(ctx):
+    import random
+    f = _teissier_family(random.Random(66), 2, 2)
+    ft = R.transpose(f)
+    assert ctx.teissier_q(ft, var=0) == ctx.teissier_q(f, var=1)
+
+
+def test_gcd_bivariate_planted_factors(ctx):
+    """gcd in Z[x, y] of A = C U and B = C V against the oracle's primitive PRS: C with a
+    content in x, a non-constant leading coefficient in y, degrees 1..3 in y; both
+    variables; coprime pairs (the gcd of the contents alone)."""
+    rng = _rng(67)
+    _, add, mul = _compose([1], 1, 1)
+    for t in range(6):
+        C = dense_curve(rng, 1 + t % 3, 6, keep_top=False)
+        if t % 2:
+            C = mul(C, [[1, 2]])                           # content 1 + 2x
+        C[-1][-1] = C[-1][-1] or 5
+        U = dense_curve(rng, 2 + t % 2, 6)
+        V = dense_curve(rng, 3, 6)
+        A, B = _grid(mul(C, U)), _grid(mul(C, V))
+        assert ctx.gcd_bivariate(A, B) == S.bigcd_y(A, B), t
+        At, Bt = R.transpose(A), R.transpose(B)
+        assert ctx.gcd_bivariate(At, Bt, var=0) == S.bigcd_y(A, B), t
+    for t in range(3):                                      # coprime: the gcd of the contents
+        A = _grid(mul(dense_curve(rng, 4, 8), [[2, 6]]))
+        B = _grid(mul(dense_curve(rng, 5, 8), [[3, 9]]))
+        assert ctx.gcd_bivariate(A, B) == S.bigcd_y(A, B) == [[1, 3]], t
+
+
+def test_gcd_bivariate_conventions(ctx):
+    A = [[1, 2], [3, 0], [-5, 1]]
+    assert ctx.gcd_bivariate([[0]], A) == S.bigcd_y([[0]], A)
+    assert ctx.gcd_bivariate([[-c for c in r] for r in A], [[0]]) == S.bigcd_y(A, [[0]])
+    assert ctx.gcd_bivariate([[0]], [[0]]) == []
+    assert ctx.gcd_bivariate(A, A) == S.bigcd_y(A, A)         # all sr_i vanish
+    Am = [[-c for c in r] for r in A]
+    assert ctx.gcd_bivariate(A, _grid(Am)) == S.bigcd_y(A, Am)
+
+
+def test_subresultant_polynomial(ctx):
+    """S_d(f, g) for every d of random pairs and of pairs with a planted common factor,
+    against the oracle's points route."""
+    rng = _rng(68)
+    _, add, mul = _compose([1], 1, 1)
+    pairs = [(dense_curve(rng, 4, 10), dense_curve(rng, 3, 10)),
+             (dense_curve(rng, 5, 6, zero_prob=0.2), dense_curve(rng, 5, 6))]
+    C = dense_curve(rng, 2, 5)
+    pairs.append((_grid(mul(C, dense_curve(rng, 2, 5))), _grid(mul(C, dense_curve(rng, 3, 5)))))
+    for t, (f, g) in enumerate(pairs):
+        q = min(len(R.y_rows(f)), len(R.y_rows(g))) - 1
+        for d in range(q):
+            assert ctx.subresultant(f, g, d) == S.subresultant_y(f, g, d), (t, d)
+    with pytest.raises(bs.BsError) as e:
+        ctx.subresultant(pairs[0][0], pairs[0][1], 3)
+    assert e.value.code == bs.BS_ERR_ARG
 
 
 @pytest.mark.parametrize("branches", SPLIT)
