@@ -12,7 +12,9 @@ events on the library's stream, L2 flushed between steps outside the events); ``
 is the same metric through the C ABI call with host buffers (copies included).
 
 --impl reference times the CPU oracle (exact Bareiss determinants at integer points
-plus exact interpolation) on a bounded sample of the same workload on the host cores.
+plus exact interpolation) on the host cores: its timed steps together compute one whole
+resultant of the same workload.  ``cpu_baseline`` in the main line is one whole oracle
+resultant on all host cores, compared with the GPU's result.
 """
 
 from __future__ import annotations
@@ -46,6 +48,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (4096 pairs) and served-stream measurements")
+    ap.add_argument("--case", choices=sorted(CASES),
+                    help="run one workload --reps times for a profiler instead of the benchmark")
+    ap.add_argument("--reps", type=int, default=2)
     return ap.parse_args()
 
 
@@ -53,94 +58,89 @@ def _args():
 # CPU oracle (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------------------
 
-def _oracle_point(args):
-    f, g, x0 = args
-    from oracle.resultant import res_at_point
-    return res_at_point(f, g, x0)
-
-
-def _oracle_sample(f, g, npts, pool, cores):
-    """Wall time of npts exact point determinants on the pool (the oracle's route)."""
-    from oracle.resultant import degree_bound
-    D = degree_bound(f, g)
-    x0 = -(D // 2)
-    xs = [x0 + (t * 131) % (D + 1) for t in range(npts)]
-    t0 = time.perf_counter()
-    pool.map(_oracle_point, [(f, g, x) for x in xs], chunksize=1)
-    return time.perf_counter() - t0, D
-
-
-def _oracle_interp_time(D, bits):
-    """Exact interpolation of D + 1 values of the result's size (synthetic values)."""
-    import random
-    from oracle.resultant import interpolate_consecutive
-    rng = random.Random(5)
-    # values of a degree-D polynomial with `bits`-bit coefficients at small integers:
-    vals = [rng.getrandbits(bits + 12) - (1 << (bits + 11)) for _ in range(D + 1)]
-    t0 = time.perf_counter()
-    try:
-        interpolate_consecutive(-(D // 2), vals)
-    except ArithmeticError:
-        pass  # synthetic values need not interpolate to an integer polynomial
-    return time.perf_counter() - t0
-
-
 def _cpu_pool():
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     return mp.get_context("spawn").Pool(cores), cores
 
 
-def _cpu_baseline(f, g, pool, cores, npts):
-    from oracle.resultant import bound_sq
-    t_pts, D = _oracle_sample(f, g, npts, pool, cores)
-    bits = (bound_sq(f, g).bit_length() + 1) // 2
-    t_int = _oracle_interp_time(D, bits)
-    per_res = t_pts * (D + 1) / npts + t_int
-    # the same route on one core: two point determinants in this process
-    from oracle.resultant import res_at_point
+def _oracle_points(f, g):
+    """The integer points of the oracle's points route for res(f, g; y)."""
+    from oracle.resultant import degree_bound
+    D = degree_bound(f, g)
+    x0 = -(D // 2)
+    return x0, list(range(x0, x0 + D + 1))
+
+
+def _oracle_whole(f, g, pool):
+    """One whole oracle resultant: every exact point determinant on the pool, then the
+    exact interpolation (oracle.resultant.res_y, points route).  Returns (R, seconds)."""
+    from oracle.resultant import res_y
     t0 = time.perf_counter()
-    for x in (-(D // 2), 1):
-        res_at_point(f, g, x)
-    t_one = (time.perf_counter() - t0) / 2
-    single = 1.0 / (t_one * (D + 1) + t_int)
-    return {"value": 1.0 / per_res, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "single_core_value": single,
-            "sample": f"{npts} of the {D + 1} exact Bareiss point determinants (63x63 over Z) "
-                      f"on {cores} processes, scaled to all {D + 1} points, plus one exact "
-                      f"interpolation of {D + 1} values ({t_pts:.2f} s + {t_int:.2f} s); "
-                      f"single core: 2 determinants in one process ({t_one:.2f} s each)"}
+    r = res_y(f, g, route="points", map=lambda fn, xs: pool.map(fn, xs, chunksize=1))
+    return r, time.perf_counter() - t0
+
+
+def _cpu_baseline(f, g, pool, cores, want=None):
+    """cpu_baseline of the main line: one whole resultant of the workload by the oracle on
+    all host cores (no sampling, no extrapolation); checked against the GPU's result."""
+    r, dt = _oracle_whole(f, g, pool)
+    x0, xs = _oracle_points(f, g)
+    out = {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "seconds": dt,
+           "sample": f"one whole resultant: all {len(xs)} exact Bareiss point determinants "
+                     f"(63x63 over Z) on {cores} processes and the exact interpolation"}
+    if want is not None:
+        out["equals_gpu_result"] = (r == want)
+    return out
 
 
 def run_reference(args):
+    """The oracle as the reference arm: the K timed steps together compute one whole
+    resultant of the workload (step s takes its share of the point determinants on all
+    host cores; the last step also interpolates), so value = 1 resultant / the K steps'
+    time; the W warm-up steps compute shares of the same size, untimed."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle.resultant import interpolate_consecutive, res_at_point
+    from functools import partial
     from workloads import cfg2_pair
     f, g = cfg2_pair(SEED)
     pool, cores = _cpu_pool()
-    npts = max(cores, 8)
-    from oracle.resultant import bound_sq
-    t_int = None
+    x0, xs = _oracle_points(f, g)
+    fn = partial(res_at_point, f, g)
+
+    def shares(k):
+        return [xs[i::k] for i in range(k)]
+
+    parts = shares(args.steps)
+    for w in range(args.warmup):             # untimed steps of the same size
+        pool.map(fn, parts[w % len(parts)], chunksize=1)
+    vals = {}
     step_s = []
-    for i in range(args.warmup + args.steps):
-        t_pts, D = _oracle_sample(f, g, npts, pool, cores)
-        if t_int is None:
-            t_int = _oracle_interp_time(D, (bound_sq(f, g).bit_length() + 1) // 2)
-        per_res = t_pts * (D + 1) / npts + t_int
-        if i >= args.warmup:
-            step_s.append(per_res)
+    for s_i, part in enumerate(parts):
+        t0 = time.perf_counter()
+        vals.update(zip(part, pool.map(fn, part, chunksize=1)))
+        if s_i == len(parts) - 1:
+            r = interpolate_consecutive(x0, [vals[x] for x in xs])
+        step_s.append(time.perf_counter() - t0)
     pool.close()
-    ms = 1000.0 * statistics.mean(step_s)
-    value = 1000.0 / ms
+    total = sum(step_s)
+    ms = 1000.0 * total / args.steps
+    value = 1.0 / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "m_y": 32, "n_y": 31,
+                                           "D": len(xs) - 1,
+                                           "resultants_per_step": 1.0 / args.steps},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"per step {npts} exact point determinants on {cores} "
-                                       f"processes scaled to {D + 1} points, plus one exact "
-                                       f"interpolation"},
+                             "seconds": total,
+                             "sample": f"one whole resultant split over the {args.steps} timed "
+                                       f"steps: its {len(xs)} exact point determinants on "
+                                       f"{cores} processes, then the exact interpolation "
+                                       f"(degree {len(r) - 1})"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -271,7 +271,8 @@ def _bench_batched(bs, ctx, reps=3):
     rc = lib.bs_autotune_batch(ctx.h, n, F, G, 1, C.byref(info))
     if rc:
         raise SystemExit(f"bs_autotune_batch failed: {rc}")
-    tune = {"eval_warps": info.eval_warps, "eval_blocks_per_sm": info.eval_blocks_per_sm,
+    tune = {"eval_independent": info.eval_independent,
+            "eval_warps": info.eval_warps, "eval_blocks_per_sm": info.eval_blocks_per_sm,
             "uni_threads": list(info.uni_threads), "crt_tile": info.crt_tile,
             "crt_blocks_per_sm": info.crt_blocks_per_sm, "trials": info.trials,
             "stage_ms_default": info.ms_default, "stage_ms_tuned": info.ms_tuned}
@@ -451,6 +452,24 @@ def _bench_served(bs, jobs=96, seed=1):
     info = srv.serve_stats()
     srv.serve_stop()
     srv.close()
+
+    def work_class(job):
+        # the library's work classes: a resultant is large when its univariate stage
+        # counts more than 2e9 multiply-reduce operations
+        if job["kind"] == "gcd":
+            return "gcd"
+        p = bs.bs_plan(job["f"], job["g"])
+        ops = p["k_total"] * p["N"] * p["m_e"] * p["n_e"]
+        return "resultant_large" if ops > 2e9 else "resultant_small"
+
+    def pct_of(vals, q):
+        vals = sorted(vals)
+        return vals[min(len(vals) - 1, int(round(q * (len(vals) - 1))))]
+    by_class = {}
+    for j, ms in zip(stream2, lat):
+        by_class.setdefault(work_class(j), []).append(ms)
+    classes = {k: {"jobs": len(v), "p50": pct_of(v, 0.5), "p99": pct_of(v, 0.99), "max": max(v)}
+               for k, v in sorted(by_class.items())}
     lat.sort()
     pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
     return {"workload": "Poisson stream, 50% resultants (dense, total degree 6-64) / 50% gcds "
@@ -459,6 +478,7 @@ def _bench_served(bs, jobs=96, seed=1):
             "saturated_jobs_per_s": sat_rate, "offered_rate_hz": rate,
             "open_loop_jobs_per_s": jobs / open_s,
             "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "max": lat[-1]},
+            "latency_ms_by_class": classes,
             "batches": info["batches"], "max_inflight_batches": info["max_inflight"],
             "arena_peak_bytes": info["arena_peak"]}
 
@@ -639,7 +659,7 @@ def run_ours(args):
 
     cpu = None
     if want_cpu:
-        cpu = _cpu_baseline(f, g, pool, cores, npts=max(32, 2 * cores))
+        cpu = _cpu_baseline(f, g, pool, cores, want=host)
         pool.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -666,8 +686,93 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------------------
+# single workloads for profilers (--case): each repetition is one call; the result is
+# checked once against the host entry point
+# --------------------------------------------------------------------------------------
+
+def _case_discriminant32(reps):
+    """res_y(f, df/dy) of the degree-32 curve with device-resident inputs, one
+    bs_resultant_device call per repetition."""
+    import numpy as np
+    import torch
+    import paper_1201_1548_gb300 as bs
+    from workloads import cfg2_pair
+    f, g = cfg2_pair(SEED)
+    ctx = bs.Context(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx.set_stream(stream.cuda_stream)
+    af, dxf, dyf, Lf = bs.bipoly_to_limbs(f)
+    ag, dxg, dyg, Lg = bs.bipoly_to_limbs(g)
+    df = torch.from_numpy(af.view(np.int32).copy()).cuda()
+    dg = torch.from_numpy(ag.view(np.int32).copy()).cuda()
+    dcap, lcap = ctx.resultant_bounds((dxf, dyf, Lf), (dxg, dyg, Lg))
+    out = torch.zeros((dcap + 1) * lcap, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(reps):
+        ctx.resultant_device(df.data_ptr(), (dxf, dyf, Lf), dg.data_ptr(), (dxg, dyg, Lg),
+                             out.data_ptr(), (dcap, lcap))
+        ctx.device_status()
+    dev = bs.limbs_to_ints(out.cpu().numpy().view(np.uint32), dcap + 1, lcap)
+    while dev and dev[-1] == 0:
+        dev.pop()
+    if dev != ctx.resultant(f, g):
+        raise SystemExit("device and host results differ")
+
+
+def _case_batch4096(reps):
+    """The 4096 ragged pairs through bs_resultant_batch, one graph launch per repetition."""
+    import paper_1201_1548_gb300 as bs
+    from workloads import cfg3_batch
+    pairs = cfg3_batch(seed=1, count=4096)
+    ctx = bs.Context(0)
+    first = None
+    for _ in range(reps):
+        got = ctx.resultant_batch(pairs)
+        first = first or got
+    for i in range(0, len(pairs), 512):
+        if first[i] != ctx.resultant(*pairs[i]):
+            raise SystemExit(f"batched and single results differ at pair {i}")
+
+
+def _case_projection32(reps):
+    """Square-free part, Yun's factorisation and the psc sequence of R = res(f, f_y) for
+    the degree-32 curve, one call each per repetition."""
+    import paper_1201_1548_gb300 as bs
+    from workloads import cfg2_pair
+    f, g = cfg2_pair(SEED)
+    ctx = bs.Context(0)
+    R = ctx.resultant(f, g)
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        sq = ctx.squarefree_part(R)
+        t1 = time.perf_counter()
+        fac = ctx.squarefree_factorization(R)
+        t2 = time.perf_counter()
+        ps = ctx.psc(f, g)
+        t3 = time.perf_counter()
+        print(f"sqf {1e3 * (t1 - t0):.2f} ms  yun {1e3 * (t2 - t1):.2f} ms  psc {1e3 * (t3 - t2):.2f} ms")
+    if fac[-1] != sq and len(fac) == 1 or ps[0] != R:
+        raise SystemExit("inconsistent projection results")
+
+
+CASES = {"discriminant32": _case_discriminant32, "batch4096": _case_batch4096,
+         "projection32": _case_projection32}
+
+
+def run_case(args):
+    from paper_1201_1548_gb300.build import build
+    build()
+    CASES[args.case](args.reps)
+    print("ok")
+
+
 def main():
     args = _args()
+    if args.case:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
