@@ -148,7 +148,11 @@ int bs_resultant_bounds(const bs_bipoly *f, const bs_bipoly *g, int var,
  * beyond planning); the degree stored is the bound D of the plan and the limb count
  * is an upper bound.  Otherwise out->deg and out->limbs give the capacity; on success
  * out->deg is set to the true degree (-1 for the zero polynomial) and coefficients
- * deg+1..capacity are zero-filled; each coefficient is sign-extended to out->limbs. */
+ * deg+1..capacity are zero-filled; each coefficient is sign-extended to out->limbs.
+ * Limits (BS_ERR_RANGE beyond them): degree at most 64 in the eliminated variable (the
+ * univariate stage keeps both polynomials in registers), at most 2^14 points per prime
+ * (degree bound D < 16384), at most 64 limbs per input coefficient, and a bound that the
+ * 6213 table primes cover (about 190,000 bits). */
 int bs_resultant(bs_ctx *ctx, const bs_bipoly *f, const bs_bipoly *g, int var,
                  bs_upoly *out);
 

@@ -1,10 +1,12 @@
 """Elementary number theory for the oracle: primality, the prime table, primitive roots.
 
 The prime table follows this definition (the same one the CUDA planner implements on
-its own): all primes p with 2**30 < p < 2**31 and p = 1 (mod 2**14), in decreasing
-order.  The paper fixes neither the prime size nor the evaluation points (Sec. 5.1,
-steps (a) and (b) leave both open); 31-bit primes with a 2**14-th root of unity let every
-prime carry an evaluation set of up to 16384 points that is a coset of the roots of unity.
+its own): all primes p with 2**30 < p < 2**31 and p = 1 (mod 2**14), in two decreasing
+runs: first those with 3p < 2**32, then the others.  The paper fixes neither the prime size
+nor the evaluation points (Sec. 5.1, steps (a) and (b) leave both open); 31-bit primes with
+a 2**14-th root of unity let every prime carry an evaluation set of up to 16384 points that
+is a coset of the roots of unity, and the first run keeps a sum of three products of
+residues below p * 2**32.
 """
 
 from __future__ import annotations
@@ -12,6 +14,7 @@ from __future__ import annotations
 PRIME_LOG_ORDER = 14          # p = 1 (mod 2**14)
 PRIME_LO = 1 << 30
 PRIME_HI = 1 << 31
+PRIME_MID = (1 << 32) // 3    # the first run: p <= PRIME_MID, i.e. 3p < 2**32
 
 
 def is_prime(n: int) -> bool:
@@ -49,17 +52,21 @@ def is_prime(n: int) -> bool:
 
 
 def prime_table(count: int, log_order: int = PRIME_LOG_ORDER):
-    """First ``count`` primes of the table (decreasing, 2**30 < p < 2**31, p = 1 mod 2**log_order)."""
+    """First ``count`` primes of the table: p = 1 mod 2**log_order, 2**30 < p < 2**31, first
+    those with p <= PRIME_MID in decreasing order, then the others in decreasing order."""
     step = 1 << log_order
     out = []
-    q = (PRIME_HI - 2) // step
-    while len(out) < count:
-        p = q * step + 1
-        if p <= PRIME_LO:
-            raise ValueError("prime table exhausted")
-        if p < PRIME_HI and is_prime(p):
-            out.append(p)
-        q -= 1
+    for top, bottom in ((PRIME_MID, PRIME_LO), (PRIME_HI - 1, PRIME_MID)):
+        q = (top - 1) // step
+        while len(out) < count:
+            p = q * step + 1
+            if p <= bottom:
+                break
+            if p <= top and is_prime(p):
+                out.append(p)
+            q -= 1
+    if len(out) < count:
+        raise ValueError("prime table exhausted")
     return out
 
 

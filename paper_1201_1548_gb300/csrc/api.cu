@@ -56,10 +56,12 @@ int ensure_workspace(bs_ctx* ctx, size_t bytes) {
   return 0;
 }
 
+// Pinned staging grows geometrically: freeing and allocating pinned memory waits for the
+// whole device, so a growth step costs as long as the longest work in flight.
 int ensure_pinned(bs_ctx* ctx, size_t up, size_t down) {
   if (up > ctx->h_up_cap) {
     if (ctx->h_up) cudaFreeHost(ctx->h_up);
-    ctx->h_up_cap = up + up / 4 + 4096;
+    ctx->h_up_cap = std::max(up + up / 4 + 4096, 2 * ctx->h_up_cap);
     if (cudaMallocHost(&ctx->h_up, ctx->h_up_cap) != cudaSuccess) {
       ctx->h_up = nullptr;
       ctx->h_up_cap = 0;
@@ -68,7 +70,7 @@ int ensure_pinned(bs_ctx* ctx, size_t up, size_t down) {
   }
   if (down > ctx->h_down_cap) {
     if (ctx->h_down) cudaFreeHost(ctx->h_down);
-    ctx->h_down_cap = down + down / 4 + 4096;
+    ctx->h_down_cap = std::max(down + down / 4 + 4096, 2 * ctx->h_down_cap);
     if (cudaMallocHost(&ctx->h_down, ctx->h_down_cap) != cudaSuccess) {
       ctx->h_down = nullptr;
       ctx->h_down_cap = 0;
@@ -944,13 +946,10 @@ extern "C" int bs_uni_resultant_modp(bs_ctx* ctx, int n, const uint32_t* p, cons
   const int cls = uni_class_of(std::max(da, db) + 1);
   if (cls < 0) return ctx_fail(ctx, BS_ERR_RANGE, "degree above 64");
   cudaSetDevice(ctx->device);
-  const HostPrimes& H = host_primes();
   std::vector<int32_t> idx(n);
   for (int i = 0; i < n; ++i) {
-    // the table is decreasing: binary search
-    auto it = std::lower_bound(H.p.begin(), H.p.end(), p[i], std::greater<uint32_t>());
-    if (it == H.p.end() || *it != p[i]) return ctx_fail(ctx, BS_ERR_ARG, "not a table prime");
-    idx[i] = (int32_t)(it - H.p.begin());
+    idx[i] = table_index(p[i]);
+    if (idx[i] < 0) return ctx_fail(ctx, BS_ERR_ARG, "not a table prime");
     for (int j = 0; j <= da; ++j)
       if (a[(size_t)i * lda + j] >= p[i]) return ctx_fail(ctx, BS_ERR_ARG, "input not reduced");
     for (int j = 0; j <= db; ++j)

@@ -1,4 +1,5 @@
-// Arithmetic in Z_p for 31-bit primes 2^30 < p < 2^31.
+// Arithmetic in Z_p for 31-bit primes 2^30 < p < 2^31 (the table's first primes also have
+// 3p < 2^32, below kSmallPrimeMax).
 //
 // Multiplication uses Montgomery's reduction (P. L. Montgomery, "Modular multiplication
 // without trial division", Math. Comp. 44 (1985)) with R = 2^32, in the variant that
@@ -19,6 +20,10 @@
 #endif
 
 namespace bs {
+
+// primes up to this bound have 3p < 2^32: a sum of three products of residues stays below
+// p 2^32 and needs no fold before Montgomery's reduction
+constexpr uint32_t kSmallPrimeMax = 1431655765u;  // floor((2^32 - 1) / 3)
 
 struct Mod {
   uint32_t p;     // the prime

@@ -718,7 +718,9 @@ __device__ __forceinline__ void unires_instance(const Job* J, int64_t inst, cons
   }
   if (A[0] == 0 || B[0] == 0) J->pstat[q] = 1;  // unlucky: a leading coefficient vanishes
   uint32_t den;
-  uint32_t num = unires_numden<L>(A, me + 1, B, ne + 1, M, pc.one_m, &den);
+  // the table's first primes have 3p < 2^32 (no fold in the fused updates)
+  const uint32_t num = pc.p <= kSmallPrimeMax ? unires_numden<L, true>(A, me + 1, B, ne + 1, M, pc.one_m, &den)
+                                              : unires_numden<L, false>(A, me + 1, B, ne + 1, M, pc.one_m, &den);
   if (dbg_ok(inst < job_vals_words(J), J->status, kDbgUniOut))
     J->vals[inst] = mmul(num, minv(den, pc.one_m, M), M);
 }

@@ -146,6 +146,8 @@ static int batch_class(const Ticket& t) { return job_type(t) * 2 + t.large; }
 constexpr double kLargeWork = 2e9;
 // share of the SMs the persistent grids of a large batch are sized for
 constexpr double kLargeShare = 0.75;
+// pinned staging of a slot allocated at start (each way)
+constexpr size_t kSlotPinnedBytes = size_t(64) << 20;
 
 // device bytes reserved for a batch: the jobs' bytes as batches of one bound the batch's
 // layout (a batch shares its headers); the slack covers alignment
@@ -177,6 +179,15 @@ static int make_slot(bs_ctx* parent, bool high_priority, bs_ctx** out) {
     return BS_ERR_CUDA;
   }
   c->stream = c->own_stream;
+  // pinned staging sized up front: a later growth waits for the whole device (cudaFreeHost,
+  // cudaMallocHost), i.e. for the longest batch in flight on the other slots
+  if (ensure_pinned(c, kSlotPinnedBytes, kSlotPinnedBytes) != 0) {
+    if (c->h_up) cudaFreeHost(c->h_up);
+    if (c->h_down) cudaFreeHost(c->h_down);
+    cudaStreamDestroy(c->own_stream);
+    delete c;
+    return BS_ERR_NOMEM;
+  }
   if (cudaMalloc(&c->d_status, sizeof(int32_t) * 4) != cudaSuccess) {
     cudaStreamDestroy(c->own_stream);
     delete c;

@@ -1,6 +1,7 @@
 // The prime table and the per-context device tables.
 //
-// Prime table: every prime 2^30 < p < 2^31 with p = 1 (mod 2^14), in decreasing order,
+// Prime table: every prime 2^30 < p < 2^31 with p = 1 (mod 2^14), in two decreasing runs
+// (first those with 3p < 2^32),
 // found with a deterministic Miller-Rabin test (bases 2, 7, 61 are sufficient below
 // 4,759,123,141 -- G. Jaeschke, Math. Comp. 61 (1993)).  p = 1 mod 2^14 gives every prime
 // a multiplicative subgroup of order 2^14, so each prime evaluates on a coset g * <omega>
@@ -8,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -85,14 +87,32 @@ static uint32_t primitive_root(uint32_t p) {
   }
 }
 
+int table_index(uint32_t p) {
+  const HostPrimes& H = host_primes();
+  // each run is decreasing: binary search in the run p belongs to
+  const auto lo = p <= kSmallPrimeMax ? H.p.begin() : H.p.begin() + H.n_small;
+  const auto hi = p <= kSmallPrimeMax ? H.p.begin() + H.n_small : H.p.end();
+  const auto it = std::lower_bound(lo, hi, p, std::greater<uint32_t>());
+  return (it != hi && *it == p) ? (int)(it - H.p.begin()) : -1;
+}
+
 const HostPrimes& host_primes() {
   static HostPrimes H;
   static std::once_flag once;
   std::call_once(once, [] {
+    // the primes p = 1 mod 2^kLogNMax with 2^30 < p < 2^31 in two runs, each decreasing:
+    // first those with 3p < 2^32 (p <= kSmallPrimeMax), whose fused elimination updates
+    // need no fold, then the rest
     const uint32_t step = 1u << kLogNMax;
-    for (uint32_t q = ((1u << 31) - 2) / step;; --q) {
-      uint64_t p = (uint64_t)q * step + 1;
+    for (uint32_t q = kSmallPrimeMax / step;; --q) {
+      const uint64_t p = (uint64_t)q * step + 1;
       if (p <= (1ull << 30)) break;
+      if (p <= kSmallPrimeMax && is_prime_u32((uint32_t)p)) H.p.push_back((uint32_t)p);
+    }
+    H.n_small = (int)H.p.size();
+    for (uint32_t q = ((1u << 31) - 2) / step;; --q) {
+      const uint64_t p = (uint64_t)q * step + 1;
+      if (p <= kSmallPrimeMax) break;
       if (p < (1ull << 31) && is_prime_u32((uint32_t)p)) H.p.push_back((uint32_t)p);
     }
     const int T = (int)H.p.size();

@@ -9,7 +9,8 @@
 namespace bs {
 
 struct HostPrimes {
-  std::vector<uint32_t> p;          // the table, decreasing
+  std::vector<uint32_t> p;          // the table: two decreasing runs (3p < 2^32 first)
+  int n_small = 0;                  // length of the first run
   std::vector<PrimeConst> pc;       // constants per prime
   std::vector<uint32_t> pw, mpw;    // [T][kMaxLimbs + 1]
   std::vector<int64_t> lg_prefix;   // [T + 1]
@@ -17,6 +18,8 @@ struct HostPrimes {
 
 // built once per process
 const HostPrimes& host_primes();
+// position of p in the table, -1 if p is not a table prime
+int table_index(uint32_t p);
 
 struct DeviceTables {
   PrimeConst* pc = nullptr;

@@ -48,8 +48,10 @@ struct SplitArr {
   __device__ __forceinline__ uint32_t operator[](int u) const { return u < K ? r[u] : s[(u - K) * S]; }
 };
 
-// P[u] = c2 P[u+2] + nc1 Q[u+2] + nc0 Q[u+1] for u < lp
-template <int L, class AP, class AQ>
+// P[u] = c2 P[u+2] + nc1 Q[u+2] + nc0 Q[u+1] for u < lp.  The sum of the three products is
+// below 3p^2; for a prime with 3p < 2^32 (SMALLP) that is below p 2^32 and Montgomery's
+// reduction applies directly, otherwise the high word is folded once first.
+template <int L, bool SMALLP = false, class AP, class AQ>
 __device__ __forceinline__ void fused_pass(AP& P, int lp, const AQ& Q, uint32_t c2,
                                            uint32_t nc1, uint32_t nc0, uint32_t p, uint32_t pinv) {
 #pragma unroll
@@ -58,7 +60,7 @@ __device__ __forceinline__ void fused_pass(AP& P, int lp, const AQ& Q, uint32_t 
 #pragma unroll
     for (int u = u0; u < u0 + 4; ++u) {
       const uint64_t t = (uint64_t)c2 * P[u + 2] + (uint64_t)nc1 * Q[u + 2] + (uint64_t)nc0 * Q[u + 1];
-      P[u] = redc_wide(t, p, pinv);
+      P[u] = SMALLP ? redc(t, p, pinv) : redc_wide(t, p, pinv);
     }
   }
 }
@@ -90,7 +92,7 @@ __device__ __forceinline__ void shift_pass(AP& P, int lp) {
 
 // Returns num (Montgomery form, sign applied) and stores den so that the resultant is
 // num / den.  A and B hold la and lb coefficients (la, lb >= 1), zero beyond.
-template <int L, class AT>
+template <int L, bool SMALLP = false, class AT>
 __device__ __forceinline__ uint32_t unires_numden(AT& A, int la, AT& B, int lb, const Mod M,
                                                   uint32_t one_m, uint32_t* den_out) {
   const uint32_t p = M.p, pinv = M.pinv;
@@ -121,7 +123,7 @@ __device__ __forceinline__ uint32_t unires_numden(AT& A, int la, AT& B, int lb, 
         const uint32_t c2 = mmul(b0, b0, M);
         const uint32_t c1 = mmul(b0, a0, M);
         const uint32_t c0 = redc((uint64_t)b0 * a1 + (uint64_t)(p - a0) * b1, p, pinv);
-        fused_pass<L>(A, la, B, c2, p - c1, p - c0, p, pinv);
+        fused_pass<L, SMALLP>(A, la, B, c2, p - c1, p - c0, p, pinv);
         la -= 2;
         pre = mmul(pre, c2, M);
       } else {
@@ -152,7 +154,7 @@ __device__ __forceinline__ uint32_t unires_numden(AT& A, int la, AT& B, int lb, 
       const uint32_t c2 = mmul(a0, a0, M);
       const uint32_t c1 = mmul(a0, b0, M);
       const uint32_t c0 = redc((uint64_t)a0 * b1 + (uint64_t)(p - b0) * a1, p, pinv);
-      fused_pass<L>(B, lb, A, c2, p - c1, p - c0, p, pinv);
+      fused_pass<L, SMALLP>(B, lb, A, c2, p - c1, p - c0, p, pinv);
       lb -= 2;
       pre = mmul(pre, c2, M);
     }

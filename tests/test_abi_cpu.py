@@ -36,6 +36,18 @@ def test_every_declared_symbol_is_exported():
     assert sorted(bs.EXPORTED_SYMBOLS) == declared
 
 
+def test_debug_build_exports_the_same_entry_points():
+    """The debug build (kernels bounds-check their accesses, BS_DEBUG_CHECKS) compiles,
+    links and exports every declared entry point."""
+    import ctypes
+    from paper_1201_1548_gb300.build import build
+    path = build(debug=True)
+    assert path.endswith("libbsres_debug.so")
+    lib = ctypes.CDLL(path)
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+
+
 def test_prime_table_matches_oracle_definition():
     ours = bs.bs_prime_table(300)
     assert ours == nt.prime_table(300)

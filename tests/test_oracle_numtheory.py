@@ -2,6 +2,8 @@
 
 import random
 
+import pytest
+
 from oracle import numtheory as nt
 
 
@@ -36,23 +38,37 @@ def test_strong_pseudoprimes_rejected():
 
 
 def test_prime_table_definition():
-    t = nt.prime_table(40)
+    """Two decreasing runs of primes p = 1 mod 2^14 in (2^30, 2^31): first those with
+    3p < 2^32, then the rest; checked by trial division at the runs' starts, between
+    consecutive entries and across the boundary, and by counting the whole table."""
     step = 1 << nt.PRIME_LOG_ORDER
-    assert all((1 << 30) < p < (1 << 31) for p in t)
-    assert all(p % step == 1 for p in t)
-    assert all(t[i] > t[i + 1] for i in range(len(t) - 1))
-    for p in t[:5]:
-        assert _trial(p)
-    # no candidate of the form q*2^14+1 between consecutive entries is prime
-    for a, b in zip(t[:4], t[1:5]):
-        c = b + step
-        while c < a:
+    full = nt.prime_table(6213)
+    with pytest.raises(ValueError):
+        nt.prime_table(6214)
+    n1 = sum(1 for p in full if 3 * p < (1 << 32))
+    assert all(3 * p < (1 << 32) for p in full[:n1]) and all(3 * p > (1 << 32) for p in full[n1:])
+    assert all((1 << 30) < p < (1 << 31) and p % step == 1 for p in full)
+    assert all(full[i] > full[i + 1] for i in range(n1 - 1))
+    assert all(full[i] > full[i + 1] for i in range(n1, len(full) - 1))
+    assert len(set(full)) == len(full)
+    for run in (full[:6], full[n1:n1 + 6]):
+        for p in run[:5]:
+            assert _trial(p)
+        # no candidate q*2^14+1 between consecutive entries is prime
+        for a, b in zip(run[:5], run[1:6]):
+            c = b + step
+            while c < a:
+                assert not _trial(c)
+                c += step
+    # the candidates above each run's first entry (up to the run's bound) are composite
+    for first, bound in ((full[0], (1 << 32) // 3), (full[n1], (1 << 31) - 1)):
+        c = first + step
+        while c <= bound:
             assert not _trial(c)
             c += step
-    # the first candidate below 2^31 that is skipped is composite
-    top = ((1 << 31) - 2) // step * step + 1
-    c = top
-    while c > t[0]:
+    # the last entry of the first run and the candidates below it down to 2^30
+    c = full[n1 - 1] - step
+    while c > (1 << 30):
         assert not _trial(c)
         c -= step
 
