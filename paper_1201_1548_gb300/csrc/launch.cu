@@ -36,7 +36,7 @@ static int crt_warps(const bs_ctx* ctx, int kmax, int lmax, size_t* smem, int* s
 
 // shared memory of the warp-per-coefficient reconstruction block
 size_t crt_warp_smem(int kmax, int lmax) {
-  return ((size_t)kmax * kmax + (size_t)kmax * lmax + (size_t)kmax * kCrtTile + 3 * (size_t)kmax +
+  return ((size_t)kmax * (kmax + 1) + (size_t)kmax * kCrtTile + 3 * (size_t)kmax +
           (size_t)kCrtTile * kmax + (size_t)kCrtTile * lmax + 3 * (size_t)kmax + 4) *
          sizeof(uint32_t);
 }

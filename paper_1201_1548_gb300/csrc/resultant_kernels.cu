@@ -1167,10 +1167,12 @@ __global__ void __launch_bounds__(kCrtWarps * 32) k_crt(const Job* jobs, WorkLis
 // limbs: the result is A + (B shifted one limb) + (C shifted two limbs), two additions
 // whose one-bit carries are resolved per 32-limb chunk with generate/propagate ballots.
 
+// The prefix products P_j (table order) are read from the context's table through L1
+// (ppg: row j at ppg + j * lpp), not staged: that keeps the block's shared memory small.
 template <int S>
 __device__ __forceinline__ void crt_coef_warp(const Job* J, const Plan& P, int i, int c,
                                               const uint32_t* Xt, const uint32_t* sinv,
-                                              const uint32_t* spp, int nl, const uint32_t* pq,
+                                              const uint32_t* ppg, int lpp, int nl, const uint32_t* pq,
                                               const uint32_t* pinvq, uint32_t* sd,
                                               uint32_t* Vw, bool table_order) {
   const int lane = threadIdx.x & 31;
@@ -1240,7 +1242,7 @@ __device__ __forceinline__ void crt_coef_warp(const Job* J, const Plan& P, int i
         const int j0 = max(0, (32 * b0 - 31) / 31);
 #pragma unroll 8
         for (int j = j0; j < k; ++j) {
-          const uint32_t pl = l < nl ? spp[j * nl + l] : 0u;
+          const uint32_t pl = l < nl ? __ldg(ppg + (int64_t)j * lpp + l) : 0u;
           const uint64_t prod = (uint64_t)sd[j] * pl;
           const uint64_t s = acc + prod;
           ah += (s < acc) ? 1u : 0u;
@@ -1410,7 +1412,8 @@ __device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, 
 }
 
 // Block: kCrtTile coefficients of one job, one warp each.  Shared memory (words):
-// [inv k*k][pp k*nlmax][X k*kCrtTile][p k][pinv k][sel k][digits kCrtTile*k][limbs kCrtTile*lmax]
+// [inv or M_k: k*(k+1)][X k*kCrtTile][p k][pinv k][sel k][digits kCrtTile*k]
+// [limbs kCrtTile*lmax][y_k k][q62 k][P_k k+4]
 template <int TILE>
 __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList wl, Tables T,
                                                          int kmax, int lmax) {
@@ -1419,9 +1422,8 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nthr = blockDim.x;
   constexpr int tile = TILE;  // coefficients per block, one warp each (<= kCrtTile)
-  uint32_t* sinv = smc;
-  uint32_t* spp = sinv + (size_t)kmax * kmax;
-  uint32_t* X = spp + (size_t)kmax * lmax;
+  uint32_t* sinv = smc;  // kmax (kmax + 1) words: Garner's k x k inverses or M_k
+  uint32_t* X = sinv + (size_t)kmax * (kmax + 1);
   uint32_t* pq = X + (size_t)kmax * kCrtTile;
   uint32_t* pinvq = pq + kmax;
   uint32_t* selq = pinvq + kmax;
@@ -1467,7 +1469,7 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
     const int L = ws_len(k);
     if (k <= T.WK &&
         dbg_ok(T.ws_moff[k] + (int64_t)k * L <= T.ws_m_words && k <= T.Tg && L <= kmax + 4 &&
-                   (int64_t)k * L <= (int64_t)kmax * kmax + (int64_t)kmax * lmax,
+                   (int64_t)k * L <= (int64_t)kmax * (kmax + 1),
                J->status, kDbgCrtWs)) {
       // weighted-sum tables, staged with the residues (they depend on k only; the Garner
       // path below overwrites them when the selected primes are not the first k):
@@ -1495,10 +1497,6 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
 #pragma unroll 4
         for (int b = lane; b < k; b += 32) sinv[a * k + b] = __ldg(T.ginv + rowa + selq[b]);
       }
-      if (table_order)
-        for (int j = warp; j < k; j += nthr / 32)
-#pragma unroll 4
-          for (int l = lane; l < nl; l += 32) spp[j * nl + l] = __ldg(T.pp + (int64_t)j * T.LPP + l);
     }
     __syncthreads();
     for (int c = warp; c < ncoef; c += nthr / 32) {
@@ -1519,11 +1517,11 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
         continue;
       }
       switch ((k + 31) >> 5) {
-        case 1: crt_coef_warp<1>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
-        case 2: crt_coef_warp<2>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
-        case 3: crt_coef_warp<3>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
-        case 4: crt_coef_warp<4>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
-        default: crt_coef_warp<5>(J, P, i0 + c, c, X, sinv, spp, nl, pq, pinvq, sd, Vw, table_order); break;
+        case 1: crt_coef_warp<1>(J, P, i0 + c, c, X, sinv, T.pp, T.LPP, nl, pq, pinvq, sd, Vw, table_order); break;
+        case 2: crt_coef_warp<2>(J, P, i0 + c, c, X, sinv, T.pp, T.LPP, nl, pq, pinvq, sd, Vw, table_order); break;
+        case 3: crt_coef_warp<3>(J, P, i0 + c, c, X, sinv, T.pp, T.LPP, nl, pq, pinvq, sd, Vw, table_order); break;
+        case 4: crt_coef_warp<4>(J, P, i0 + c, c, X, sinv, T.pp, T.LPP, nl, pq, pinvq, sd, Vw, table_order); break;
+        default: crt_coef_warp<5>(J, P, i0 + c, c, X, sinv, T.pp, T.LPP, nl, pq, pinvq, sd, Vw, table_order); break;
       }
     }
     __syncthreads();
