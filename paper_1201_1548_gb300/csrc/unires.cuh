@@ -48,20 +48,28 @@ struct SplitArr {
   __device__ __forceinline__ uint32_t operator[](int u) const { return u < K ? r[u] : s[(u - K) * S]; }
 };
 
-// P[u] = c2 P[u+2] + nc1 Q[u+2] + nc0 Q[u+1] for u < lp.  The sum of the three products is
-// below 3p^2; for a prime with 3p < 2^32 (SMALLP) that is below p 2^32 and Montgomery's
-// reduction applies directly, otherwise the high word is folded once first.
+// P[u] = c2 P[u+2] + nc1 Q[u+2] + nc0 Q[u+1] for u < lp - 2, the new length (Q is at
+// most lp - 1 long).  The sum of the three products is below 3p^2; for a prime with
+// 3p < 2^32 (SMALLP) that is below p 2^32 and Montgomery's reduction applies directly,
+// otherwise the high word is folded once first.  The blocks of four stop at the first
+// multiple of four at or above lp - 2: the updates there past lp - 2 read only zeros and
+// write zeros, and each block clears the two entries after it (it has read them; the next
+// block overwrites them), which leaves zeros in the at most two entries between the last
+// block and lp.  No update is spent on the two entries that the pass removes.
 template <int L, bool SMALLP = false, class AP, class AQ>
 __device__ __forceinline__ void fused_pass(AP& P, int lp, const AQ& Q, uint32_t c2,
                                            uint32_t nc1, uint32_t nc0, uint32_t p, uint32_t pinv) {
+  const int ln = lp - 2;
 #pragma unroll
   for (int u0 = 0; u0 < Arr<L>::LL; u0 += 4) {
-    if (u0 >= lp) break;
+    if (u0 >= ln) break;
 #pragma unroll
     for (int u = u0; u < u0 + 4; ++u) {
       const uint64_t t = (uint64_t)c2 * P[u + 2] + (uint64_t)nc1 * Q[u + 2] + (uint64_t)nc0 * Q[u + 1];
       P[u] = SMALLP ? redc(t, p, pinv) : redc_wide(t, p, pinv);
     }
+    P[u0 + 4] = 0u;
+    P[u0 + 5] = 0u;
   }
 }
 
