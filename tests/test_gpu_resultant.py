@@ -104,6 +104,47 @@ def test_device_path_matches_host_path(ctx):
         assert vals == host
 
 
+def _device_call(ctx, f, g):
+    torch = pytest.importorskip("torch")
+    import paper_1201_1548_gb300 as bs
+    af, dxf, dyf, Lf = bs.bipoly_to_limbs(f)
+    ag, dxg, dyg, Lg = bs.bipoly_to_limbs(g)
+    df = torch.from_numpy(af.view(np.int32).copy()).cuda()
+    dg = torch.from_numpy(ag.view(np.int32).copy()).cuda()
+    dcap, lcap = ctx.resultant_bounds((dxf, dyf, Lf), (dxg, dyg, Lg))
+    out = torch.zeros((dcap + 1) * lcap, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    ctx.resultant_device(df.data_ptr(), (dxf, dyf, Lf), dg.data_ptr(), (dxg, dyg, Lg),
+                         out.data_ptr(), (dcap, lcap))
+    ctx.device_status()
+    vals = bs.limbs_to_ints(out.cpu().numpy().view(np.uint32), dcap + 1, lcap)
+    while vals and vals[-1] == 0:
+        vals.pop()
+    return vals
+
+
+def test_device_path_large_transforms(ctx):
+    """Device-planned jobs with 2048- and 4096-point sets (the plan is made on the device, so
+    the size-class dispatch and the shared-memory transform run from device-side offsets)
+    give what the host path gives; the last pair has rows of 1101 coefficients, folded
+    modulo N."""
+    import paper_1201_1548_gb300 as bs
+    rng = _rng(77)
+    pairs = []
+    for tdeg, bits in ((40, 8), (48, 6)):
+        f = dense_curve(rng, tdeg, bits)
+        pairs.append((f, d_dy(f)))
+    f = [[int(v) for v in rng.integers(-99, 100, 1101)] for _ in range(3)]  # deg_y 2, deg_x 1100
+    pairs.append((f, d_dy(f)))
+    for f, g in pairs:
+        assert bs.bs_plan(f, g)["N"] >= 2048
+        dev = _device_call(ctx, f, g)
+        assert dev == ctx.resultant(f, g)
+        p = 2147483647  # outside the library's table
+        for x0 in (3, 12345):
+            assert P.evaluate(dev, x0) % p == R.res_at_point_modp(f, g, x0, p)
+
+
 def test_degenerate_cfg4(ctx):
     cases = cfg4_cases(seed=1, deg=5, bits=12, poison_prime=nt.prime_table(1)[0])
     # square factors: res_y(f, f_y) vanishes identically
