@@ -412,7 +412,8 @@ def _bench_served(bs, jobs=96, seed=1):
     the latency percentiles."""
     from workloads import cfg5_stream
     srv = bs.Context(0)
-    srv.serve_start(slots=3, max_batch=16)
+    slots = 6  # three take any job, three no large ones
+    srv.serve_start(slots=slots, max_batch=16)
     stream = cfg5_stream(seed=seed, jobs=jobs)
 
     def submit(job):
@@ -433,6 +434,7 @@ def _bench_served(bs, jobs=96, seed=1):
         srv.poll(t)
     sat_rate = jobs / sat_s
     rate = 0.7 * sat_rate
+    info0 = srv.serve_stats()
     stream2 = cfg5_stream(seed=seed + 1, jobs=jobs, rate_hz=rate)
     t0 = time.perf_counter()
     tickets = []
@@ -441,13 +443,14 @@ def _bench_served(bs, jobs=96, seed=1):
         if dt > 0:
             time.sleep(dt)
         tickets.append(submit(j))
-    lat = []
+    lat, queue = [], []
     for t in tickets:
         srv.wait(t)
-        status, _, _, ms = srv.poll(t)
+        status, _, qms, ms = srv.poll(t)
         if status:
             raise SystemExit(f"served job failed: {status}")
         lat.append(ms)
+        queue.append(qms)
     open_s = time.perf_counter() - t0
     info = srv.serve_stats()
     srv.serve_stop()
@@ -455,32 +458,35 @@ def _bench_served(bs, jobs=96, seed=1):
 
     def work_class(job):
         # the library's work classes: a resultant is large when its univariate stage
-        # counts more than 2e9 multiply-reduce operations
+        # counts more than 2e9 multiply-reduce operations, tiny at most 2e8
         if job["kind"] == "gcd":
             return "gcd"
         p = bs.bs_plan(job["f"], job["g"])
         ops = p["k_total"] * p["N"] * p["m_e"] * p["n_e"]
-        return "resultant_large" if ops > 2e9 else "resultant_small"
+        return "resultant_large" if ops > 2e9 else "resultant_small" if ops > 2e8 else "resultant_tiny"
 
     def pct_of(vals, q):
         vals = sorted(vals)
         return vals[min(len(vals) - 1, int(round(q * (len(vals) - 1))))]
-    by_class = {}
-    for j, ms in zip(stream2, lat):
+    by_class, q_class = {}, {}
+    for j, ms, qms in zip(stream2, lat, queue):
         by_class.setdefault(work_class(j), []).append(ms)
-    classes = {k: {"jobs": len(v), "p50": pct_of(v, 0.5), "p99": pct_of(v, 0.99), "max": max(v)}
+        q_class.setdefault(work_class(j), []).append(qms)
+    classes = {k: {"jobs": len(v), "p50": pct_of(v, 0.5), "p99": pct_of(v, 0.99), "max": max(v),
+                   "queue_p50": pct_of(q_class[k], 0.5), "queue_p99": pct_of(q_class[k], 0.99)}
                for k, v in sorted(by_class.items())}
     lat.sort()
     pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
     return {"workload": "Poisson stream, 50% resultants (dense, total degree 6-64) / 50% gcds "
                         f"(planted factor), 16-256-bit coefficients, seed {seed}",
-            "jobs": jobs, "slots": 3, "max_batch": 16,
+            "jobs": jobs, "slots": slots, "max_batch": 16,
             "saturated_jobs_per_s": sat_rate, "offered_rate_hz": rate,
             "open_loop_jobs_per_s": jobs / open_s,
             "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "max": lat[-1]},
             "latency_ms_by_class": classes,
             "batches": info["batches"], "max_inflight_batches": info["max_inflight"],
-            "arena_peak_bytes": info["arena_peak"]}
+            "arena_peak_bytes": info["arena_peak"],
+            "open_loop_phase_ms": {k: info[k] - info0[k] for k in ("host_plan_ms", "device_ms", "host_finish_ms")}}
 
 
 def run_ours(args):
@@ -560,8 +566,13 @@ def run_ours(args):
     time.sleep(0.3)
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # after each flush a short device-side wait (about 50 us at 2 GHz), outside the events:
+    # the host queues the whole step meanwhile, so the timed region holds the step's device
+    # work without gaps where the GPU waits for a launch (the e2e figure carries the host
+    # path: planning, launches, copies)
     for i in range(args.steps):
         flush.zero_()
+        torch.cuda._sleep(100_000)
         e0[i].record(stream)
         step()
         e1[i].record(stream)
@@ -670,6 +681,7 @@ def run_ours(args):
                            "points_per_prime": plan["N"], "primes": plan["k_need"],
                            "primes_evaluated": plan["k_total"],
                            "l2": "flushed between steps (256 MiB write, outside the events)",
+                           "launch_headroom": "a 100k-cycle device wait after each flush, outside the events",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "latency_ms": {"p50": p50, "p99": p99},
                 "modp_univariate_resultants_per_s": world * instances / (ms * 1e-3),

@@ -469,14 +469,16 @@ int bs_set_tune(bs_ctx *ctx, const bs_tune_info *t);
  * stream, and one device arena of `arena_bytes` (0: half the free device memory, capped
  * by the context's budget).  bs_submit() copies a job's operands and queues it.  A free
  * worker forms a batch from the queued jobs of the head job's type (resultants in y,
- * resultants in x, or gcd / square-free jobs) and work class (large: a resultant whose
- * plan counts more than 2e9 multiply-reduce operations in its univariate stage, about a
- * millisecond of the GPU; small otherwise), first come first served and at most
- * `max_batch` jobs; with two or more slots the last worker takes small jobs only, on a
- * stream of the highest priority, and the persistent grids of a large batch are sized for
- * three quarters of the SMs, so small jobs neither queue behind large ones nor wait for
- * a large kernel to free the SMs.  The batch is admitted once the arena can hold it; the
- * worker then runs the batch
+ * resultants in x, or gcd / square-free jobs) and work class (a resultant whose plan
+ * counts more than 2e9 multiply-reduce operations in its univariate stage, about a
+ * millisecond of the GPU, is large, one of at most 2e8 tiny, any other job small), first
+ * come first served and at most `max_batch` jobs; with two or more slots the last half of
+ * the workers (at least one) take no large jobs.  Tiny and small
+ * batches run on a stream of the highest priority, large ones on a stream of the lowest
+ * with grids of short blocks sized by their work, so small jobs neither queue behind
+ * large ones nor wait for a large kernel to free the SMs (their blocks start as the large
+ * kernel's blocks end), and a large batch alone still has the whole GPU.  The batch is
+ * admitted once the arena can hold it; the worker then runs the batch
  * (one graph launch for resultants, one pass of launches for gcds), posts the results
  * and frees the arena space.  Workers run concurrently, so batches admitted while
  * others are on the GPU overlap with them.  Every intermediate (residues, images,
@@ -512,6 +514,10 @@ typedef struct {
   int64_t submitted, completed, batches, jobs_in_batches, queued;
   int32_t inflight, max_inflight;   /* batches on the GPU now / at most at once */
   int64_t arena_bytes, arena_used, arena_peak;
+  /* wall time summed over the batches run so far, per phase of a batch: host planning,
+   * device work (upload, kernels and download, until the slot's stream is idle; batches
+   * of several slots overlap) and the formatting of the results */
+  double host_plan_ms, device_ms, host_finish_ms;
 } bs_serve_info;
 
 /* Start the serving loop (1 <= slots <= 16, max_batch >= 1).  BS_ERR_NOMEM if the arena

@@ -77,7 +77,8 @@ class _ServeInfo(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("batches", C.c_int64),
                 ("jobs_in_batches", C.c_int64), ("queued", C.c_int64),
                 ("inflight", C.c_int32), ("max_inflight", C.c_int32),
-                ("arena_bytes", C.c_int64), ("arena_used", C.c_int64), ("arena_peak", C.c_int64)]
+                ("arena_bytes", C.c_int64), ("arena_used", C.c_int64), ("arena_peak", C.c_int64),
+                ("host_plan_ms", C.c_double), ("device_ms", C.c_double), ("host_finish_ms", C.c_double)]
 
 
 BS_PENDING = 10

@@ -135,6 +135,7 @@ extern "C" void bs_free(bs_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
   if (ctx->stream && ctx->stream != ctx->own_stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->aux_stream) cudaStreamSynchronize(ctx->aux_stream);
   ctx->own_tabs.release();  // serving slots borrow their parent's tables
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->dev_ws) cudaFree(ctx->dev_ws);
@@ -143,6 +144,7 @@ extern "C" void bs_free(bs_ctx* ctx) {
   if (ctx->h_down) cudaFreeHost(ctx->h_down);
   ctx_release_extra(ctx);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   delete ctx;
 }
 
@@ -475,6 +477,7 @@ int batch_launch(bs_ctx* ctx, HostBatch& B, const bs_bipoly* f, const bs_bipoly*
       J.rows = (P.me + 1) + (P.ne + 1);
       J.ev = (uint32_t*)(base + B.o_ev[i]);
       J.vals = (uint32_t*)(base + B.o_vals[i]);
+      J.den_in_ev = P.logN <= kWarpInttLogNMax;  // interpolated one warp per prime
       J.rmod = (uint32_t*)(base + B.o_rmod[i]);
       J.sel = (int32_t*)(base + B.o_sel[i]);
       J.pstat = (int32_t*)(base + B.o_pstat) + ps_pos;
@@ -834,12 +837,14 @@ extern "C" int bs_set_tune(bs_ctx* ctx, const bs_tune_info* t) {
 extern "C" int bs_resultant(bs_ctx* ctx, const bs_bipoly* f, const bs_bipoly* g, int var,
                             bs_upoly* out) {
   if (!ctx) return BS_ERR_ARG;
+  NvtxScope nv("bs_resultant");
   return run_host_batch(ctx, 1, f, g, var, out, false);
 }
 
 extern "C" int bs_resultant_batch(bs_ctx* ctx, int n, const bs_bipoly* f, const bs_bipoly* g,
                                   int var, bs_upoly* out) {
   if (!ctx) return BS_ERR_ARG;
+  NvtxScope nv("bs_resultant_batch");
   return run_host_batch(ctx, n, f, g, var, out, true);
 }
 
@@ -851,6 +856,7 @@ extern "C" int bs_resultant_device(bs_ctx* ctx, const bs_bipoly* f, const bs_bip
   if (!ctx) return BS_ERR_ARG;
   if (!out || !out->c || (var != 0 && var != 1)) return ctx_fail(ctx, BS_ERR_ARG, "bad arguments");
   if (ctx->server) return ctx_fail(ctx, BS_ERR_ARG, "the context runs a serving loop");
+  NvtxScope nv("bs_resultant_device");
   int rc = check_bipoly(ctx, f, "f");
   if (rc) return rc;
   rc = check_bipoly(ctx, g, "g");

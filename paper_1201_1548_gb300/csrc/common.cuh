@@ -80,6 +80,12 @@ struct Job {
   Plan plan;
   uint32_t* ev;    // [k_total][rows][N] evaluations (Montgomery form)
   uint32_t* vals;  // [k_total][N] univariate resultants (Montgomery form, bit-reversed order)
+  // 1 (host batches whose transforms are interpolated one warp per prime): the univariate
+  // stage leaves each value's numerator in vals and its denominator in the instance's
+  // first evaluation word ev[q][0][t] (read by the instance itself, then dead), and the
+  // interpolating warp divides them with one inversion per prime (Montgomery's
+  // simultaneous inversion); 0: vals are final
+  int32_t den_in_ev;
   uint32_t* rmod;  // [k_need][D + 1] residues of the result coefficients (standard form)
   int32_t* pstat;  // [k_total] 0 = good prime, 1 = rejected
   int32_t* sel;    // [k_need] table index of the j-th selected prime

@@ -1,6 +1,7 @@
 // Host-side context of libbsres.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 
@@ -10,6 +11,14 @@
 #include "tables.cuh"
 
 namespace bs {
+
+// names a host call for a profiler (an NVTX range over the call); nothing without one
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
 // launch shapes of the batched stages: defaults, or what bs_autotune_batch measured best
 // for a batch (the device-planned single job always uses the defaults)
 struct Tune {
@@ -30,6 +39,11 @@ struct bs_ctx {
   int smem_optin = 48 * 1024;
   size_t budget = 0;
   cudaStream_t own_stream = nullptr;
+  // serving slots: a second stream of the lowest priority for large batches (own_stream
+  // has the highest), and grids sized by the work instead of the SMs for those batches, so
+  // that blocks of small batches are scheduled between theirs
+  cudaStream_t aux_stream = nullptr;
+  bool fine_grids = false;
   cudaStream_t stream = nullptr;
   bs::DeviceTables own_tabs;
   bs::DeviceTables* tabs = &own_tabs;  // serving slots point at their parent's tables

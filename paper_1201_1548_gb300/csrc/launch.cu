@@ -7,6 +7,9 @@
 
 namespace bs {
 
+// SM count that stands in for the real one when a context's grids follow the work
+constexpr int kFineGridSms = 1 << 16;
+
 static int grid_for(int64_t items, int cap) {
   if (items <= 0) return 0;
   return (int)std::min<int64_t>(items, cap);
@@ -41,6 +44,14 @@ size_t crt_warp_smem(int kmax, int lmax) {
          sizeof(uint32_t);
 }
 
+// NVTX ranges around each stage's launches ("bs.plan", "bs.eval", "bs.unires",
+// "bs.interp", "bs.crt") let a profiler select a stage's kernels (ncu --nvtx
+// --nvtx-include "bs.unires/"); without a tool attached the calls do nothing
+static inline void nvtx_next(const char* name) {
+  nvtxRangePop();
+  nvtxRangePushA(name);
+}
+
 static inline void mark(bs_ctx* ctx, int i, cudaStream_t s) {
   if (!ctx->profile) return;
   cudaEventRecord(ctx->prof_ev[i], s);
@@ -49,11 +60,14 @@ static inline void mark(bs_ctx* ctx, int i, cudaStream_t s) {
 
 static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStream_t s, int crt_w,
                     size_t crt_smem, int crt_staged) {
-  const int sms = ctx->sms;
+  // fine grids: the caps below (persistent grids of a few blocks per SM) become far larger
+  // than any work list, so every grid is sized by its work and each block is short
+  const int sms = ctx->fine_grids ? kFineGridSms : ctx->sms;
   const size_t tsmem = sizeof(uint32_t) * (size_t)L.maxN;
   // the profiling events between the stages would separate them: no overlap then
   set_launch_pdl(L.pdl && !ctx->profile);
   mark(ctx, 1, s);
+  nvtxRangePushA("bs.eval");
   int g;
   const PfHint pf{L.kt_max, 1 << L.logN_max, L.kmax};
   for (int c = 0; c < kNumEvalClasses; ++c) {
@@ -79,6 +93,7 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   g = grid_for(L.eval_items, (int64_t)sms * ebps);
   if (g) launch_eval(g, ecw, s, L.jobs, L.eval, Tv);
   mark(ctx, 2, s);
+  nvtx_next("bs.unires");
   for (int c = 0; c < kNumUniClasses; ++c) {
     const int th = L.uni_threads[c];
     const int ti = th == 64 ? 0 : th == 128 ? 1 : 2;
@@ -86,11 +101,13 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
     if (g) launch_uni(c, g, th, s, L.jobs, L.uni[c], Tv);
   }
   mark(ctx, 3, s);
+  nvtx_next("bs.interp");
   g = grid_for((L.intt_w_items + kInttWarps - 1) / kInttWarps, (int64_t)sms * 8);
   if (g) launch_intt_w(g, s, L.jobs, L.intt_w, Tv);
   g = grid_for(L.intt_items, (int64_t)sms * 8);
   if (g) launch_intt(g, kInttSmemWords * tsmem, s, L.jobs, L.intt, Tv);
   mark(ctx, 4, s);
+  nvtx_next("bs.crt");
   g = grid_for(L.crt_items, (int64_t)sms * L.crt_blocks_per_sm);
   const size_t wsm = crt_warp_smem(L.kmax, L.lmax);
   if (g && L.kmax <= kCrtWarpMaxK && wsm <= (size_t)ctx->smem_optin - 64)
@@ -109,6 +126,7 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
     if (g && fw) launch_crt(g, fw * 32, fsm, s, L.jobs, L.crt_big_fb, Tv, L.kmax_big, L.lmax_big, fst, 1);
   }
   set_launch_pdl(false);
+  nvtxRangePop();
   mark(ctx, 5, s);
 }
 
@@ -178,7 +196,9 @@ int launch_device_job(bs_ctx* ctx, const Job& J, Job* dj, int64_t* offs, const M
   // the plan kernel receives the job by value, zeroes its prime flags and stores the
   // planned job for the stage kernels
   const bool indep = ctx->tune.eval_independent != 0;
+  nvtxRangePushA("bs.plan");
   launch_plan_single(s, J, dj, offs, Tv, indep ? 1 : kEvalThreads / 32);
+  nvtxRangePop();
   StageLaunch L;
   L.jobs = dj;
   const bool wsize = mb.logN <= kWarpLogNMax;  // the actual size is at most the bound

@@ -721,8 +721,13 @@ __device__ __forceinline__ void unires_instance(const Job* J, int64_t inst, cons
   // the table's first primes have 3p < 2^32 (no fold in the fused updates)
   const uint32_t num = pc.p <= kSmallPrimeMax ? unires_numden<L, true>(A, me + 1, B, ne + 1, M, pc.one_m, &den)
                                               : unires_numden<L, false>(A, me + 1, B, ne + 1, M, pc.one_m, &den);
-  if (dbg_ok(inst < job_vals_words(J), J->status, kDbgUniOut))
+  if (!dbg_ok(inst < job_vals_words(J), J->status, kDbgUniOut)) return;
+  if (J->den_in_ev) {  // the warp interpolation divides (one inversion per prime)
+    J->vals[inst] = num;
+    J->ev[b0] = den;   // this instance's own first evaluation word, read above
+  } else {
     J->vals[inst] = mmul(num, minv(den, pc.one_m, M), M);
+  }
 }
 
 template <int L>
@@ -759,6 +764,46 @@ __global__ void __maxnreg__(SplitK<L>::regs) k_unires_split(const Job* jobs, Wor
     unires_instance<L>(jobs + (wl.ids ? wl.ids[ji] : ji), g - wl.off[ji], T, A, B);
   }
   pdl_trigger();
+}
+
+// ------------------------------------------------------------------------------------
+// the division of the univariate values (jobs with den_in_ev): Montgomery's simultaneous
+// inversion.  With d_0 ... d_(n-1) the denominators of one prime, one inversion of their
+// product G and prefix / suffix products give every 1/d_i = (1/G) (d_0...d_(i-1))
+// (d_(i+1)...d_(n-1)); each thread holds a few values, the threads' products are joined
+// with shuffles.  Every denominator is a product of nonzero leading-coefficient powers, so
+// G is invertible.
+// ------------------------------------------------------------------------------------
+
+// v[k] /= d[k] for the R values of each lane of a warp (padding: d = one, any v)
+template <int R>
+__device__ __forceinline__ void warp_divide(uint32_t (&v)[R], const uint32_t (&d)[R], const Mod& M,
+                                            uint32_t one) {
+  const int lane = threadIdx.x & 31;
+  uint32_t pl[R];  // pl[k] = d[0] ... d[k]
+  pl[0] = d[0];
+#pragma unroll
+  for (int k = 1; k < R; ++k) pl[k] = mmul(pl[k - 1], d[k], M);
+  uint32_t pre = pl[R - 1], suf = pl[R - 1];  // inclusive products over the lanes
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(0xffffffffu, pre, o);
+    const uint32_t b = __shfl_down_sync(0xffffffffu, suf, o);
+    if (lane >= o) pre = mmul(pre, a, M);
+    if (lane + o < 32) suf = mmul(suf, b, M);
+  }
+  const uint32_t G = __shfl_sync(0xffffffffu, pre, 31);
+  uint32_t epre = __shfl_up_sync(0xffffffffu, pre, 1);
+  uint32_t esuf = __shfl_down_sync(0xffffffffu, suf, 1);
+  if (lane == 0) epre = one;
+  if (lane == 31) esuf = one;
+  uint32_t inv = mmul(minv(G, one, M), mmul(epre, esuf, M), M);  // 1 / pl[R - 1]
+#pragma unroll
+  for (int k = R - 1; k >= 0; --k) {
+    const uint32_t invd = k ? mmul(inv, pl[k - 1], M) : inv;
+    v[k] = mmul(v[k], invd, M);
+    if (k) inv = mmul(inv, d[k], M);
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -876,6 +921,14 @@ __device__ __forceinline__ void intt_prime_warp(const Job* J, int q, int r, cons
   uint32_t v[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) v[k] = (32 * k + lane < N) ? src[32 * k + lane] : 0u;
+  if (J->den_in_ev &&
+      dbg_ok(((int64_t)q * J->rows + 1) * N <= job_ev_words(J), J->status, kDbgInttIn)) {  // uniform
+    const uint32_t* den = J->ev + (int64_t)q * J->rows * N;
+    uint32_t d[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) d[k] = (32 * k + lane < N) ? den[32 * k + lane] : pc.one_m;
+    warp_divide<R>(v, d, M, pc.one_m);
+  }
   __syncwarp();
   if constexpr (R == 32)
     warp_dit_1024_pk(v, sw, Pi, M);

@@ -10,14 +10,17 @@
 // All slots share the context's prime tables; a slot that needs larger tables waits
 // until no batch is in flight before growing them.
 //
-// Work classes keep small jobs from waiting behind large ones: a job is large when its
-// plan counts more than kLargeWork multiply-reduce operations (for a resultant: the
-// univariate eliminations of all its (prime, point) images), and a batch never mixes
-// classes, since every job of a batch finishes when the batch does.  With two or more
-// slots the last slot takes small jobs only, on a stream of the highest priority, so a
-// small job finds a slot even while the others run large batches; and the persistent
-// grids of a large batch are sized for kLargeShare of the SMs, so that the blocks of
-// small batches find room on every SM instead of waiting for a large kernel to end.
+// Work classes keep small jobs from waiting behind large ones: a resultant is large when
+// its plan counts more than kLargeWork multiply-reduce operations (the univariate
+// eliminations of all its (prime, point) images), tiny when it counts at most kTinyWork,
+// small otherwise, and a batch never mixes classes, since every job of a batch finishes
+// when the batch does.  With two or more slots the last half of them (at least one) take
+// tiny and small jobs only, so those find a slot even while the others run large
+// batches.  Every slot launches small batches on a stream of the highest
+// priority and large batches on one of the lowest, and a large batch's grids are sized by
+// its work (short blocks) instead of persistent blocks on every SM: the block scheduler
+// then starts the blocks of a small batch as soon as blocks of the large kernel end, and
+// a large batch alone still has the whole GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -106,7 +109,8 @@ struct Ticket {
   bs_upoly a{}, b{};
   std::vector<uint32_t> ac, bc;
   size_t bytes = 0;  // device bytes of the job as a batch of one (admission estimate)
-  int large = 0;     // work class (1: more than kLargeWork operations)
+  int large = 0;     // 1: more than kLargeWork operations
+  int work = 0;      // work class: 0 up to kTinyWork operations, 1 up to kLargeWork, 2 above
   int state = 0;     // 0 queued, 1 running, 2 done
   int status = 0;
   int deg = -1, limbs = 1;
@@ -133,6 +137,7 @@ struct bs_server {
   // statistics
   int64_t submitted = 0, completed = 0, batches = 0, jobs_in_batches = 0;
   int inflight = 0, max_inflight = 0;
+  double phase_ms[3] = {0, 0, 0};  // host planning, device (launch to stream idle), formatting
 };
 
 namespace bs {
@@ -140,12 +145,13 @@ namespace bs {
 static int job_type(const Ticket& t) { return t.kind == BS_JOB_RESULTANT ? (t.var ? 1 : 0) : 2; }
 
 // jobs of one batch: the same type and the same work class
-static int batch_class(const Ticket& t) { return job_type(t) * 2 + t.large; }
+static int batch_class(const Ticket& t) { return job_type(t) * 3 + t.work; }
 
 // work of a large job: about a millisecond of the GPU's multiply pipe
 constexpr double kLargeWork = 2e9;
-// share of the SMs the persistent grids of a large batch are sized for
-constexpr double kLargeShare = 0.75;
+// work of a tiny job (a tenth of that): tiny jobs are not batched with larger small ones,
+// whose batch would hold them back
+constexpr double kTinyWork = 2e8;
 // pinned staging of a slot allocated at start (each way)
 constexpr size_t kSlotPinnedBytes = size_t(64) << 20;
 
@@ -159,8 +165,9 @@ static size_t jobs_bytes(const std::vector<Ticket*>& jobs) {
   return s;
 }
 
-// the slot context: own stream, status word and graph; the parent's tables
-static int make_slot(bs_ctx* parent, bool high_priority, bs_ctx** out) {
+// the slot context: two streams (small batches at the highest priority, large ones at
+// the lowest), status word and graph; the parent's tables
+static int make_slot(bs_ctx* parent, bs_ctx** out) {
   bs_ctx* c = new bs_ctx();
   c->device = parent->device;
   c->sms = parent->sms;
@@ -173,8 +180,12 @@ static int make_slot(bs_ctx* parent, bool high_priority, bs_ctx** out) {
   c->tune = parent->tune;
   int lo = 0, hi = 0;  // numerically lower is higher priority
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
-  if (cudaStreamCreateWithPriority(&c->own_stream, cudaStreamNonBlocking, high_priority ? hi : lo) !=
-      cudaSuccess) {
+  if (cudaStreamCreateWithPriority(&c->own_stream, cudaStreamNonBlocking, hi) != cudaSuccess) {
+    delete c;
+    return BS_ERR_CUDA;
+  }
+  if (cudaStreamCreateWithPriority(&c->aux_stream, cudaStreamNonBlocking, lo) != cudaSuccess) {
+    cudaStreamDestroy(c->own_stream);
     delete c;
     return BS_ERR_CUDA;
   }
@@ -185,11 +196,13 @@ static int make_slot(bs_ctx* parent, bool high_priority, bs_ctx** out) {
     if (c->h_up) cudaFreeHost(c->h_up);
     if (c->h_down) cudaFreeHost(c->h_down);
     cudaStreamDestroy(c->own_stream);
+    cudaStreamDestroy(c->aux_stream);
     delete c;
     return BS_ERR_NOMEM;
   }
   if (cudaMalloc(&c->d_status, sizeof(int32_t) * 4) != cudaSuccess) {
     cudaStreamDestroy(c->own_stream);
+    cudaStreamDestroy(c->aux_stream);
     delete c;
     return BS_ERR_CUDA;
   }
@@ -198,13 +211,24 @@ static int make_slot(bs_ctx* parent, bool high_priority, bs_ctx** out) {
   return 0;
 }
 
+static double ms_since(Clock::time_point& t0) {
+  const auto t1 = Clock::now();
+  const double ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  t0 = t1;
+  return ms;
+}
+
 // run one batch of tickets (all of one type) on slot context c, inside dev; fills the
-// tickets' results (called without the server lock)
-static void run_batch(bs_server* S, bs_ctx* c, std::vector<Ticket*>& jobs, char* dev) {
+// tickets' results (called without the server lock) and adds the wall time of its host
+// planning, device work and result formatting to ph[0..2]
+static void run_batch(bs_server* S, bs_ctx* c, std::vector<Ticket*>& jobs, char* dev, double* ph) {
+  NvtxScope nv(jobs[0]->large ? "bs.serve.large_batch" : "bs.serve.batch");
+  auto t0 = Clock::now();
   const int n = (int)jobs.size();
   const int type = job_type(*jobs[0]);
-  // a large batch leaves room on every SM for the blocks of small ones
-  c->sms = jobs[0]->large ? std::max(1, (int)(S->parent->sms * kLargeShare)) : S->parent->sms;
+  // a large batch: low priority, short blocks (small batches' blocks start between them)
+  c->stream = jobs[0]->large ? c->aux_stream : c->own_stream;
+  c->fine_grids = jobs[0]->large != 0;
   int rc = 0;
   std::vector<bs_upoly> outs(n);
   auto fail_all = [&](int code) {
@@ -224,6 +248,7 @@ static void run_batch(bs_server* S, bs_ctx* c, std::vector<Ticket*>& jobs, char*
     rc = batch_plan(c, n, f.data(), g.data(), type, &B);
     if (!rc && B.total > jobs_bytes(jobs)) rc = BS_ERR_INTERNAL;
     if (rc) return fail_all(rc);
+    ph[0] += ms_since(t0);
     {
       std::shared_lock<std::shared_mutex> lk(S->tables_mu, std::defer_lock);
       for (;;) {
@@ -238,6 +263,7 @@ static void run_batch(bs_server* S, bs_ctx* c, std::vector<Ticket*>& jobs, char*
       if (!rc) rc = batch_launch(c, B, f.data(), g.data(), dev, (char*)c->h_up, (char*)c->h_down, true);
       if (!rc) rc = ctx_cuda(c, cudaStreamSynchronize(c->stream), "stream");
     }
+    ph[1] += ms_since(t0);
     if (rc) return fail_all(rc);
     for (int i = 0; i < n; ++i) {
       const Plan& P = B.plans[i];
@@ -246,6 +272,7 @@ static void run_batch(bs_server* S, bs_ctx* c, std::vector<Ticket*>& jobs, char*
       outs[i] = bs_upoly{std::max(P.D, 0), P.out_limbs, jobs[i]->out.data()};
     }
     rc = batch_finish(c, B, (const char*)c->h_down, outs.data());
+    ph[2] += ms_since(t0);
     if (rc) return fail_all(rc);
     for (int i = 0; i < n; ++i) {
       jobs[i]->status = 0;
@@ -264,6 +291,7 @@ static void run_batch(bs_server* S, bs_ctx* c, std::vector<Ticket*>& jobs, char*
   rc = mg_plan(c, n, kind.data(), a.data(), b.data(), &B);
   if (!rc && B.total > jobs_bytes(jobs)) rc = BS_ERR_INTERNAL;
   if (rc) return fail_all(rc);
+  ph[0] += ms_since(t0);
   {
     std::shared_lock<std::shared_mutex> lk(S->tables_mu, std::defer_lock);
     for (;;) {
@@ -278,6 +306,7 @@ static void run_batch(bs_server* S, bs_ctx* c, std::vector<Ticket*>& jobs, char*
     if (!rc) rc = mg_launch(c, B, a.data(), b.data(), dev, (char*)c->h_up, (char*)c->h_down);
     if (!rc) rc = ctx_cuda(c, cudaStreamSynchronize(c->stream), "stream");
   }
+  ph[1] += ms_since(t0);
   if (rc) return fail_all(rc);
   for (int i = 0; i < n; ++i) {
     int d, l;
@@ -288,6 +317,7 @@ static void run_batch(bs_server* S, bs_ctx* c, std::vector<Ticket*>& jobs, char*
   }
   std::vector<int> st(n, 0);
   mg_finish(c, B, (const char*)c->h_down, outs.data(), st.data());
+  ph[2] += ms_since(t0);
   for (int i = 0; i < n; ++i) {
     jobs[i]->status = st[i];
     jobs[i]->deg = st[i] ? -1 : outs[i].deg;
@@ -304,7 +334,9 @@ static void slot_main(bs_server* S, int slot) {
     std::vector<uint64_t> ids;
     std::vector<Ticket*> jobs;
     size_t off = 0, bytes = 0;
-    const bool small_only = S->slots.size() >= 2 && slot == (int)S->slots.size() - 1;
+    // the last half of the slots (at least one of two or more) take no large jobs
+    const int ns = (int)S->slots.size();
+    const bool small_only = ns >= 2 && slot >= ns - std::max(1, ns / 2);
     for (;;) {
       if (S->stop && S->queue.empty()) return;
       // the head: the oldest queued job (the oldest small one for the small-job slot)
@@ -347,8 +379,10 @@ static void slot_main(bs_server* S, int slot) {
     ++S->inflight;
     S->max_inflight = std::max(S->max_inflight, S->inflight);
     lk.unlock();
-    run_batch(S, c, jobs, S->arena_base + off);
+    double ph[3] = {0, 0, 0};
+    run_batch(S, c, jobs, S->arena_base + off, ph);
     lk.lock();
+    for (int i = 0; i < 3; ++i) S->phase_ms[i] += ph[i];
     --S->inflight;
     S->arena.release(off, bytes);
     const auto done = Clock::now();
@@ -388,7 +422,7 @@ extern "C" int bs_serve_start(bs_ctx* ctx, int slots, int max_batch, size_t aren
   S->arena.reset(arena_bytes);
   for (int i = 0; i < slots; ++i) {
     bs_ctx* c = nullptr;
-    if (make_slot(ctx, slots >= 2 && i == slots - 1, &c) != 0) {
+    if (make_slot(ctx, &c) != 0) {
       for (bs_ctx* d : S->slots) bs_free(d);
       cudaFree(S->arena_base);
       delete S;
@@ -447,6 +481,7 @@ extern "C" int bs_submit(bs_ctx* ctx, const bs_job* job, uint64_t* ticket) {
     if (rc) return rc;
     t.bytes = B.total;
     t.large = (double)B.mulmods > kLargeWork;
+    t.work = t.large ? 2 : (double)B.mulmods > kTinyWork ? 1 : 0;
   } else if (job->kind == BS_JOB_GCD || job->kind == BS_JOB_SQFREE) {
     if (copy_upoly(&job->a, &t.a, &t.ac)) return ctx_fail(ctx, BS_ERR_ARG, "bad operand a");
     if (job->kind == BS_JOB_GCD) {
@@ -537,5 +572,8 @@ extern "C" int bs_serve_stats(bs_ctx* ctx, bs_serve_info* out) {
   out->arena_bytes = (int64_t)S->arena.size();
   out->arena_used = (int64_t)S->arena.used();
   out->arena_peak = (int64_t)S->arena.peak();
+  out->host_plan_ms = S->phase_ms[0];
+  out->device_ms = S->phase_ms[1];
+  out->host_finish_ms = S->phase_ms[2];
   return BS_OK;
 }
