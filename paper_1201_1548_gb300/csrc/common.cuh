@@ -115,6 +115,14 @@ struct Job {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Asynchronous 4-byte copy from global to shared memory (cp.async, no register staging):
+// a thread issues many and waits once with cp_async_wait_all (a hardware wait).
+__device__ __forceinline__ void cp_async4(uint32_t* sdst, const uint32_t* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // work lists: stage work of job ids[i] occupies [off[i], off[i+1]) of a flat index space
 struct WorkList {
   const int32_t* ids;  // may be null: identity

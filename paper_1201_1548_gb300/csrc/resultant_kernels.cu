@@ -839,10 +839,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
       const uint32_t* icq = T.icp + (int64_t)q * T.NT;
       const bool in_ok = dbg_ok(((int64_t)(q + 1) << logN) <= job_vals_words(J), J->status, kDbgInttIn) &&
                          dbg_ok(q < T.Tt && N <= T.NT, J->status, kDbgInttTab);
-      for (int t = threadIdx.x; t < N && in_ok; t += blockDim.x) {
-        sm[t] = src[t];
-        sit[t] = __ldg(itq + t);
-        sic[t] = __ldg(icq + t);
+      for (int t = threadIdx.x; t < N && in_ok; t += blockDim.x) {  // all in flight at once
+        cp_async4(sm + t, src + t);
+        cp_async4(sit + t, itq + t);
+        cp_async4(sic + t, icq + t);
       }
     }
     int cnt = 0;
@@ -853,6 +853,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
       for (int j = threadIdx.x; j < k_total; j += blockDim.x) g += (J->pstat[j] == 0);
       if (g) atomicAdd(&s_good, g);
     }
+    cp_async_wait_all();
     __syncthreads();
     const int r = s_rank;
     if (q == 0) {
@@ -1504,6 +1505,40 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
     const int k = P.k_need, D = P.D, Tg = T.Tg;
     const int nvalid = min(ncoef, D + 1 - i0);
     const int nl = min(min(P.out_limbs, lmax), T.LPP);
+    // Every staging copy is issued before any is waited for: the tables and the residues
+    // go to shared memory by asynchronous copies (all in flight at once, one round trip),
+    // while the selected primes' constants come through registers.
+    const int L = ws_len(k);
+    if (k <= T.WK &&
+        dbg_ok(T.ws_moff[k] + (int64_t)k * L <= T.ws_m_words && k <= T.Tg && L <= kmax + 4 &&
+                   (int64_t)k * L <= (int64_t)kmax * (kmax + 1),
+               J->status, kDbgCrtWs)) {
+      // weighted-sum tables (they depend on k only; the Garner path below overwrites them
+      // when the selected primes are not the first k): M_k is k rows of L limbs, contiguous
+      const uint32_t* Mk = T.ws_m + T.ws_moff[k];
+      const int n = k * L;
+      for (int t = threadIdx.x; t < n; t += nthr) cp_async4(sinv + t, Mk + t);
+      const uint32_t* yk = T.ws_y + T.ws_yoff[k];
+      for (int t = threadIdx.x; t < k; t += nthr) {
+        cp_async4(sy + t, yk + t);
+        cp_async4(sq62 + t, T.q62 + t);
+      }
+      const uint32_t* Pk = T.pp + (int64_t)k * T.LPP;
+      for (int t = threadIdx.x; t < L; t += nthr) {
+        if (t < T.LPP)
+          cp_async4(sPk + t, Pk + t);
+        else
+          sPk[t] = 0u;
+      }
+    }
+    const bool x_ok = dbg_ok((int64_t)(k - 1) * (D + 1) + i0 + nvalid <= job_rmod_words(J), J->status, kDbgCrtIn);
+    for (int t = threadIdx.x; t < k * kCrtTile; t += nthr) {  // columns >= tile stay unused
+      const int j = t / kCrtTile, c = t - j * kCrtTile;
+      if (c < nvalid && x_ok)
+        cp_async4(X + t, J->rmod + (int64_t)j * (D + 1) + i0 + c);
+      else
+        X[t] = 0u;
+    }
     for (int j = threadIdx.x; j < k; j += nthr) {
       int s = J->sel[j];
       if (!dbg_ok(s >= 0 && s < T.Tg && s < J->plan.k_total, J->status, kDbgCrtSel) || s < 0 || s >= T.Tg)
@@ -1513,32 +1548,7 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
       pinvq[j] = pc.pinv;
       selq[j] = (uint32_t)s;
     }
-    const bool x_ok = dbg_ok((int64_t)(k - 1) * (D + 1) + i0 + nvalid <= job_rmod_words(J), J->status, kDbgCrtIn);
-#pragma unroll 4
-    for (int t = threadIdx.x; t < k * kCrtTile; t += nthr) {  // columns >= tile stay unused
-      const int j = t / kCrtTile, c = t - j * kCrtTile;
-      X[t] = (c < nvalid && x_ok) ? J->rmod[(int64_t)j * (D + 1) + i0 + c] : 0u;
-    }
-    const int L = ws_len(k);
-    if (k <= T.WK &&
-        dbg_ok(T.ws_moff[k] + (int64_t)k * L <= T.ws_m_words && k <= T.Tg && L <= kmax + 4 &&
-                   (int64_t)k * L <= (int64_t)kmax * (kmax + 1),
-               J->status, kDbgCrtWs)) {
-      // weighted-sum tables, staged with the residues (they depend on k only; the Garner
-      // path below overwrites them when the selected primes are not the first k):
-      // M_k is k rows of L limbs, contiguous: one flat copy with many loads in flight
-      const uint32_t* Mk = T.ws_m + T.ws_moff[k];
-      const int n = k * L;
-#pragma unroll 8
-      for (int t = threadIdx.x; t < n; t += nthr) sinv[t] = __ldg(Mk + t);
-      const uint32_t* yk = T.ws_y + T.ws_yoff[k];
-      for (int t = threadIdx.x; t < k; t += nthr) {
-        sy[t] = __ldg(yk + t);
-        sq62[t] = __ldg(T.q62 + t);
-      }
-      const uint32_t* Pk = T.pp + (int64_t)k * T.LPP;
-      for (int t = threadIdx.x; t < L; t += nthr) sPk[t] = t < T.LPP ? __ldg(Pk + t) : 0u;
-    }
+    cp_async_wait_all();
     __syncthreads();
     const bool table_order = (selq[k - 1] == (uint32_t)(k - 1));
     // weighted-sum path for table-ordered jobs with tabulated k; Garner otherwise
