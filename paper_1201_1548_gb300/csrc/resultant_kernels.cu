@@ -1410,23 +1410,27 @@ __device__ __forceinline__ void crt_ws_warp(const Job* J, const Plan& P, int i, 
     uint64_t acc = 0;
     uint32_t ah = 0;
     if (b0 < L) {
-      // two independent accumulation chains (even and odd q), joined at the end
+      // two independent accumulation chains, each adding the sum of two products at a
+      // time: t_q < p_q < 2^31 and a limb is below 2^32, so a product is below 2^63 and the
+      // sum of two fits 64 bits (one carry test per two products)
       uint64_t a0 = 0, a1 = 0;
       uint32_t h0 = 0, h1 = 0;
       const int lc = l < L ? l : 0;
       const uint32_t keep = l < L ? 0xffffffffu : 0u;
       int q = 0;
-#pragma unroll 4
-      for (; q + 1 < k; q += 2) {
-        const uint64_t p0 = (uint64_t)sd[q] * (Msm[q * L + lc] & keep);
-        const uint64_t p1 = (uint64_t)sd[q + 1] * (Msm[(q + 1) * L + lc] & keep);
-        const uint64_t s0 = a0 + p0, s1 = a1 + p1;
+#pragma unroll 2
+      for (; q + 3 < k; q += 4) {
+        const uint64_t pa = (uint64_t)sd[q] * (Msm[q * L + lc] & keep) +
+                            (uint64_t)sd[q + 1] * (Msm[(q + 1) * L + lc] & keep);
+        const uint64_t pb = (uint64_t)sd[q + 2] * (Msm[(q + 2) * L + lc] & keep) +
+                            (uint64_t)sd[q + 3] * (Msm[(q + 3) * L + lc] & keep);
+        const uint64_t s0 = a0 + pa, s1 = a1 + pb;
         h0 += (s0 < a0) ? 1u : 0u;
         h1 += (s1 < a1) ? 1u : 0u;
         a0 = s0;
         a1 = s1;
       }
-      if (q < k) {
+      for (; q < k; ++q) {
         const uint64_t p0 = (uint64_t)sd[q] * (Msm[q * L + lc] & keep);
         const uint64_t s0 = a0 + p0;
         h0 += (s0 < a0) ? 1u : 0u;
@@ -1540,12 +1544,15 @@ __global__ void __launch_bounds__(TILE * 32) k_crt_w(const Job* jobs, WorkList w
         X[t] = 0u;
     }
     for (int j = threadIdx.x; j < k; j += nthr) {
+      // the constants of table prime j are read together with the slot: a table-ordered
+      // selection (the usual one) then needs no second round trip
+      const int js = j < T.Tg ? j : 0;
+      const uint32_t pj = T.pc[js].p, pinvj = T.pc[js].pinv;
       int s = J->sel[j];
       if (!dbg_ok(s >= 0 && s < T.Tg && s < J->plan.k_total, J->status, kDbgCrtSel) || s < 0 || s >= T.Tg)
         s = 0;  // never read outside the tables, whatever the slot holds
-      const PrimeConst pc = T.pc[s];
-      pq[j] = pc.p;
-      pinvq[j] = pc.pinv;
+      pq[j] = s == j ? pj : T.pc[s].p;
+      pinvq[j] = s == j ? pinvj : T.pc[s].pinv;
       selq[j] = (uint32_t)s;
     }
     cp_async_wait_all();
