@@ -286,6 +286,13 @@ __device__ int prime_count_warp(const int64_t* lg_prefix, int T, int64_t need) {
   }
 }
 
+// whether p divides c (c < 2^64): the high word reduced modulo p, then one Montgomery
+// reduction of hi' 2^32 + lo < p 2^32, which is 0 exactly when p divides c
+__device__ __forceinline__ bool divides64(uint64_t c, uint32_t p, uint32_t pinv) {
+  const uint32_t hi = (uint32_t)(c >> 32) % p;
+  return redc(((uint64_t)hi << 32) | (uint32_t)c, p, pinv) == 0u;
+}
+
 __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, int64_t* offs, Tables T,
                                                               int eval_group) {
   constexpr int kRows = kPlanThreads / 16;  // row slots per half
@@ -295,6 +302,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
   __shared__ Plan sP;
   __shared__ int64_t s_need;
 
+  // the table's total, read now so that the check below does not wait for it
+  const int64_t lg_all = threadIdx.x == 0 ? T.lg_prefix[T.T] : 0;
   // warm L2 with the input grids (read right below)
   if (threadIdx.x == blockDim.x - 1)
     l2_prefetch_range(J.f.c, sizeof(uint32_t) * (size_t)(J.f.dx + 1) * (J.f.dy + 1) * J.f.L);
@@ -310,7 +319,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
     int64_t need;
     sP = plan_head_logs(sf.l2S, sf.m, sf.td, sf.dego, sg.l2S, sg.m, sg.td, sg.dego, &need);
     s_need = need;
-    if (sP.status == 0 && sP.trivial == 0 && T.lg_prefix[T.T] < need) sP.status = kErrRange;
+    if (sP.status == 0 && sP.trivial == 0 && lg_all < need) sP.status = kErrRange;
   }
   __syncthreads();
   if (threadIdx.x < 32 && sP.status == 0 && sP.trivial == 0) {
@@ -318,7 +327,52 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_single(Job J, Job* dst, i
     const int k = prime_count_warp(T.lg_prefix, T.T, s_need);
     // conservative count of primes that can divide a leading row; no coset spares when
     // both leading rows are monomials (they never vanish on a coset, which avoids 0)
-    if (lane == 0) plan_tail(sP, k, sf.lcb, sg.lcb, T.T, sf.lcnt == 1 && sg.lcnt == 1);
+    const bool mono = sf.lcnt == 1 && sg.lcnt == 1;
+    if (lane == 0) plan_tail(sP, k, sf.lcb, sg.lcb, T.T, mono);
+    __syncwarp();
+    if (mono && J.f.L <= 2 && J.g.L <= 2 && sP.status == 0) {
+      // both leading rows are single coefficients of at most 64 bits: count exactly the
+      // table primes that divide one of them (the host plan's rule), 32 primes per round,
+      // instead of the bound on how many can
+      const uint64_t cf = mag_narrow(coef_ptr(J.f, J.var, sf.m, sf.lco), J.f.L);
+      const uint64_t cg = mag_narrow(coef_ptr(J.g, J.var, sg.m, sg.lco), J.g.L);
+      const int want = sP.k_need;
+      const int Kmax = min(sP.k_total, T.T);  // the bound: want good primes lie below it
+      // constants of the first four rounds of primes, all loaded at once
+      uint32_t pp[4] = {1u, 1u, 1u, 1u}, pi[4] = {1u, 1u, 1u, 1u};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int j = 32 * r + lane;
+        if (j < Kmax) {
+          pp[r] = T.pc[j].p;
+          pi[r] = T.pc[j].pinv;
+        }
+      }
+      int K = Kmax, good = 0;
+      for (int base = 0, r = 0; base < Kmax; base += 32, ++r) {
+        const int j = base + lane;
+        bool div = false;
+        if (j < Kmax) {
+          uint32_t p, pinv;
+          if (r == 0) { p = pp[0]; pinv = pi[0]; }
+          else if (r == 1) { p = pp[1]; pinv = pi[1]; }
+          else if (r == 2) { p = pp[2]; pinv = pi[2]; }
+          else if (r == 3) { p = pp[3]; pinv = pi[3]; }
+          else { p = T.pc[j].p; pinv = T.pc[j].pinv; }
+          div = divides64(cf, p, pinv) || divides64(cg, p, pinv);
+        }
+        const unsigned gm = __ballot_sync(0xffffffffu, j < Kmax && !div);
+        const int g = __popc(gm);
+        if (good + g >= want) {  // the want-th good prime lies in this round
+          unsigned m = gm;
+          for (int t = 1; t < want - good; ++t) m &= m - 1;  // drop the lower good primes
+          K = base + __ffs(m);
+          break;
+        }
+        good += g;
+      }
+      if (lane == 0 && K <= sP.k_total) sP.k_total = K;  // never above the bound
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -845,6 +899,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
         cp_async4(sic + t, icq + t);
       }
     }
+    // the prime's constants, read now so that they arrive with the staged values
+    const PrimeConst pc = T.pc[q];
+    const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
     int cnt = 0;
     for (int j = threadIdx.x; j < q; j += blockDim.x) cnt += (J->pstat[j] == 0);
     if (cnt) atomicAdd(&s_rank, cnt);
@@ -873,10 +930,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_intt(const Job* jobs, WorkList
     __syncthreads();
     if (!good || r >= k_need) continue;
     const int D = J->plan.D;
-    const PrimeConst pc = T.pc[q];
     const Mod M{pc.p, pc.pinv};
     dit_intt(sm, logN, sit, M);
-    const uint32_t ni = T.ninv[q * (kLogNMax + 1) + logN];
     uint32_t* dst = J->rmod + (int64_t)r * (D + 1);
     const bool out_ok = dbg_ok((int64_t)(r + 1) * (D + 1) <= job_rmod_words(J), J->status, kDbgInttOut);
     bool bad = false;

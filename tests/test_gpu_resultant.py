@@ -145,6 +145,23 @@ def test_device_path_large_transforms(ctx):
             assert P.evaluate(dev, x0) % p == R.res_at_point_modp(f, g, x0, p)
 
 
+def test_device_plan_exact_spares(ctx):
+    """Single-coefficient leading rows: the device plan counts exactly the table primes that
+    divide them.  With lc_y f = p_0 p_1 (two table primes) those two are rejected and
+    replaced; with lc_y f = 1 no spare is evaluated.  Both results equal the oracle's."""
+    import paper_1201_1548_gb300 as bs
+    rng = _rng(41)
+    p0, p1 = nt.prime_table(2)
+    for lc in (p0 * p1, 1):
+        f = dense_curve(rng, 9, 12)
+        f[-1] = [lc] + [0] * (len(f[-1]) - 1)   # leading row in y: the constant lc
+        g = d_dy(f)
+        before = bs.bs_plan(f, g)
+        dev = _device_call(ctx, f, g)
+        assert dev == R.res_y(f, g)
+        assert before["k_total"] == before["k_need"] + (2 if lc != 1 else 0)
+
+
 def test_degenerate_cfg4(ctx):
     cases = cfg4_cases(seed=1, deg=5, bits=12, poison_prime=nt.prime_table(1)[0])
     # square factors: res_y(f, f_y) vanishes identically
