@@ -797,29 +797,6 @@ __global__ void __launch_bounds__(kUniMaxThreads) k_unires(const Job* jobs, Work
   pdl_trigger();
 }
 
-// The same with the polynomials' high entries in shared memory (SplitArr): blocks of
-// kSplitThreads threads, SplitK<L>::K register entries per polynomial, sized so that
-// SplitK<L>::blocks blocks fit on an SM.  For the degree-32 class this gives 18 warps per
-// SM instead of 16, enough to hold the 81 x 1024 images of a degree-32 discriminant in
-// one pass over the SMs.
-template <int L>
-__global__ void __maxnreg__(SplitK<L>::regs) k_unires_split(const Job* jobs, WorkList wl,
-                                                                                  Tables T) {
-  extern __shared__ uint32_t sm_split[];
-  constexpr int K = SplitK<L>::K, H = Arr<L>::N - K;
-  pdl_wait();
-  const int64_t total = wl.off[wl.n];
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const int ji = find_item(wl.off, wl.n, g);
-    SplitArr<L, K, kSplitThreads> A, B;
-    A.s = sm_split + threadIdx.x;
-    B.s = sm_split + H * kSplitThreads + threadIdx.x;
-    unires_instance<L>(jobs + (wl.ids ? wl.ids[ji] : ji), g - wl.off[ji], T, A, B);
-  }
-  pdl_trigger();
-}
-
 // ------------------------------------------------------------------------------------
 // the division of the univariate values (jobs with den_in_ev): Montgomery's simultaneous
 // inversion.  With d_0 ... d_(n-1) the denominators of one prime, one inversion of their
@@ -1730,7 +1707,6 @@ template __global__ void k_unires<24>(const Job*, WorkList, Tables);
 template __global__ void k_unires<33>(const Job*, WorkList, Tables);
 template __global__ void k_unires<48>(const Job*, WorkList, Tables);
 template __global__ void k_unires<65>(const Job*, WorkList, Tables);
-template __global__ void k_unires_split<33>(const Job*, WorkList, Tables);
 
 // ------------------------------------------------------------------------------------
 // launchers (kernels are launched from the translation unit that defines them)
@@ -1753,19 +1729,6 @@ int uni_occupancy(int cls, int threads) {
   }
 }
 
-size_t uni_split_smem() {
-  return sizeof(uint32_t) * 2 * (size_t)(Arr<33>::N - SplitK<33>::K) * kSplitThreads;
-}
-
-int uni_split_occupancy() {
-  int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_unires_split<33>, kSplitThreads, uni_split_smem());
-  return b > 0 ? b : 1;
-}
-
-void launch_uni_split(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
-  launch_k(k_unires_split<33>, grid, kSplitThreads, uni_split_smem(), s, jobs, wl, T);
-}
 
 void launch_uni(int cls, int grid, int threads, cudaStream_t s, const Job* jobs, WorkList wl, Tables T) {
   switch (cls) {

@@ -70,23 +70,6 @@ inline int big_ws_len(int k) { return (31 * k + 31) / 32 + 1; }
 void launch_bigcrt(int g_tab, int g_gemm, int g_carry, cudaStream_t s, const Job* jobs, WorkList tab,
                    WorkList gemm, WorkList carry, Tables T);
 
-// the univariate stage with the polynomials' high entries in shared memory (classes that
-// SplitK lists): threads per block, and per class the register entries of a polynomial and
-// the registers per thread the kernel is compiled for
-constexpr int kSplitThreads = 64;
-template <int L>
-struct SplitK {
-  static constexpr int K = 0, regs = 255;
-};
-template <>
-struct SplitK<33> {
-  static constexpr int K = 28, regs = 112;  // 9 blocks of 64 threads per SM
-};
-constexpr int kSplitClass = 3;  // the class (length 33) that has the split kernel
-int uni_split_occupancy();
-size_t uni_split_smem();
-void launch_uni_split(int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T);
-
 // degree classes of the univariate stage: max(m_e, n_e) + 1 <= class length
 constexpr int kUniClasses[] = {8, 16, 24, 33, 48, 65};
 constexpr int kNumUniClasses = 6;

@@ -34,20 +34,6 @@ struct Arr {
   static constexpr int N = LL + 2;            // storage (two zeros of headroom)
 };
 
-// A register array of Arr<L>::N entries whose entries from K on live in a column of
-// shared memory (entry u >= K at s[(u - K) * S], S the threads of the block): a thread
-// holds fewer registers, so more threads fit on an SM.  Every index the elimination uses
-// is a compile-time constant after unrolling, so the choice between register and shared
-// memory is resolved at compile time and the register part stays in registers.  The high
-// entries are touched only while a polynomial is longer than K - 2, in the first passes.
-template <int L, int K, int S>
-struct SplitArr {
-  uint32_t r[K];
-  uint32_t* s;
-  __device__ __forceinline__ uint32_t& operator[](int u) { return u < K ? r[u] : s[(u - K) * S]; }
-  __device__ __forceinline__ uint32_t operator[](int u) const { return u < K ? r[u] : s[(u - K) * S]; }
-};
-
 // P[u] = c2 P[u+2] + nc1 Q[u+2] + nc0 Q[u+1] for u < lp - 2, the new length (Q is at
 // most lp - 1 long).  The sum of the three products is below 3p^2; for a prime with
 // 3p < 2^32 (SMALLP) that is below p 2^32 and Montgomery's reduction applies directly,
