@@ -49,6 +49,9 @@ struct Tables {
   // (len = 1, 2, ..., NT/2; j < len; entry 0 is 1), Montgomery form
   const uint32_t* twp;
   const uint32_t* itwp;
+  // [Tt][64]: for j = 1 .. 31, tws[2 j] = twp[j] in standard form w and tws[2 j + 1] =
+  // floor(w 2^32 / p), the pairs of Shoup's products in the transforms' short stages
+  const uint32_t* tws;
   // Garner table for the first Tg primes: ginv[a * Tg + b] = p_a^-1 mod p_b (Montgomery)
   const uint32_t* ginv;
   // prefix products of the table primes: pp[j * LPP + l] = limb l of p_0 ... p_{j-1}

@@ -92,6 +92,15 @@ BS_HD uint32_t mpow(uint32_t a, uint32_t e, uint32_t one_m, const Mod& M) {
   return r;
 }
 
+// x w mod p for x < p and a fixed w < p with ws = floor(w 2^32 / p) (Shoup's method): the
+// quotient estimate umulhi(x, ws) is exact or one too small, so x w - q p lies in [0, 2p)
+BS_HD uint32_t mmul_shoup(uint32_t x, uint32_t w, uint32_t ws, uint32_t p) {
+  const uint32_t q = umulhi32(x, ws);
+  const uint32_t r = x * w - q * p;
+  const uint32_t r2 = r - p;
+  return r2 < r ? r2 : r;
+}
+
 // inverse of a non-zero Montgomery-form value by Fermat's little theorem
 BS_HD uint32_t minv(uint32_t a, uint32_t one_m, const Mod& M) {
   return mpow(a, M.p - 2, one_m, M);

@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kEvalBigMaxWarps * 32) k_eval(const Job* jobs,
     if (active) {
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = sm[1024 * warp + 32 * r + lane];
-      warp_dif_1024_pk<0xffffffffu>(v, sw, s_tw, M);
+      warp_dif_1024_pk<0xffffffffu>(v, sw, s_tw, T.tws + (int64_t)q * 64, M);
       uint32_t* dst = J->ev + ((int64_t)q * rows + row) * N + 1024 * warp;
 #pragma unroll
       for (int r = 0; r < 32; ++r) dst[32 * r + lane] = v[r];
@@ -567,7 +567,7 @@ __device__ __forceinline__ void eval_row_nz(const Job* J, int q, int row, const 
   uint32_t v[R];
   eval_load_row<R, (NZ < R ? NZ : R)>(v, J, q, row, T, sw, s_cp, pc, M, N);
   if constexpr (R == 32)
-    warp_dif_1024_pk<MASK>(v, sw, s_tw, M);
+    warp_dif_1024_pk<MASK>(v, sw, s_tw, T.tws + (int64_t)q * 64, M);
   else
     warp_dif_pk<R, MASK>(v, s_tw, M, pc.one_m);
   uint32_t* dst = J->ev + ((int64_t)q * J->rows + row) * N;

@@ -199,6 +199,17 @@ __global__ void k_init_packed(const PrimeConst* pc, int Tt, int NT, int logNT, c
   }
 }
 
+// the Shoup pairs of the first 32 packed twiddles of every prime
+__global__ void k_init_shoup(const PrimeConst* pc, int Tt, int NT, const uint32_t* twp, uint32_t* tws) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < Tt * 32; idx += gridDim.x * blockDim.x) {
+    const int q = idx >> 5, j = idx & 31;
+    const uint32_t p = pc[q].p;
+    const uint32_t w = j ? redc((uint64_t)twp[(int64_t)q * NT + j], p, pc[q].pinv) : 0u;
+    tws[2 * idx] = w;
+    tws[2 * idx + 1] = (uint32_t)(((uint64_t)w << 32) / p);
+  }
+}
+
 __global__ void k_init_garner(const PrimeConst* pc, int Tg, uint32_t* ginv) {
   const int64_t total = (int64_t)Tg * Tg;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -305,9 +316,10 @@ int DeviceTables::init(cudaStream_t s) {
 void DeviceTables::release() {
   for (void* p : {(void*)pc, (void*)pw, (void*)mpw, (void*)lgp, (void*)tw, (void*)itw,
                   (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp, (void*)ws_m,
-                  (void*)ws_y, (void*)ws_moff, (void*)ws_yoff, (void*)q62, (void*)twp, (void*)itwp})
+                  (void*)ws_y, (void*)ws_moff, (void*)ws_yoff, (void*)q62, (void*)twp, (void*)itwp,
+                  (void*)tws})
     if (p) cudaFree(p);
-  twp = itwp = nullptr;
+  twp = itwp = tws = nullptr;
   ws_m = ws_y = q62 = nullptr;
   ws_moff = nullptr;
   ws_yoff = nullptr;
@@ -335,12 +347,14 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   // finish any work that may still read the old tables
   if (cudaStreamSynchronize(s) != cudaSuccess) return kErrCuda;
   uint32_t *ntw = nullptr, *nitw = nullptr, *ncp = nullptr, *nicp = nullptr, *nninv = nullptr,
-           *nginv = nullptr, *omega = nullptr, *gi = nullptr, *ntwp = nullptr, *nitwp = nullptr;
+           *nginv = nullptr, *omega = nullptr, *gi = nullptr, *ntwp = nullptr, *nitwp = nullptr,
+           *ntws = nullptr;
   int rc = 0;
   rc |= cu_fail(cudaMalloc(&ntw, sizeof(uint32_t) * (size_t)newT * (newNT / 2)));
   rc |= cu_fail(cudaMalloc(&nitw, sizeof(uint32_t) * (size_t)newT * (newNT / 2)));
   rc |= cu_fail(cudaMalloc(&ntwp, sizeof(uint32_t) * (size_t)newT * newNT));
   rc |= cu_fail(cudaMalloc(&nitwp, sizeof(uint32_t) * (size_t)newT * newNT));
+  rc |= cu_fail(cudaMalloc(&ntws, sizeof(uint32_t) * (size_t)newT * 64));
   rc |= cu_fail(cudaMalloc(&ncp, sizeof(uint32_t) * (size_t)newT * newNT));
   rc |= cu_fail(cudaMalloc(&nicp, sizeof(uint32_t) * (size_t)newT * newNT));
   rc |= cu_fail(cudaMalloc(&nninv, sizeof(uint32_t) * (size_t)newT * (kLogNMax + 1)));
@@ -352,7 +366,7 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   rc |= cu_fail(cudaMalloc(&gi, sizeof(uint32_t) * newT));
   if (rc) {
     for (void* p : {(void*)ntw, (void*)nitw, (void*)ncp, (void*)nicp, (void*)nninv, (void*)nginv,
-                    (void*)omega, (void*)gi, (void*)ntwp, (void*)nitwp})
+                    (void*)omega, (void*)gi, (void*)ntwp, (void*)nitwp, (void*)ntws})
       if (p) cudaFree(p);
     return kErrNoMem;
   }
@@ -369,6 +383,8 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   k_init_transform<<<1024, 256, 0, s>>>(pc, omega, gi, newT, newNT, newLog, ntw, nitw, ncp, nicp, nninv);
   rc |= cu_fail(cudaGetLastError());
   k_init_packed<<<1024, 256, 0, s>>>(pc, newT, newNT, newLog, ntw, nitw, ntwp, nitwp);
+  rc |= cu_fail(cudaGetLastError());
+  k_init_shoup<<<(newT * 32 + 255) / 256, 256, 0, s>>>(pc, newT, newNT, ntwp, ntws);
   rc |= cu_fail(cudaGetLastError());
   k_init_garner<<<1024, 256, 0, s>>>(pc, newT, nginv);
   rc |= cu_fail(cudaGetLastError());
@@ -405,10 +421,11 @@ int DeviceTables::ensure(int needT, int needLogN, cudaStream_t s) {
   cudaFree(gi);
   for (void* p : {(void*)tw, (void*)itw, (void*)cp, (void*)icp, (void*)ninv, (void*)ginv, (void*)pp,
                   (void*)ws_m, (void*)ws_y, (void*)ws_moff, (void*)ws_yoff, (void*)q62, (void*)twp,
-                  (void*)itwp})
+                  (void*)itwp, (void*)tws})
     if (p) cudaFree(p);
   twp = ntwp;
   itwp = nitwp;
+  tws = ntws;
   ws_m = nwsm;
   ws_y = nwsy;
   ws_moff = nmoff;
@@ -441,6 +458,7 @@ Tables DeviceTables::view() const {
   t.itw = itw;
   t.twp = twp;
   t.itwp = itwp;
+  t.tws = tws;
   t.cp = cp;
   t.icp = icp;
   t.ninv = ninv;

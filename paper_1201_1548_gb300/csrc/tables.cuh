@@ -27,7 +27,7 @@ struct DeviceTables {
   uint32_t* mpw = nullptr;
   int64_t* lgp = nullptr;
   uint32_t *tw = nullptr, *itw = nullptr, *cp = nullptr, *icp = nullptr, *ninv = nullptr;
-  uint32_t *twp = nullptr, *itwp = nullptr;
+  uint32_t *twp = nullptr, *itwp = nullptr, *tws = nullptr;
   uint32_t* ginv = nullptr;
   uint32_t* pp = nullptr;
   int LPP = 0;

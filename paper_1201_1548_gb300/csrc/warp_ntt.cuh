@@ -69,6 +69,32 @@ struct RegStages<R, -1, MASK, LEN0, LANEMUL> {
   static __device__ __forceinline__ void run(uint32_t (&)[R], const uint32_t*, int, const Mod&) {}
 };
 
+// layout B register stages h = 2^LH .. 1 on full registers with Shoup's products: the
+// twiddle of a pair is the same in every lane, S[2 j] = omega_{2h}^(r mod h) in standard
+// form (j = h + r mod h) and S[2 j + 1] = floor(S[2 j] 2^32 / p); the results are the same
+// residues as with the Montgomery-form twiddles of P
+template <int R, int LH>
+struct RegStagesS {
+  static __device__ __forceinline__ void run(uint32_t (&v)[R], const uint32_t* S, const Mod& M) {
+    constexpr int h = 1 << LH;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & h) continue;
+      const int j = h + (r & (h - 1));
+      const uint32_t w = __ldg(S + 2 * j), ws = __ldg(S + 2 * j + 1);
+      const uint32_t a = v[r], b = v[r + h];
+      v[r] = madd(a, b, M.p);
+      v[r + h] = mmul_shoup(msub(a, b, M.p), w, ws, M.p);
+    }
+    RegStagesS<R, LH - 1>::run(v, S, M);
+  }
+};
+
+template <int R>
+struct RegStagesS<R, -1> {
+  static __device__ __forceinline__ void run(uint32_t (&)[R], const uint32_t*, const Mod&) {}
+};
+
 template <int R>
 struct Log2R {
   static constexpr int v = (R >= 32) ? 5 : (R >= 16) ? 4 : (R >= 8) ? 3 : (R >= 4) ? 2 : (R >= 2) ? 1 : 0;
@@ -132,14 +158,15 @@ __device__ __forceinline__ void warp_transpose_ba(uint32_t (&v)[32], uint32_t* s
 }
 
 // N = 1024: five register stages in layout A (len = 512 .. 32), transpose, five register
-// stages in layout B (len = 16 .. 1), transpose back
+// stages in layout B (len = 16 .. 1, Shoup's products with the prime's pairs S), transpose
+// back
 template <uint32_t MASK>
 __device__ __forceinline__ void warp_dif_1024_pk(uint32_t (&v)[32], uint32_t* sw, const uint32_t* P,
-                                                 const Mod M) {
+                                                 const uint32_t* S, const Mod M) {
   const int lane = threadIdx.x & 31;
   RegStages<32, 4, MASK, 32, 1>::run(v, P, lane, M);
   warp_transpose_ab(v, sw);
-  RegStages<32, 4, 0xffffffffu, 1, 0>::run(v, P, lane, M);
+  RegStagesS<32, 4>::run(v, S, M);
   warp_transpose_ba(v, sw);
 }
 

@@ -1,5 +1,6 @@
 """The 31-bit modular arithmetic of the kernels (Montgomery's reduction with predicate-free
-corrections, modular add / subtract / negate, powers and Fermat inverses) is compiled for
+corrections, modular add / subtract / negate, powers, Fermat inverses and Shoup's products
+by a fixed factor) is compiled for
 the host as well as the device; here its host build is checked against Python integers
 on the extreme inputs its preconditions allow, for primes at both ends of the table."""
 
@@ -39,6 +40,7 @@ int main() {
       case 8: r = M.pinv; break;
       case 9: r = host_to_mont(x, p); break;
       case 10: r = host_powmod(x, y, p); break;
+      case 11: r = mmul_shoup((uint32_t)x, (uint32_t)y, (uint32_t)((y << 32) / p), M.p); break;
     }
     std::printf("%" PRIu64 "\n", r);
   }
@@ -118,4 +120,19 @@ def test_modular_operations(harness):
             want.append(am)
             cases.append((10, p, a, e))
             want.append(pow(a, e, p))
+    assert harness(cases) == want
+
+
+def test_shoup_products(harness):
+    """x w mod p by Shoup's method (the transforms' short stages) for x, w below p, at the
+    ends of both runs of the table (primes with 3p < 2^32 first, then up to 2^31)."""
+    rng = random.Random(33)
+    cases, want = [], []
+    table = bs.bs_prime_table(6213)
+    for p in table[:2] + table[2085:2089] + table[-2:]:
+        edge = [0, 1, 2, p - 2, p - 1]
+        for x in edge + [rng.randrange(p) for _ in range(100)]:
+            for w in (rng.choice(edge), rng.randrange(p)):
+                cases.append((11, p, x, w))
+                want.append(x * w % p)
     assert harness(cases) == want
