@@ -548,6 +548,12 @@ int bs_serve_stats(bs_ctx *ctx, bs_serve_info *out);
 
 /* ---------------------------------------------------------------------------------
  * Measurement
+ *
+ * Every stage's kernel launches lie in an NVTX range named "bs.plan", "bs.eval",
+ * "bs.unires", "bs.interp" or "bs.crt", and bs_resultant, bs_resultant_batch,
+ * bs_resultant_device and each served batch ("bs.serve.batch", "bs.serve.large_batch")
+ * in one of their own, so that a profiler can select them (ncu --nvtx --nvtx-include
+ * "bs.unires/"); without a tool attached the ranges cost nothing.
  * ------------------------------------------------------------------------------ */
 
 /* Throughput of one integer-multiply instruction kind on every SM of the context's
