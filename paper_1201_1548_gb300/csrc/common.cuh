@@ -50,7 +50,8 @@ struct Tables {
   const uint32_t* twp;
   const uint32_t* itwp;
   // [Tt][64]: for j = 1 .. 31, tws[2 j] = twp[j] in standard form w and tws[2 j + 1] =
-  // floor(w 2^32 / p), the pairs of Shoup's products in the transforms' short stages
+  // floor(w 2^32 / p), the pairs of Shoup's products in the transforms' short stages;
+  // j = 0 holds the pair of 1
   const uint32_t* tws;
   // Garner table for the first Tg primes: ginv[a * Tg + b] = p_a^-1 mod p_b (Montgomery)
   const uint32_t* ginv;

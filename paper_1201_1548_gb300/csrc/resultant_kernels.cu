@@ -569,7 +569,7 @@ __device__ __forceinline__ void eval_row_nz(const Job* J, int q, int row, const 
   if constexpr (R == 32)
     warp_dif_1024_pk<MASK>(v, sw, s_tw, T.tws + (int64_t)q * 64, M);
   else
-    warp_dif_pk<R, MASK>(v, s_tw, M, pc.one_m);
+    warp_dif_pk<R, MASK>(v, s_tw, T.tws + (int64_t)q * 64, M);
   uint32_t* dst = J->ev + ((int64_t)q * J->rows + row) * N;
   if (dbg_ok(((int64_t)q * J->rows + row + 1) * N <= job_ev_words(J), J->status, kDbgEvalOut)) {
 #pragma unroll
@@ -587,9 +587,9 @@ __device__ __forceinline__ void eval_row_small(const Job* J, int q, int row, con
   uint32_t v[1];
   eval_load_row<1>(v, J, q, row, T, sw, s_cp, pc, M, N);
   if (N < 32)
-    warp_dif_short(v[0], N, s_tw, M, pc.one_m);
+    warp_dif_short(v[0], N, T.tws + (int64_t)q * 64, M);
   else
-    warp_dif_pk<1, 1u>(v, s_tw, M, pc.one_m);
+    warp_dif_pk<1, 1u>(v, s_tw, T.tws + (int64_t)q * 64, M);
   if (lane < N && dbg_ok(((int64_t)q * J->rows + row + 1) * N <= job_ev_words(J), J->status, kDbgEvalOut))
     J->ev[((int64_t)q * J->rows + row) * N + lane] = v[0];
   __syncwarp();

@@ -204,7 +204,8 @@ __global__ void k_init_shoup(const PrimeConst* pc, int Tt, int NT, const uint32_
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < Tt * 32; idx += gridDim.x * blockDim.x) {
     const int q = idx >> 5, j = idx & 31;
     const uint32_t p = pc[q].p;
-    const uint32_t w = j ? redc((uint64_t)twp[(int64_t)q * NT + j], p, pc[q].pinv) : 0u;
+    // j = 0 holds the pair of 1 (the factor of the lanes that only add in a shuffle stage)
+    const uint32_t w = j ? redc((uint64_t)twp[(int64_t)q * NT + j], p, pc[q].pinv) : 1u;
     tws[2 * idx] = w;
     tws[2 * idx + 1] = (uint32_t)(((uint64_t)w << 32) / p);
   }

@@ -102,36 +102,37 @@ struct Log2R {
 
 // N = 32 R, 2 <= R <= 16 (R = 1 with N = 32 as well): register stages, then five
 // shuffle stages (len = 16 .. 1)
+// (the shuffle stages multiply by Shoup's method with the prime's pairs S, the pair of 1
+// for the lanes that only add)
 template <int R, uint32_t MASK>
-__device__ __forceinline__ void warp_dif_pk(uint32_t (&v)[R], const uint32_t* P, const Mod M,
-                                            uint32_t one_m) {
+__device__ __forceinline__ void warp_dif_pk(uint32_t (&v)[R], const uint32_t* P, const uint32_t* S,
+                                            const Mod M) {
   const int lane = threadIdx.x & 31;
   RegStages<R, Log2R<R>::v - 1, MASK, 32, 1>::run(v, P, lane, M);
 #pragma unroll 1
   for (int lg = 4; lg >= 0; --lg) {
     const int len = 1 << lg;
     const bool upper = (lane & len) != 0;
-    const uint32_t w = upper ? P[len + (lane & (len - 1))] : one_m;
+    const uint2 ww = __ldg(reinterpret_cast<const uint2*>(S) + (upper ? len + (lane & (len - 1)) : 0));
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t x = v[r];
       const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
       const uint32_t t = upper ? msub(y, x, M.p) : madd(x, y, M.p);
-      v[r] = mmul(t, w, M);
+      v[r] = mmul_shoup(t, ww.x, ww.y, M.p);
     }
   }
 }
 
 // N < 32: one register per lane, lanes >= N hold zeros; stages len = N/2 .. 1
-__device__ __forceinline__ void warp_dif_short(uint32_t& v, int N, const uint32_t* P, const Mod M,
-                                               uint32_t one_m) {
+__device__ __forceinline__ void warp_dif_short(uint32_t& v, int N, const uint32_t* S, const Mod M) {
   const int lane = threadIdx.x & 31;
   for (int len = N >> 1; len >= 1; len >>= 1) {
     const bool upper = (lane & len) != 0;
-    const uint32_t w = upper ? P[len + (lane & (len - 1))] : one_m;
+    const uint2 ww = __ldg(reinterpret_cast<const uint2*>(S) + (upper ? len + (lane & (len - 1)) : 0));
     const uint32_t x = v;
     const uint32_t y = __shfl_xor_sync(0xffffffffu, x, len);
-    v = mmul(upper ? msub(y, x, M.p) : madd(x, y, M.p), w, M);
+    v = mmul_shoup(upper ? msub(y, x, M.p) : madd(x, y, M.p), ww.x, ww.y, M.p);
   }
 }
 
