@@ -129,7 +129,11 @@ def test_batches_overlap_and_context_is_reserved(server):
     for t in tickets:
         assert server.wait(t, 120000)
         assert server.poll(t)[0] == 0
-    assert server.serve_stats()["max_inflight"] >= 2
+    st = server.serve_stats()
+    assert st["max_inflight"] >= 2
+    # the per-phase wall times cover the 12 batches: some device work, no negative phase
+    assert st["batches"] == 12 and st["device_ms"] > 0.0
+    assert st["host_plan_ms"] >= 0.0 and st["host_finish_ms"] >= 0.0
 
 
 def test_submit_from_several_threads(ctx, server):
@@ -152,3 +156,31 @@ def test_submit_from_several_threads(ctx, server):
         assert status == 0 and coeffs == _alone(ctx, job)
     with pytest.raises(bs.BsError):
         server.poll(tickets[0])                              # released after collection
+
+
+def test_work_classes_and_priorities(ctx, server):
+    """A large resultant (more than 2e9 multiply-reduces) and tiny ones submitted together:
+    every result equals the same call alone, and the tiny jobs, which take other slots and
+    the high-priority stream, complete before the large one."""
+    import time
+    rng = _rng(59)
+    big = (dense_curve(rng, 44, 200), dense_curve(rng, 44, 200))
+    p = bs.bs_plan(*big)
+    assert p["k_total"] * p["N"] * p["m_e"] * p["n_e"] > 2e9
+    tiny = [(dense_curve(rng, 4, 16), dense_curve(rng, 4, 16)) for _ in range(8)]
+    want_big = ctx.resultant(*big)
+    want_tiny = [ctx.resultant(f, g) for f, g in tiny]
+    server.serve_start(slots=4, max_batch=4)
+    tb = server.submit(bs.JOB_RESULTANT, *big)
+    time.sleep(0.001)
+    tt = [server.submit(bs.JOB_RESULTANT, f, g) for f, g in tiny]
+    done_tiny = []
+    for t in tt:
+        assert server.wait(t, 120000)
+        done_tiny.append(server.poll(t))
+    assert server.wait(tb, 120000)
+    st_b, coeffs_b, _, lat_b = server.poll(tb)
+    assert st_b == 0 and coeffs_b == want_big
+    for (st, coeffs, _, lat), want in zip(done_tiny, want_tiny):
+        assert st == 0 and coeffs == want
+        assert lat < lat_b
