@@ -457,7 +457,7 @@ int bs_autotune_batch(bs_ctx *ctx, int n, const bs_bipoly *f, const bs_bipoly *g
                       bs_tune_info *info);
 
 /* Set the batched launch shapes explicitly (t == NULL restores the defaults: evaluation
- * by independent warps with 4 blocks per SM, 128 threads per univariate block, 8
+ * by independent warps with 5 blocks of 7 warps per SM, 128 threads per univariate block, 8
  * coefficients and 4 blocks per SM for reconstruction).  The timing fields of *t are
  * ignored.  BS_ERR_ARG for a shape outside the ranges of bs_tune_info. */
 int bs_set_tune(bs_ctx *ctx, const bs_tune_info *t);

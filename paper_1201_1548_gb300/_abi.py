@@ -661,7 +661,7 @@ class Context:
         out["uni_threads"] = list(info.uni_threads)
         return out
 
-    def set_tune(self, eval_warps=8, eval_blocks_per_sm=4, uni_threads=(128,) * 6, crt_tile=8,
+    def set_tune(self, eval_warps=8, eval_blocks_per_sm=5, uni_threads=(128,) * 6, crt_tile=8,
                  crt_blocks_per_sm=4, eval_independent=1):
         t = _TuneInfo()
         t.eval_warps, t.eval_blocks_per_sm = eval_warps, eval_blocks_per_sm

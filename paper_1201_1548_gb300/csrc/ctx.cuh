@@ -23,7 +23,7 @@ struct NvtxScope {
 // for a batch (the device-planned single job always uses the defaults)
 struct Tune {
   int eval_warps = 8;           // rows (one warp each) per evaluation block, 1..8
-  int eval_blocks_per_sm = 4;   // cap of the persistent evaluation grid
+  int eval_blocks_per_sm = 5;   // cap of the persistent evaluation grid
   int uni_threads[kNumUniClasses] = {128, 128, 128, 128, 128, 128};  // 64, 128 or 256
   int crt_tile = 8;             // coefficients (one warp each) per reconstruction block, 1..8
   int crt_blocks_per_sm = 4;    // cap of the persistent reconstruction grid

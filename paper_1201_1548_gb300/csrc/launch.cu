@@ -71,8 +71,8 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
   int g;
   const PfHint pf{L.kt_max, 1 << L.logN_max, L.kmax};
   for (int c = 0; c < kNumEvalClasses; ++c) {
-    if (L.eval_independent) {  // items are rows, eight warps per block
-      g = grid_for((L.evw_items[c] + 7) / 8, (int64_t)sms * L.eval_blocks_per_sm);
+    if (L.eval_independent) {  // items are rows, kEvalIwWarps warps per block
+      g = grid_for((L.evw_items[c] + kEvalIwWarps - 1) / kEvalIwWarps, (int64_t)sms * L.eval_blocks_per_sm);
       if (g) launch_eval_iw(c, g, s, L.jobs, L.evw[c], Tv, pf);
     } else {
       g = grid_for(L.evw_items[c], (int64_t)sms * L.eval_blocks_per_sm);
@@ -80,7 +80,7 @@ static void enqueue(bs_ctx* ctx, const StageLaunch& L, const Tables& Tv, cudaStr
     }
   }
   if (L.eval_independent) {
-    g = grid_for((L.evw_any_items + 7) / 8, (int64_t)sms * 4);
+    g = grid_for((L.evw_any_items + kEvalIwWarps - 1) / kEvalIwWarps, (int64_t)sms * kEvalIwBlocksPerSm);
     if (g) launch_eval_iw(-1, g, s, L.jobs, L.evw_any, Tv, pf);
   } else {
     g = grid_for(L.evw_any_items, (int64_t)sms * 8);

@@ -692,13 +692,16 @@ __global__ void __launch_bounds__(kEvalThreads, 4) k_eval_w(const Job* jobs, Wor
 // The same evaluation with independent warps: the work list counts single rows, each
 // warp takes any (job, prime, row) item, and the prime's packed twiddles and coset powers
 // are read through the L1 cache instead of being staged per block, so no block waits at
-// a barrier for a change of prime and no warp idles at the end of a prime's rows.
+// a barrier for a change of prime and no warp idles at the end of a prime's rows.  Blocks
+// of seven warps at 56 registers, five per SM: 35 resident warps per SM instead of 32 at
+// 64 registers, which takes the 5,200 rows of 80 primes x 65 rows in one wave of 5,320
+// warps (at 32 per SM, 336 rows ran in a second wave behind the first).
 template <int R>
-__global__ void __launch_bounds__(kEvalThreads, 4) k_eval_iw(const Job* jobs, WorkList wl,
-                                                             Tables T, PfHint pf) {
+__global__ void __launch_bounds__(kEvalIwWarps * 32, kEvalIwBlocksPerSm)
+    k_eval_iw(const Job* jobs, WorkList wl, Tables T, PfHint pf) {
   pdl_wait();
   constexpr int NS = R == 0 ? (1 << kWarpLogNMax) : 32 * R;  // largest transform size
-  __shared__ uint32_t s_stage[kEvalThreads / 32][(R == 32 || R == 0) ? 33 * 32 : NS];
+  __shared__ uint32_t s_stage[kEvalIwWarps][(R == 32 || R == 0) ? 33 * 32 : NS];
   const int warp = threadIdx.x >> 5;
   uint32_t* sw = s_stage[warp];
   const int nw = blockDim.x >> 5;
@@ -1759,7 +1762,7 @@ void launch_eval(int grid, int warps, cudaStream_t s, const Job* jobs, WorkList 
   launch_k(k_eval, grid, warps * 32, smem, s, jobs, wl, T);
 }
 void launch_eval_iw(int cls, int grid, cudaStream_t s, const Job* jobs, WorkList wl, Tables T, PfHint pf) {
-  const int th = kEvalThreads;
+  const int th = kEvalIwWarps * 32;
   switch (cls) {
     case -1: launch_k(k_eval_iw<0>, grid, th, 0, s, jobs, wl, T, pf); break;
     case 0: launch_k(k_eval_iw<1>, grid, th, 0, s, jobs, wl, T, pf); break;

@@ -7,6 +7,10 @@ namespace bs {
 constexpr int kUniTile = 128;     // default threads of a univariate-resultant block
 constexpr int kUniMaxThreads = 256;  // largest univariate-resultant block
 constexpr int kEvalThreads = 256; // threads of a transform block
+// warps of an independent-warp evaluation block; five such blocks fit an SM at 56 registers,
+// so 35 warps per SM take the 80 x 65 rows of a degree-32 discriminant in one wave
+constexpr int kEvalIwWarps = 7;
+constexpr int kEvalIwBlocksPerSm = 5;
 constexpr int kCrtWarps = 8;      // warps of a reconstruction block
 constexpr int kCrtTile = 8;       // coefficients per reconstruction block
 constexpr int kCrtInvSmem = 160;  // prime counts whose inverse table is staged in smem
