@@ -508,7 +508,18 @@ __global__ void __launch_bounds__(kEvalBigMaxWarps * 32) k_eval(const Job* jobs,
     if (active) {
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = sm[1024 * warp + 32 * r + lane];
-      warp_dif_1024_pk<0xffffffffu>(v, sw, s_tw, T.tws + (int64_t)q * 64, M);
+      // the stages above combine only points 1024 or more apart, so element e of this
+      // warp's 1024 is a sum over the row's points e + 1024 k; a row reaches point
+      // eo < 1024 at most, so only elements e <= eo can be nonzero: the first registers
+      // of layout A, and the pruned transform skips the rest (rows of up to 96
+      // coefficients, e.g. degree-64 curves)
+      const uint32_t* S = T.tws + (int64_t)q * 64;
+      if (eo < 64)
+        warp_dif_1024_pk<0x3u>(v, sw, s_tw, S, M);
+      else if (eo < 96)
+        warp_dif_1024_pk<0x7u>(v, sw, s_tw, S, M);
+      else
+        warp_dif_1024_pk<0xffffffffu>(v, sw, s_tw, S, M);
       uint32_t* dst = J->ev + ((int64_t)q * rows + row) * N + 1024 * warp;
 #pragma unroll
       for (int r = 0; r < 32; ++r) dst[32 * r + lane] = v[r];
