@@ -145,6 +145,22 @@ def test_device_path_large_transforms(ctx):
             assert P.evaluate(dev, x0) % p == R.res_at_point_modp(f, g, x0, p)
 
 
+def test_large_transform_rows_of_65_to_96_coefficients(ctx):
+    """Rows of 81 coefficients at 2048 points: the stages of the shared-memory transform
+    that combine points 1024 apart leave only the first three registers of each warp's
+    chunk nonzero, and the warp runs its pruned 1024-point variant.  The host and device
+    paths give the oracle's resultant coefficient by coefficient."""
+    import paper_1201_1548_gb300 as bs
+    rng = _rng(88)
+    f = [[int(v) for v in rng.integers(-99, 100, 81)] for _ in range(8)]  # deg_y 7, deg_x 80
+    g = d_dy(f)
+    assert bs.bs_plan(f, g)["N"] == 2048
+    want = R.res_y(f, g)
+    assert len(want) == 1041
+    assert ctx.resultant(f, g) == want
+    assert _device_call(ctx, f, g) == want
+
+
 def test_device_plan_exact_spares(ctx):
     """Single-coefficient leading rows: the device plan counts exactly the table primes that
     divide them.  With lc_y f = p_0 p_1 (two table primes) those two are rejected and
