@@ -769,8 +769,31 @@ def _case_projection32(reps):
         raise SystemExit("inconsistent projection results")
 
 
+def _case_large64(reps):
+    """A degree 57 x 64 pair of dense curves with 256-bit coefficients (seed 7; 1,047
+    primes x 4096 points), one bs_resultant call per repetition with the stages separated
+    by events; prints each call's stage times."""
+    import numpy as np
+    import paper_1201_1548_gb300 as bs
+    from workloads import dense_curve
+    rng = np.random.Generator(np.random.PCG64(7))
+    f = dense_curve(rng, 57, 256)
+    g = dense_curve(rng, 64, 256)
+    ctx = bs.Context(0)
+    first = ctx.resultant(f, g)
+    ctx.profile(True)
+    for _ in range(reps):
+        if ctx.resultant(f, g) != first:
+            raise SystemExit("repeated calls differ")
+        st = ctx.stage_times()
+        print("stage ms (upload, evaluation, univariate, interpolation, reconstruction):",
+              " ".join(f"{x:.3f}" for x in st))
+    ctx.profile(False)
+    print("stats", ctx.last_stats())
+
+
 CASES = {"discriminant32": _case_discriminant32, "batch4096": _case_batch4096,
-         "projection32": _case_projection32}
+         "projection32": _case_projection32, "large64": _case_large64}
 
 
 def run_case(args):
